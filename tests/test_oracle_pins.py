@@ -1,0 +1,310 @@
+"""Pins of the CPU oracle to facts the paper and mathematics fix.
+
+Each ``check_*`` function takes the oracle module, so that
+``test_oracle_mutations.py`` can run the same checks against deliberately
+broken copies of it and show that every plausible mistake fails one of them.
+"""
+import math
+import os
+import types
+
+import numpy as np
+import pytest
+import scipy.fft
+import scipy.linalg
+
+from oracle import tx16_oracle as O
+from paper_1606_07414_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_kv(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if line:
+                out[line[0]] = [float(v) for v in line[1:]]
+    return out
+
+
+def _golden_ints(name):
+    vals = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            vals += [int(v) for v in line.split("#")[0].split()]
+    return vals
+
+
+# ----------------------------------------------------------------------------
+# Sec. 2.1: T, S, C_hat
+# ----------------------------------------------------------------------------
+def check_T_gram_matches_printed_S(o):
+    """Two printed items agree: S (printed) == sqrt((T T^t)^-1) from the
+    printed T, via scipy's matrix square root; T T^t is diagonal."""
+    Tm = o.T.astype(np.float64)
+    assert set(np.unique(o.T)) <= {-1, 0, 1}
+    G = Tm @ Tm.T
+    assert np.count_nonzero(G - np.diag(np.diag(G))) == 0, "T T^t not diagonal"
+    S_from_T = scipy.linalg.sqrtm(np.linalg.inv(G)).real
+    np.testing.assert_allclose(S_from_T, np.diag(o.S_DIAG), atol=1e-14)
+
+
+def check_c_hat_orthogonal(o):
+    C = o.c_hat()
+    np.testing.assert_allclose(C @ C.T, np.eye(16), atol=1e-14)
+
+
+def check_factor_product_is_T(o):
+    F = o.factor_matrices()
+    P = np.eye(16, dtype=np.int64)
+    for name in o.FACTOR_ORDER:
+        P = F[name] @ P
+    assert np.array_equal(P, o.T), "P2 M4 M3 M2 P1 M1 != T"
+
+
+def check_addition_counts(o):
+    """Table 1: 44 additions (16 + 16 + 8 + 4), 0 multiplications; direct 112."""
+    g = _golden_kv("table1_complexity.txt")
+    F = o.factor_matrices()
+    per_stage = [o.stage_additions(F[n]) for n in o.FACTOR_ORDER]
+    assert per_stage == [16, 0, 16, 8, 4, 0]
+    assert sum(per_stage) == g["proposed_add"][0]
+    assert o.stage_additions(o.T) == g["direct_add"][0]
+    # counted while running, too
+    _, adds = o.t16_factored(np.arange(16))
+    assert adds == g["proposed_add"][0]
+    for key, other in (("saving_vs_60", 60), ("saving_vs_64", 64), ("saving_vs_72", 72)):
+        assert round(100 * (1 - adds / other), 2) == g[key][0]
+
+
+def check_factored_equals_direct_1d(o):
+    """Linearity makes the 16 unit vectors an exhaustive proof; add brute force
+    over {0,1}^16 and 10,000 seeded random vectors (the hardware test size of
+    Sec. 4)."""
+    E = np.eye(16, dtype=np.int64)
+    y, _ = o.t16_factored(E)  # row j of E -> T e_j
+    assert np.array_equal(y.T, o.T)
+    bits = ((np.arange(1 << 16)[:, None] >> np.arange(16)[None, :]) & 1).astype(np.int64)
+    y, _ = o.t16_factored(bits)
+    assert np.array_equal(y, bits @ o.T.T)
+    x = (synth.splitmix64(2016, 16 * 10000) % np.uint64(2048)).astype(np.int64).reshape(-1, 16) - 1024
+    y, _ = o.t16_factored(x)
+    assert np.array_equal(y, x @ o.T.T)
+
+
+def check_forward_2d(o):
+    """Factored == direct on random 8- and 10-bit blocks; DC is the block sum
+    (row 0 of T is all ones); a block that varies only along its rows
+    (horizontally) has energy only in row u = 0 of Y, and one that varies only
+    down its columns only in column v = 0 (B = C A C^t transforms columns of A
+    on the left and rows on the right)."""
+    for bits in (8, 10):
+        X = (synth.splitmix64(7 + bits, 64 * 256) % np.uint64(1 << bits)).astype(np.int64)
+        X = X.reshape(64, 16, 16)
+        Yd = o.forward_direct(X)
+        assert np.array_equal(Yd, o.forward_factored(X))
+        assert np.array_equal(Yd[:, 0, 0], X.sum(axis=(1, 2)))
+    row = np.arange(16, dtype=np.int64) * 13 % 251
+    horiz = np.broadcast_to(row[None, :], (16, 16))
+    Y = o.forward_direct(horiz[None])[0]
+    assert np.any(Y[0, 1:] != 0) and np.all(Y[1:, :] == 0)
+    Y = o.forward_direct(horiz.T[None])[0]
+    assert np.any(Y[1:, 0] != 0) and np.all(Y[:, 1:] == 0)
+    # magnitude bound used for int32 kernels: 256 * max|x|
+    ext = np.full((1, 16, 16), 255, dtype=np.int64)
+    assert np.abs(o.forward_direct(ext)).max() == 255 * 256
+
+
+# ----------------------------------------------------------------------------
+# Sec. 2.3, Table 2
+# ----------------------------------------------------------------------------
+def check_exact_dct_is_textbook(o):
+    """The exact DCT-II of Table 2 is scipy's orthonormal DCT-II."""
+    ref = scipy.fft.dct(np.eye(16), type=2, norm="ortho", axis=0)
+    np.testing.assert_allclose(o.dct_matrix(16), ref, atol=1e-14)
+
+
+def check_table2(o):
+    g = _golden_kv("table2_proposed.txt")
+    C = o.c_hat()
+    got = [o.dct_distortion(C), o.total_error_energy(C), o.transform_mse(C),
+           o.coding_gain(C), o.transform_efficiency(C)]
+    for name, want, have in zip(("d2", "eps", "mse", "cg", "eta"), g["proposed"], got):
+        assert round(have, 3) == pytest.approx(want, abs=1e-9), (name, have, want)
+    D = o.dct_matrix(16)
+    got = [o.dct_distortion(D), o.total_error_energy(D), o.transform_mse(D),
+           o.coding_gain(D), o.transform_efficiency(D)]
+    for name, want, have in zip(("d2", "eps", "mse", "cg", "eta"), g["exact_dct"], got):
+        assert abs(round(have, 3)) == pytest.approx(want, abs=1e-9), (name, have, want)
+
+
+# ----------------------------------------------------------------------------
+# Sec. 3.1 codec
+# ----------------------------------------------------------------------------
+def check_zigzag_matches_jpeg(o):
+    want = _golden_ints("jpeg_zigzag8.txt")
+    assert [u * 8 + v for (u, v) in o.zigzag_order(8)] == want
+    zz = o.zigzag_order(16)
+    assert len(set(zz)) == 256
+    # the 16x16 scan restricted to the first 36 cells (the triangle shared
+    # with the 8x8 scan) is the JPEG scan
+    assert [(u, v) for (u, v) in zz[:36]] == [(k // 8, k % 8) for k in want[:36]]
+
+
+def check_zonal_is_prefix_per_column(o):
+    """Inside each column v the kept rows are a prefix 0..m_v-1, and the zone
+    grows by exactly one cell per step of r."""
+    prev = 0
+    for r in range(1, 257):
+        m = o.zonal_mask(r)
+        assert m.sum() == r
+        for v in range(16):
+            col = m[:, v]
+            k = col.sum()
+            assert col[:k].all() and not col[k:].any()
+        assert m.sum() - prev == 1
+        prev = m.sum()
+
+
+def check_blocks_roundtrip(o):
+    img = np.arange(48 * 32, dtype=np.int64).reshape(48, 32)
+    b = o.image_to_blocks(img)
+    assert b.shape == (6, 16, 16)
+    assert np.array_equal(b[3], img[16:32, 16:32])  # raster block order
+    assert np.array_equal(o.blocks_to_image(b, 48, 32), img)
+
+
+def check_perfect_reconstruction(o):
+    """r = 256 with no quantiser reconstructs exactly: C_hat^t C_hat X C_hat^t
+    C_hat = X by orthogonality (Sec. 2.1), here as the integer identity
+    256 X = T^t (D' Y D') T."""
+    for bits in (8, 10):
+        img = synth.ar1_image(3 + bits, 64, 48, 0.95, bits).astype(np.int64)
+        X = o.image_to_blocks(img)
+        Y = o.forward_direct(X)
+        num = o.inverse_exact_zonal(Y, 256)
+        assert np.array_equal(num, 256 * X)
+        res = o.codec_image(img, None, 256, bits)
+        assert res["sse"] == 0 and res["psnr"] == math.inf
+
+
+def check_dc_only_is_block_mean(o):
+    """r = 1 keeps only DC: every pixel of a block becomes the rounded block
+    mean (closed form), with no quantiser and with a tiny power-of-two q."""
+    img = synth.ar1_image(11, 64, 64, 0.9).astype(np.int64)
+    X = o.image_to_blocks(img)
+    mean = X.sum(axis=(1, 2)) / 256.0
+    want = np.sign(mean) * np.floor(np.abs(mean) + 0.5)
+    for q, prec in ((None, "fp64"), (2.0 ** -12, "fp64"), (2.0 ** -12, "fp32")):
+        rec = o.image_to_blocks(o.codec_image(img, q, 1, 8, prec)["recon"])
+        assert np.array_equal(rec, np.broadcast_to(want[:, None, None], rec.shape)), (q, prec)
+
+
+def check_quantiser_limits(o):
+    img = synth.ar1_image(12, 32, 64, 0.95).astype(np.int64)
+    for prec in ("fp64", "fp32"):
+        res = o.codec_image(img, 2.0 ** -8, 256, 8, prec)
+        assert res["sse"] == 0, prec  # step -> 0 recovers X
+        res = o.codec_image(img, 1e9, 256, 8, prec)
+        assert np.all(res["levels"] == 0) and res["sse"] == int(np.sum(img * img)), prec
+
+
+def check_quantiser_scaling(o):
+    """level = round(s_u s_v Y / q): checked on constructed coefficients whose
+    orthonormal value is an exact half-integer multiple of q (ties away from
+    zero) and against the class of each (u, v) (d_u d_v / 16)."""
+    d = np.array([1, 1, 2, 2 ** 0.5, 2 ** 0.5, 1, 2, 2, 1, 2, 2, 2 ** 0.5, 2 ** 0.5, 2, 2, 2])
+    Y = np.zeros((1, 16, 16), dtype=np.int64)
+    Y[0, 0, 0] = 40   # c = 40/16 = 2.5 -> q=1 -> 3
+    Y[0, 0, 2] = -20  # c = -20*2/16 = -2.5 -> -3
+    Y[0, 2, 6] = 9    # c = 9*4/16 = 2.25 -> 2
+    Y[0, 3, 4] = 8    # c = 8*2/16 = 1 -> 1
+    Y[0, 3, 0] = 16   # c = 16*sqrt2/16 = 1.414 -> 1
+    for prec in ("fp64", "fp32"):
+        L = o.quantise(Y, 1.0, 256, prec)[0]
+        assert (L[0, 0], L[0, 2], L[2, 6], L[3, 4], L[3, 0]) == (3, -3, 2, 1, 1), prec
+    c = np.outer(d, d) / 16.0
+    np.testing.assert_allclose(np.outer(o.S_DIAG, o.S_DIAG), c, rtol=1e-15)
+
+
+def check_fp32_decisions_only_differ_at_near_ties(o):
+    img = synth.ar1_image(21, 128, 128, 0.95).astype(np.int64)
+    X = o.image_to_blocks(img)
+    Y = o.forward_direct(X)
+    for q, r in ((16.0, 64), (8.0, 16), (32.0, 256), (5.3, 100)):
+        L64 = o.quantise(Y, q, r, "fp64")
+        L32 = o.quantise(Y, q, r, "fp32")
+        c = np.outer(o.S_DIAG, o.S_DIAG) * Y / q
+        diff = L64 != L32
+        assert np.all(np.abs(L64 - L32) <= 1)
+        assert np.all(np.abs(np.abs(c[diff]) - np.floor(np.abs(c[diff])) - 0.5) < 1e-5)
+        X64 = o.inverse_fp64(o.dequantise(L32, q))
+        X32 = o.inverse_fp32(L32, q).astype(np.float64)
+        # Higham-style bound for at most ~34 rounded operations along any path
+        Wabs = np.abs(o.dequantise(L32, q))
+        Ta = np.abs(o.T).astype(np.float64)
+        bound = 40 * 2.0 ** -24 * np.matmul(np.matmul(Ta.T, Wabs), Ta) + 1e-12
+        assert np.all(np.abs(X64 - X32) <= bound)
+        p64 = o.pixels_from_float(X64, 8)
+        p32 = o.pixels_from_float(X32, 8)
+        bad = p64 != p32
+        assert np.all(np.abs(p64 - p32) <= 1)
+        assert np.all(np.abs(np.abs(X64[bad]) % 1.0 - 0.5) <= bound[bad])
+
+
+def check_rounding(o):
+    x = np.array([0.5, -0.5, 1.5, -1.5, 2.5, -2.5, 0.49999997, -0.49999997, 3.7, -3.7])
+    assert list(o.round_half_away(x)) == [1, -1, 2, -2, 3, -3, 0, 0, 4, -4]
+    x32 = np.float32(0.49999997)
+    assert o.round_half_away(np.array([x32]))[0] == 0.0
+
+
+def check_psnr_closed_forms(o):
+    assert o.psnr(0, 16, 16, 8) == math.inf
+    # an error of exactly 1 at every pixel: PSNR = 20 log10(peak)
+    assert o.psnr(512 * 512, 512, 512, 8) == pytest.approx(20 * math.log10(255), abs=1e-12)
+    assert o.psnr(64 * 32, 32, 64, 10) == pytest.approx(20 * math.log10(1023), abs=1e-12)
+    # error 4 everywhere: 12.04 dB lower
+    assert o.psnr(16 * 256, 16, 16, 8) == pytest.approx(20 * math.log10(255 / 4), abs=1e-12)
+    a = np.array([[0, 10], [255, 7]])
+    b = np.array([[3, 10], [250, 9]])
+    assert o.sse(a, b) == 9 + 25 + 4
+
+
+ALL_CHECKS = [v for k, v in sorted(globals().items()) if k.startswith("check_")]
+
+
+@pytest.mark.parametrize("check", ALL_CHECKS, ids=[c.__name__ for c in ALL_CHECKS])
+def test_oracle_pin(check):
+    check(O)
+
+
+def test_permutation_convention_is_the_only_one():
+    """Of the four ways to read the cyclic notation (positions or values,
+    sigma or its inverse) only the oracle's reproduces T."""
+    F = O.factor_matrices()
+    ok = 0
+    for transpose_p1 in (False, True):
+        for transpose_p2 in (False, True):
+            P1 = F["P1"].T if transpose_p1 else F["P1"]
+            P2 = F["P2"].T if transpose_p2 else F["P2"]
+            prod = P2 @ F["M4"] @ F["M3"] @ F["M2"] @ P1 @ F["M1"]
+            ok += int(np.array_equal(prod, O.T))
+            if np.array_equal(prod, O.T):
+                assert not transpose_p1 and not transpose_p2
+    assert ok == 1
+
+
+def test_quantiser_constants_are_far_from_binary32_midpoints():
+    """f = fl32(s_u s_v / q) and g = fl32(q s_u s_v) are computed independently
+    on the GPU host side; they agree only if no double value lies within a few
+    double ulps of a binary32 rounding midpoint.  Check the step sizes used."""
+    ss = np.unique(np.outer(O.S_DIAG, O.S_DIAG))
+    for q in (1.0, 2.0, 5.3, 8.0, 10.0, 16.0, 32.0, 2.0 ** -8, 2.0 ** -12, 1e9):
+        for x in np.concatenate([ss / q, ss * q]):
+            f = np.float32(x)
+            ulp32 = np.spacing(f)
+            frac = abs(float(x) - float(f)) / float(ulp32)
+            assert abs(frac - 0.5) > 1e-6, (q, x)
