@@ -1,0 +1,446 @@
+"""Throughput benchmark of the fused 16x16 block codec (libtx16) on GB300.
+
+Workload (one step): 256 frames of 1920 x 1088 uint8 luma -- one AR(1)
+field (rho 0.95) cropped along a 2-pixel random walk, a stand-in for video --
+through the fused forward transform, S-scaled quantiser (q = 16, zonal r = 16),
+inverse, reconstruction and per-frame squared-error reduction: 2,088,960
+16x16 blocks, one kernel launch.  Inputs (535 MB) and outputs (535 MB) are
+larger than the 129 MB L2, so every step streams from HBM.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mblocks/s & % of HBM roofline (fused fwd+quant+inv); serving p50/p99 latency"
+UNIT = "Mblocks/s"
+FRAMES, H, W = 256, 1088, 1920
+BLOCKS_PER_FRAME = (H // 16) * (W // 16)
+BYTES_PER_BLOCK_CODEC = 512    # 256 B samples in + 256 B reconstructed samples out
+BYTES_PER_BLOCK_FORWARD = 1280  # 256 B samples in + 1024 B int32 coefficients out
+SEED = 2016
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def _workload(q, r):
+    return {"workload": f"{FRAMES} frames {W}x{H} uint8 AR(1) rho=0.95 with 2-px random-walk translation; "
+                        f"fused forward+quantise(q={q:g},r={r})+inverse+SSE",
+            "frames": FRAMES, "width": W, "height": H, "q": q, "r": r,
+            "blocks_per_step": FRAMES * BLOCKS_PER_FRAME,
+            "l2": "inputs larger than L2 (535 MB in + 535 MB out per step)"}
+
+
+# ---------------------------------------------------------------------------
+# Clocks sampled with nvidia-smi while the GPU is busy
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) == 7:
+                try:
+                    rows.append((float(p[0]), float(p[1]), float(p[2]), p[3:]))
+                except ValueError:
+                    pass
+        loaded = [r for r in rows if r[2] >= 50.0] or rows
+        if not loaded:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in loaded),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def _events_time(fn, steps, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps  # ms per step
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1606_07414_gb300 import synth, tx16
+
+    rank, local_rank, world = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    lib = tx16.load()
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    frames = synth.video_frames(SEED + rank, FRAMES, H, W, rho=0.95)
+    h_in = torch.from_numpy(frames).pin_memory()
+    d_in = h_in.to("cuda", non_blocking=False)
+    d_out = torch.empty_like(d_in)
+    d_sse = torch.zeros(FRAMES, dtype=torch.int64, device="cuda")
+    ins = (tx16.tx16_image * FRAMES)(*[tx16.image(d_in[i]) for i in range(FRAMES)])
+    outs = (tx16.tx16_image * FRAMES)(*[tx16.image(d_out[i]) for i in range(FRAMES)])
+
+    def qparams(q, r):
+        return (tx16.tx16_qparams * FRAMES)(*[tx16.tx16_qparams(q, r)] * FRAMES)
+
+    qp = qparams(args.q, args.r)
+    sse_ptr = ctypes.c_void_p(d_sse.data_ptr())
+
+    def step():
+        st = lib.tx16_codec_batch(ins, outs, FRAMES, qp, sse_ptr, None, sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_codec_batch")
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = _events_time(step, args.steps, stream)
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    blocks = FRAMES * BLOCKS_PER_FRAME
+    value = world * blocks / (ms * 1e-3) / 1e6
+
+    # Per-frame PSNR of the last step (reported, from the library's host helper)
+    sse_host = d_sse.cpu().tolist()
+    psnr = tx16.tx16_psnr(sse_host, [ins[0]] * FRAMES)
+    mean_psnr = float(np.mean(psnr))
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, sptr, stream, qparams)
+    clocks = sampler.stop() if sampler else None
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    peak = _measured_peak()
+    achieved = blocks * BYTES_PER_BLOCK_CODEC / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic", "config": _workload(args.q, args.r),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak["value"], "unit": "GB/s",
+                     "frac": round(achieved / peak["value"], 4), "traffic": _traffic_per_launch(),
+                     "peak_source": peak["source"], "kernel": "tx16::block_kernel<uint8_t,256,codec>",
+                     "algorithmic_bytes_per_launch": blocks * BYTES_PER_BLOCK_CODEC},
+        "gpu_launches": args.steps,
+        "mean_psnr_db": round(mean_psnr, 4),
+    }
+    line.update(extra)
+    line["clocks"] = clocks
+    print(json.dumps(line), flush=True)
+
+
+def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, sptr, stream, qparams):
+    out = {}
+    blocks = FRAMES * BLOCKS_PER_FRAME
+    peak = _measured_peak()["value"]
+
+    # -- end to end through the public API: pinned host frames in, host
+    #    reconstruction and per-frame SSE out, copies inside the timed region.
+    h_out = torch.empty_like(h_in).pin_memory()
+    h_sse = torch.empty(FRAMES, dtype=torch.int64).pin_memory()
+    qp = qparams(args.q, args.r)
+    chunk = 32
+    copy_in = torch.cuda.Stream()
+    copy_out = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(FRAMES // chunk)]
+    ev_k = [torch.cuda.Event() for _ in range(FRAMES // chunk)]
+    sse_ptr = d_sse.data_ptr()
+
+    def e2e_step():
+        # chunked pipeline: H2D of chunk i+1 and D2H of chunk i-1 overlap the
+        # kernel on chunk i (separate copy engines, full-duplex link)
+        for c in range(FRAMES // chunk):
+            s = slice(c * chunk, (c + 1) * chunk)
+            with torch.cuda.stream(copy_in):
+                d_in[s].copy_(h_in[s], non_blocking=True)
+                ev_in[c].record(copy_in)
+            stream.wait_event(ev_in[c])
+            st = lib.tx16_codec_batch(ctypes.byref(ins, c * chunk * ctypes.sizeof(tx16.tx16_image)),
+                                      ctypes.byref(outs, c * chunk * ctypes.sizeof(tx16.tx16_image)), chunk,
+                                      qp, ctypes.c_void_p(sse_ptr + 8 * c * chunk), None, sptr)
+            if st != 0:
+                raise tx16.Tx16Error(st, "tx16_codec_batch")
+            ev_k[c].record(stream)
+            with torch.cuda.stream(copy_out):
+                copy_out.wait_event(ev_k[c])
+                h_out[s].copy_(d_out[s], non_blocking=True)
+        copy_out.wait_stream(stream)
+        with torch.cuda.stream(copy_out):
+            h_sse.copy_(d_sse, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    n_e2e = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    out["e2e"] = {"value": round(blocks / (e2e_ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                  "h2d_bytes_per_step": h_in.numel(), "d2h_bytes_per_step": h_out.numel() + 8 * FRAMES,
+                  "ms_per_step": round(e2e_ms, 4), "pipeline": f"{FRAMES // chunk} chunks of {chunk} frames, "
+                                                               "copy streams overlapping the kernel"}
+
+    # -- q x r sweep of the fused kernel (the workload's full parameter grid)
+    sweep = []
+    for q in (8.0, 16.0, 32.0):
+        for r in (4, 16, 64, 256):
+            qpx = qparams(q, r)
+
+            def f():
+                lib.tx16_codec_batch(ins, outs, FRAMES, qpx, ctypes.c_void_p(sse_ptr), None, sptr)
+            for _ in range(3):
+                f()
+            ms = _events_time(f, 10, stream)
+            gbs = blocks * BYTES_PER_BLOCK_CODEC / (ms * 1e-3) / 1e9
+            sweep.append({"q": q, "r": r, "Mblocks_s": round(blocks / (ms * 1e-3) / 1e6, 1),
+                          "GB_s": round(gbs, 1), "frac": round(gbs / peak, 4)})
+    out["sweep"] = sweep
+
+    # -- the unfused ("plain") form: per-frame forward, quantise, inverse and
+    #    SSE launches through int32 coefficients in HBM
+    nbf = BLOCKS_PER_FRAME
+    coeffs = torch.empty(FRAMES * nbf * 256, dtype=torch.int32, device="cuda")
+    one_qp = qparams(args.q, args.r)
+    qsingle = tx16.tx16_qparams(args.q, args.r)
+
+    def plain():
+        for i in range(FRAMES):
+            cp = ctypes.c_void_p(coeffs.data_ptr() + i * nbf * 1024)
+            a = ctypes.byref(ins, i * ctypes.sizeof(tx16.tx16_image))
+            b = ctypes.byref(outs, i * ctypes.sizeof(tx16.tx16_image))
+            lib.tx16_forward(a, 1, cp, sptr)
+            lib.tx16_quantise(cp, nbf, qsingle, cp, sptr)
+            lib.tx16_inverse(cp, b, 1, one_qp, sptr)
+            lib.tx16_sse(a, b, 1, ctypes.c_void_p(sse_ptr + 8 * i), sptr)
+    plain()
+    ms_plain = _events_time(plain, 3, stream)
+    out["plain_form"] = {"value": round(blocks / (ms_plain * 1e-3) / 1e6, 2), "unit": UNIT,
+                         "ms_per_step": round(ms_plain, 4), "launches_per_step": 4 * FRAMES}
+
+    # -- forward only to int32 coefficients (64 images of 2048 x 2048):
+    #    one batched launch vs one launch per image
+    del coeffs
+    n2, s2 = 64, 2048
+    nb2 = (s2 // 16) ** 2
+    base = torch.from_numpy(np.ascontiguousarray(d_in[:2].cpu().numpy()[:, :1024, :1024])).cuda()
+    imgs2 = torch.empty((n2, s2, s2), dtype=torch.uint8, device="cuda")
+    for i in range(n2):  # tile crops of the frames: the transform's cost is data independent
+        imgs2[i] = base[i % 2].repeat(2, 2)
+    co2 = torch.empty(n2 * nb2 * 256, dtype=torch.int32, device="cuda")
+    d2 = (tx16.tx16_image * n2)(*[tx16.image(imgs2[i]) for i in range(n2)])
+    cptr = ctypes.c_void_p(co2.data_ptr())
+
+    def fwd_batched():
+        lib.tx16_forward(d2, n2, cptr, sptr)
+
+    def fwd_per_image():
+        for i in range(n2):
+            lib.tx16_forward(ctypes.byref(d2, i * ctypes.sizeof(tx16.tx16_image)), 1,
+                             ctypes.c_void_p(co2.data_ptr() + i * nb2 * 1024), sptr)
+    for f in (fwd_batched, fwd_per_image):
+        for _ in range(3):
+            f()
+    ms_b = _events_time(fwd_batched, 10, stream)
+    ms_p = _events_time(fwd_per_image, 10, stream)
+    gb = n2 * nb2 * BYTES_PER_BLOCK_FORWARD / 1e9
+    out["forward_only"] = {"workload": "64 images 2048x2048 uint8 -> int32 coefficients",
+                           "batched": {"Mblocks_s": round(n2 * nb2 / (ms_b * 1e-3) / 1e6, 1),
+                                       "GB_s": round(gb / (ms_b * 1e-3), 1),
+                                       "frac": round(gb / (ms_b * 1e-3) / peak, 4)},
+                           "per_image_launches": {"Mblocks_s": round(n2 * nb2 / (ms_p * 1e-3) / 1e6, 1),
+                                                  "GB_s": round(gb / (ms_p * 1e-3), 1)}}
+    del co2, imgs2
+
+    # -- CPU baseline: the oracle on a bounded sample, all host cores
+    if not args.no_cpu:
+        frames_np = h_in[: args.cpu_frames].numpy()
+        out["cpu_baseline"] = cpu_oracle_rate(frames_np, args.q, args.r)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------
+def _oracle_frame(job):
+    frame, q, r = job
+    from oracle import tx16_oracle as O
+
+    O.codec_image(frame, q, r, 8, "fp64")
+    return frame.shape
+
+
+def cpu_oracle_rate(frames_np, q, r, pool=None, cores=None):
+    import multiprocessing as mp
+
+    cores = cores or os.cpu_count() or 1
+    own = pool is None
+    if own:
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        pool = mp.get_context("spawn").Pool(cores)
+        pool.map(_oracle_frame, [(frames_np[0][:16, :16], q, r)] * cores)  # warm the workers
+    t0 = time.perf_counter()
+    pool.map(_oracle_frame, [(f, q, r) for f in frames_np], chunksize=1)
+    dt = time.perf_counter() - t0
+    if own:
+        pool.close()
+        pool.join()
+    nblk = len(frames_np) * (frames_np.shape[1] // 16) * (frames_np.shape[2] // 16)
+    return {"value": round(nblk / dt / 1e6, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(frames_np)} of the {FRAMES} frames (float64 oracle codec_image, one frame per "
+                      f"task, {cores} single-threaded processes), {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    import numpy as np
+    import multiprocessing as mp
+
+    from paper_1606_07414_gb300 import synth
+
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return
+    frames = synth.video_frames(SEED, args.cpu_frames, H, W, rho=0.95)
+    cores = os.cpu_count() or 1
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    pool = mp.get_context("spawn").Pool(cores)
+    pool.map(_oracle_frame, [(frames[0][:16, :16], args.q, args.r)] * cores)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(frames[:1], args.q, args.r, pool, cores)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rates.append(cpu_oracle_rate(frames, args.q, args.r, pool, cores))
+    dt = time.perf_counter() - t0
+    pool.close()
+    pool.join()
+    nblk = args.steps * len(frames) * BLOCKS_PER_FRAME
+    value = nblk / dt / 1e6
+    line = {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64", "data": "synthetic",
+            "config": _workload(args.q, args.r), "impl": "reference",
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {len(frames)} frames of the workload through the float64 "
+                                       f"oracle on {cores} single-threaded processes"},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return {"value": float(json.load(f)["hbm_gbs"]), "source": "measured (copy, MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"value": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def _traffic_per_launch():
+    """DRAM bytes per launch of the codec kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "codec_traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for fn in rec.get("sources", []):
+        with open(os.path.join(ROOT, fn), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("sha256"):
+        return None
+    scale = (FRAMES * BLOCKS_PER_FRAME) / rec["blocks"]
+    return int(rec["dram_bytes"] * scale)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="tx16", choices=["tx16", "reference"])
+    ap.add_argument("--q", type=float, default=16.0)
+    ap.add_argument("--r", type=int, default=16)
+    ap.add_argument("--cpu-frames", type=int, default=32)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline number only")
+    ap.add_argument("--frames", type=int, default=FRAMES, help="smaller cases for profiling")
+    args = ap.parse_args()
+    globals()["FRAMES"] = args.frames
+    if args.warmup < 3 and args.impl == "tx16":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * libtx16 -- GB300 (sm_103a) implementation of the orthogonal 16-point DCT
+ * approximation of Cintra, Bayer, Oliveira et al., "Multiplierless 16-point
+ * DCT approximation for low-complexity image and video coding".
+ *
+ * Notation (the paper's):
+ *   T        16x16 matrix with entries in {0, +1, -1}                (Sec. 2.1)
+ *   S        (1/4) diag(1,1,2,r2,r2,1,2,2,1,2,2,r2,r2,2,2,2), r2 = sqrt 2
+ *            = sqrt((T T^t)^-1)                                      (Sec. 2.1)
+ *   C_hat    S T, orthogonal                                         (Sec. 2.1)
+ *   X        one 16x16 block of samples; row index i is vertical
+ *   Y        T X T^t, exact integers; Y[u][v], u vertical frequency (Sec. 3.1)
+ *   Z_r      the first r cells of the zig-zag scan of a 16x16 block,
+ *            JPEG convention extended to 16x16                       (Sec. 3.1)
+ *
+ * Every transform runs through the 44-addition factorisation
+ * T = P2 M4 M3 M2 P1 M1 (Sec. 2.2) in exact int32; S is merged into the
+ * quantiser (Sec. 2.1, last paragraph), so the only floating point on the
+ * device is one binary32 multiply per kept coefficient each way and the
+ * binary32 inverse network.
+ *
+ * Conventions for every call below:
+ *   - Pointers named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  Arrays of descriptors (tx16_image,
+ *     tx16_qparams) are HOST arrays, read before the call returns.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream).  Argument errors are returned synchronously and nothing
+ *     is launched.  A CUDA launch error returns TX16_ECUDA.
+ *   - Coefficient / level layout ("block-major"): the blocks of image 0 in
+ *     raster block order, then those of image 1, ...; block b occupies int32
+ *     elements [256 b, 256 b + 256), row-major Y[u][v] at 256 b + 16 u + v.
+ *   - Images: width and height are positive multiples of 16 (the paper splits
+ *     images into disjoint 16x16 blocks, Sec. 3.1); pitch_bytes is a multiple
+ *     of 16 and at least width * sample size; data is 16-byte aligned.
+ *     bits = 8 means uint8 samples, 9..12 means uint16 samples.
+ */
+#ifndef TX16_H
+#define TX16_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TX16_OK = 0,
+  TX16_EINVAL = 1,   /* bad argument; nothing launched */
+  TX16_ENOMEM = 2,   /* device or host allocation failed / admission refused */
+  TX16_ECUDA = 3,    /* a CUDA runtime call or launch failed */
+  TX16_ETIMEOUT = 4, /* a bounded wait ran out */
+  TX16_EBUSY = 5     /* no free slot */
+} tx16_status;
+
+/* One image plane.  `data` is a device pointer: read by calls that take the
+ * image as input, written by calls that take it as output. */
+typedef struct {
+  void* data;
+  int32_t width;
+  int32_t height;
+  int64_t pitch_bytes;
+  int32_t bits;
+} tx16_image;
+
+/* Quantiser of one image (Sec. 3.1 zonal coding; Sec. 2.1 S merged into the
+ * quantiser).  r in 1..256 keeps Z_r.  q > 0: uniform step q on the
+ * orthonormal coefficient c = s_u s_v Y[u][v], level = round_half_away(c / q)
+ * taken in binary32 as round(fl32(Y) * f), f = fl32(s_u s_v / q).
+ * q <= 0: no uniform quantiser (the paper's image experiment): the "level"
+ * of a kept coefficient is Y[u][v] itself and the inverse is exact. */
+typedef struct {
+  float q;
+  int32_t r;
+} tx16_qparams;
+
+/* Human-readable name of a status code (static storage). */
+const char* tx16_status_str(tx16_status s);
+
+/* Number of 16x16 blocks of an image (width/16 * height/16), or -1 if the
+ * descriptor is invalid. */
+int64_t tx16_image_blocks(const tx16_image* img);
+
+/*
+ * Forward 2-D transform Y = T X T^t of every block of n images (Sec. 3.1
+ * forward transform with C = T; Sec. 2.2 fast algorithm: 16 row transforms,
+ * then 16 column transforms, 44 additions each).
+ *   imgs    host array of n input descriptors
+ *   coeffs  device int32 array of 256 * sum(blocks) elements, block-major
+ * Exact: |Y| <= 256 (2^bits - 1).
+ */
+tx16_status tx16_forward(const tx16_image* imgs, int32_t n, int32_t* coeffs, void* stream);
+
+/*
+ * Zonal / uniform quantisation of nblk coefficient blocks with one quantiser
+ * (Sec. 3.1 zonal mask; Sec. 2.1 S merged into the quantiser).
+ *   coeffs  device int32, 256 * nblk, block-major (as written by tx16_forward)
+ *   levels  device int32, 256 * nblk: level inside Z_r, 0 outside
+ *           (q <= 0: Y[u][v] inside Z_r, 0 outside).  May equal coeffs.
+ */
+tx16_status tx16_quantise(const int32_t* coeffs, int64_t nblk, tx16_qparams qp,
+                          int32_t* levels, void* stream);
+
+/*
+ * Inverse 2-D transform and reconstruction (Sec. 3.1: A_tilde = C_hat^t
+ * B_tilde C_hat, blocks rearranged into the image).
+ *   levels  device int32, block-major, for the n images of `out` in order;
+ *           only the cells inside each image's Z_r are read.
+ *   out     host array of n output descriptors (device sample buffers written)
+ *   qp      host array of n quantisers (q and r of each image)
+ * q > 0:  W = fl32(level * fl32(q s_u s_v)); X_tilde = T^t W T in binary32
+ *         through the transposed factorisation, columns first.
+ * q <= 0: 256 X_tilde = T^t (D' Y D') T exactly, D' = 16 S^2.
+ * Sample = clip(round_half_away(X_tilde), 0, 2^bits - 1).
+ */
+tx16_status tx16_inverse(const int32_t* levels, const tx16_image* out, int32_t n,
+                         const tx16_qparams* qp, void* stream);
+
+/*
+ * Fused codec: forward, quantise, inverse, reconstruction and squared-error
+ * reduction of every block in one launch (Sec. 3.1 procedure; PSNR of
+ * Sec. 3.1 from the returned SSE, see tx16_psnr).
+ *   in      host array of n input descriptors
+ *   out     host array of n output descriptors, or NULL (no samples written)
+ *   qp      host array of n quantisers
+ *   sse     device uint64[n] or NULL: sse[i] = sum (x - x_tilde)^2 over image
+ *           i; zeroed by the call itself before accumulation
+ *   levels  device int32, block-major, or NULL (levels not written)
+ * Results are identical to tx16_forward + tx16_quantise + tx16_inverse.
+ */
+tx16_status tx16_codec_batch(const tx16_image* in, const tx16_image* out, int32_t n,
+                             const tx16_qparams* qp, uint64_t* sse, int32_t* levels,
+                             void* stream);
+
+/*
+ * Squared error between two sets of n images of equal shape (the separate
+ * PSNR reduction of the unfused form).  sse: device uint64[n], zeroed by the
+ * call before accumulation.
+ */
+tx16_status tx16_sse(const tx16_image* a, const tx16_image* b, int32_t n, uint64_t* sse,
+                     void* stream);
+
+/*
+ * PSNR from squared error (host arithmetic, float64):
+ * 10 log10((2^bits - 1)^2 W H / SSE), +inf for SSE = 0.
+ *   sse   host array of n values; imgs: host descriptors (shape and bits);
+ *   psnr  host array of n results.
+ */
+tx16_status tx16_psnr(const uint64_t* sse, const tx16_image* imgs, int32_t n, double* psnr);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TX16_H */

@@ -1,0 +1,64 @@
+// Internal types shared by the libtx16 translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tx16.h"
+
+namespace tx16 {
+
+constexpr int kTileBlocks = 16;            // 16x16 blocks per CTA iteration
+constexpr int kThreads = 16 * kTileBlocks;  // one thread per block row
+constexpr int kQuantFlag = 1 << 8;          // ImgParam::flags: q > 0
+
+// Everything a kernel needs to know about one image, passed by value in the
+// launch parameters (no device-side descriptor table, no allocation).
+struct ImgParam {
+  const void* src;     // samples read (forward / codec) -- device
+  void* dst;           // samples written (codec / inverse) or nullptr -- device
+  int64_t src_pitch;   // bytes
+  int64_t dst_pitch;   // bytes
+  int64_t blk0;        // index of the image's first block in the coefficient buffer
+  int32_t nbx;         // blocks per block row (width / 16)
+  int32_t nblk;        // blocks in the image
+  int32_t tile0;       // first tile of this image within the launch
+  int32_t flags;       // bits (low 8) | kQuantFlag
+  float f[5];          // fl32(sqrt2^k / (16 q)), k = e(u) + e(v)   (forward scale)
+  float g[5];          // fl32(q sqrt2^k / 16)                      (inverse scale)
+  uint8_t colh[16];    // kept rows of column v: |Z_r ∩ column v| (a prefix 0..colh-1)
+};
+
+template <int MAXI>
+struct BatchParams {
+  int32_t nimg;
+  int32_t ntiles;
+  unsigned long long* sse;  // per image of this launch (already offset), or nullptr
+  int32_t* coeffs;          // forward: output; inverse: input; codec: levels or nullptr
+  ImgParam img[MAXI];
+};
+
+// Largest per-launch image count; sizeof(BatchParams<kMaxImg>) must stay under
+// the 32 KB kernel-parameter limit.
+constexpr int kMaxImg = 256;
+static_assert(sizeof(BatchParams<kMaxImg>) < 32000, "kernel parameters too large");
+
+enum Op { kOpForward = 0, kOpCodec = 1, kOpInverse = 2, kOpSse = 3 };
+
+// Host helpers (tx16_host.cpp)
+bool valid_image(const tx16_image& im);
+int sample_bytes(int bits);
+void zonal_column_heights(int r, uint8_t colh[16]);
+void quant_constants(float q, float f[5], float g[5]);
+
+// Launchers (tx16_codec.cu).  `imgs` points at `n` ImgParam already filled in
+// (except tile0, set here), all with the same sample size.
+tx16_status launch_blocks(Op op, int sample_bytes, ImgParam* imgs, int n,
+                          unsigned long long* sse, int32_t* coeffs, cudaStream_t stream);
+tx16_status launch_quantise(const int32_t* coeffs, int64_t nblk, const ImgParam& qp,
+                            int32_t* levels, cudaStream_t stream);
+
+int device_sm_count();
+
+}  // namespace tx16

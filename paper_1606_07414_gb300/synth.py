@@ -67,7 +67,7 @@ def ar1_field(seed: int, H: int, W: int, rho: float) -> np.ndarray:
     """A separable AR(1) Gaussian field, unit variance, correlation
     rho^|di| rho^|dj|: filtered along rows, then along columns."""
     z = normals(seed, H * W).reshape(H, W)
-    return _ar1_along(_ar1_along(z, rho, axis=1), rho, axis=0)
+    return np.ascontiguousarray(_ar1_along(_ar1_along(z, rho, axis=1), rho, axis=0))
 
 
 def to_samples(field: np.ndarray, bits: int, mean: float | None = None,
@@ -82,7 +82,7 @@ def to_samples(field: np.ndarray, bits: int, mean: float | None = None,
     v = mean + std * field
     v = np.sign(v) * np.floor(np.abs(v) + 0.5)
     v = np.clip(v, 0, (1 << bits) - 1)
-    return v.astype(np.uint8 if bits == 8 else np.uint16)
+    return np.ascontiguousarray(v.astype(np.uint8 if bits == 8 else np.uint16))
 
 
 def ar1_image(seed: int, H: int, W: int, rho: float = 0.95, bits: int = 8) -> np.ndarray:

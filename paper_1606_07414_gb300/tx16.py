@@ -1,0 +1,181 @@
+"""ctypes binding of libtx16 (include/tx16.h): the same entry points, with
+argument marshalling from torch CUDA tensors only -- every step of the path
+runs in the library's kernels.
+
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libtx16.so")
+
+TX16_OK, TX16_EINVAL, TX16_ENOMEM, TX16_ECUDA, TX16_ETIMEOUT, TX16_EBUSY = range(6)
+
+
+class Tx16Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class tx16_image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("pitch_bytes", ctypes.c_int64), ("bits", ctypes.c_int32)]
+
+
+class tx16_qparams(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_float), ("r", ctypes.c_int32)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGNATURES = {
+    "tx16_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "tx16_image_blocks": (ctypes.c_int64, [ctypes.POINTER(tx16_image)]),
+    "tx16_forward": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
+    "tx16_quantise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, tx16_qparams, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    "tx16_inverse": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tx16_image), ctypes.c_int32,
+                                    ctypes.POINTER(tx16_qparams), ctypes.c_void_p]),
+    "tx16_codec_batch": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image),
+                                        ctypes.c_int32, ctypes.POINTER(tx16_qparams), ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "tx16_sse": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image), ctypes.c_int32,
+                                ctypes.c_void_p, ctypes.c_void_p]),
+    "tx16_psnr": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(tx16_image),
+                                 ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libtx16.so (built by ``paper_1606_07414_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtx16 is not built ({path} missing): run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_str(status: int) -> str:
+    try:
+        return load().tx16_status_str(status).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(status: int, what: str) -> None:
+    if status != TX16_OK:
+        raise Tx16Error(status, what)
+
+
+# ---------------------------------------------------------------------------
+# torch tensor -> descriptor marshalling
+# ---------------------------------------------------------------------------
+def image(t, bits: int | None = None) -> tx16_image:
+    """Descriptor of a 2-D CUDA tensor of samples (uint8 for 8 bits; uint16 or
+    int16 storage for 9..12 bits).  Rows may be padded (stride(0) >= width)."""
+    import torch
+
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("image tensors must be 2-D with unit column stride")
+    esz = t.element_size()
+    if bits is None:
+        bits = 8 if t.dtype == torch.uint8 else 10
+    if (bits == 8) != (esz == 1):
+        raise ValueError("8-bit images are uint8; 9..12-bit images use 16-bit storage")
+    return tx16_image(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0) * esz, bits)
+
+
+def _images(ts: Sequence, bits) -> ctypes.Array:
+    arr = (tx16_image * max(1, len(ts)))()
+    for i, t in enumerate(ts):
+        arr[i] = t if isinstance(t, tx16_image) else image(t, bits)
+    return arr
+
+
+def _qparams(qp: Sequence[tuple[float, int]]) -> ctypes.Array:
+    arr = (tx16_qparams * max(1, len(qp)))()
+    for i, (q, r) in enumerate(qp):
+        arr[i] = tx16_qparams(float(q) if q is not None else 0.0, int(r))
+    return arr
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# Entry points (names as in include/tx16.h)
+# ---------------------------------------------------------------------------
+def tx16_image_blocks(t, bits: int | None = None) -> int:
+    d = t if isinstance(t, tx16_image) else image(t, bits)
+    return int(load().tx16_image_blocks(ctypes.byref(d)))
+
+
+def tx16_forward(imgs: Sequence, coeffs, stream=None, bits: int | None = None) -> None:
+    """coeffs: int32 CUDA tensor with 256 * total_blocks elements."""
+    lib = load()
+    arr = _images(imgs, bits)
+    _check(lib.tx16_forward(arr, len(imgs), _ptr(coeffs), _stream(stream)), "tx16_forward")
+
+
+def tx16_quantise(coeffs, nblk: int, q: float | None, r: int, levels, stream=None) -> None:
+    lib = load()
+    qp = tx16_qparams(float(q) if q is not None else 0.0, int(r))
+    _check(lib.tx16_quantise(_ptr(coeffs), int(nblk), qp, _ptr(levels), _stream(stream)), "tx16_quantise")
+
+
+def tx16_inverse(levels, out: Sequence, qp: Sequence[tuple[float, int]], stream=None,
+                 bits: int | None = None) -> None:
+    lib = load()
+    _check(lib.tx16_inverse(_ptr(levels), _images(out, bits), len(out), _qparams(qp), _stream(stream)),
+           "tx16_inverse")
+
+
+def tx16_codec_batch(inp: Sequence, out: Sequence | None, qp: Sequence[tuple[float, int]], sse=None,
+                     levels=None, stream=None, bits: int | None = None) -> None:
+    """Fused codec.  sse: uint64/int64 CUDA tensor of len(inp) or None."""
+    lib = load()
+    out_arr = _images(out, bits) if out is not None else None
+    _check(lib.tx16_codec_batch(_images(inp, bits), out_arr, len(inp), _qparams(qp), _ptr(sse),
+                                _ptr(levels), _stream(stream)), "tx16_codec_batch")
+
+
+def tx16_sse(a: Sequence, b: Sequence, sse, stream=None, bits: int | None = None) -> None:
+    lib = load()
+    _check(lib.tx16_sse(_images(a, bits), _images(b, bits), len(a), _ptr(sse), _stream(stream)), "tx16_sse")
+
+
+def tx16_psnr(sse_values: Sequence[int], imgs: Sequence) -> list[float]:
+    """PSNR (host arithmetic in the library) from squared errors."""
+    lib = load()
+    n = len(sse_values)
+    s = (ctypes.c_uint64 * max(1, n))(*[int(v) for v in sse_values])
+    arr = (tx16_image * max(1, n))()
+    for i, d in enumerate(imgs):
+        arr[i] = d
+    out = (ctypes.c_double * max(1, n))()
+    _check(lib.tx16_psnr(s, arr, n, out), "tx16_psnr")
+    return [out[i] for i in range(n)]

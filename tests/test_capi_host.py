@@ -1,0 +1,108 @@
+"""CPU-only checks of the C-ABI library: it builds for sm_103a, loads, exports
+every entry point include/tx16.h declares, and its host-only logic (argument
+checking, block counts, PSNR) behaves -- no compute call needs a GPU here."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from oracle import tx16_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1606_07414_gb300 import build, tx16
+
+    build.build()
+    return tx16.load()
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tx16_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_symbols()
+    assert {"tx16_forward", "tx16_quantise", "tx16_inverse", "tx16_codec_batch"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    from paper_1606_07414_gb300 import tx16
+
+    assert tx16.status_str(0) == "ok"
+    assert tx16.status_str(1) == "invalid argument"
+    assert tx16.status_str(99) == "unknown status"
+
+
+def _img(w, h, pitch=None, bits=8, ptr=0x10000):
+    from paper_1606_07414_gb300 import tx16
+
+    esz = 1 if bits == 8 else 2
+    return tx16.tx16_image(ptr, w, h, pitch if pitch is not None else w * esz, bits)
+
+
+def test_image_blocks_and_validation(lib):
+    f = lib.tx16_image_blocks
+    assert f(ctypes.byref(_img(512, 512))) == 1024
+    assert f(ctypes.byref(_img(1920, 1088))) == 8160
+    assert f(ctypes.byref(_img(3840, 2160, bits=10))) == 32400
+    for bad in (_img(500, 512), _img(512, 0), _img(32, 32, pitch=40), _img(32, 32, pitch=16),
+                _img(32, 32, bits=7), _img(32, 32, bits=13), _img(32, 32, ptr=0x10008),
+                _img(32, 32, ptr=0), _img(32, 32, bits=10, pitch=48)):
+        assert f(ctypes.byref(bad)) == -1
+
+
+def test_argument_errors_launch_nothing(lib):
+    """Invalid arguments return TX16_EINVAL before touching CUDA (so this runs
+    without a GPU)."""
+    from paper_1606_07414_gb300 import tx16
+
+    good = (tx16.tx16_image * 1)(_img(32, 32))
+    bad = (tx16.tx16_image * 1)(_img(30, 32))
+    qp = (tx16.tx16_qparams * 1)(tx16.tx16_qparams(8.0, 16))
+    qbad = (tx16.tx16_qparams * 1)(tx16.tx16_qparams(8.0, 0))
+    qbad2 = (tx16.tx16_qparams * 1)(tx16.tx16_qparams(8.0, 257))
+    qnan = (tx16.tx16_qparams * 1)(tx16.tx16_qparams(float("nan"), 16))
+    dev = ctypes.c_void_p(0x20000)
+    E = tx16.TX16_EINVAL
+    assert lib.tx16_forward(bad, 1, dev, None) == E
+    assert lib.tx16_forward(good, -1, dev, None) == E
+    assert lib.tx16_forward(good, 1, None, None) == E
+    assert lib.tx16_forward(good, 1, ctypes.c_void_p(0x20004), None) == E
+    assert lib.tx16_codec_batch(good, None, 1, qbad, None, None, None) == E
+    assert lib.tx16_codec_batch(good, None, 1, qbad2, None, None, None) == E
+    assert lib.tx16_codec_batch(good, None, 1, qnan, None, None, None) == E
+    assert lib.tx16_codec_batch(bad, None, 1, qp, None, None, None) == E
+    other = (tx16.tx16_image * 1)(_img(48, 32))
+    assert lib.tx16_codec_batch(good, other, 1, qp, None, None, None) == E
+    assert lib.tx16_inverse(dev, bad, 1, qp, None) == E
+    assert lib.tx16_inverse(dev, good, 1, qbad, None) == E
+    assert lib.tx16_sse(good, other, 1, dev, None) == E
+    assert lib.tx16_quantise(dev, 4, tx16.tx16_qparams(8.0, 0), dev, None) == E
+    assert lib.tx16_quantise(dev, -1, tx16.tx16_qparams(8.0, 4), dev, None) == E
+    # empty batches are valid no-ops
+    assert lib.tx16_forward(good, 0, dev, None) == tx16.TX16_OK
+    assert lib.tx16_quantise(dev, 0, tx16.tx16_qparams(8.0, 4), dev, None) == tx16.TX16_OK
+
+
+def test_psnr_matches_oracle(lib):
+    from paper_1606_07414_gb300 import tx16
+
+    imgs = [_img(512, 512), _img(64, 32, bits=10), _img(16, 16)]
+    sse = [123456, 2048, 0]
+    got = tx16.tx16_psnr(sse, imgs)
+    want = [O.psnr(123456, 512, 512, 8), O.psnr(2048, 32, 64, 10), math.inf]
+    for g, w in zip(got, want):
+        assert g == pytest.approx(w, rel=1e-15) if math.isfinite(w) else g == w
