@@ -94,6 +94,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def _at(arr, i):
+    """Pointer to element i of a ctypes array of descriptors."""
+    t = arr._type_
+    return ctypes.cast(ctypes.addressof(arr) + i * ctypes.sizeof(t), ctypes.POINTER(t))
+
+
 def _events_time(fn, steps, stream):
     import torch
 
@@ -216,8 +222,7 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                 d_in[s].copy_(h_in[s], non_blocking=True)
                 ev_in[c].record(copy_in)
             stream.wait_event(ev_in[c])
-            st = lib.tx16_codec_batch(ctypes.byref(ins, c * chunk * ctypes.sizeof(tx16.tx16_image)),
-                                      ctypes.byref(outs, c * chunk * ctypes.sizeof(tx16.tx16_image)), chunk,
+            st = lib.tx16_codec_batch(_at(ins, c * chunk), _at(outs, c * chunk), chunk,
                                       qp, ctypes.c_void_p(sse_ptr + 8 * c * chunk), None, sptr)
             if st != 0:
                 raise tx16.Tx16Error(st, "tx16_codec_batch")
@@ -268,8 +273,8 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
     def plain():
         for i in range(FRAMES):
             cp = ctypes.c_void_p(coeffs.data_ptr() + i * nbf * 1024)
-            a = ctypes.byref(ins, i * ctypes.sizeof(tx16.tx16_image))
-            b = ctypes.byref(outs, i * ctypes.sizeof(tx16.tx16_image))
+            a = _at(ins, i)
+            b = _at(outs, i)
             lib.tx16_forward(a, 1, cp, sptr)
             lib.tx16_quantise(cp, nbf, qsingle, cp, sptr)
             lib.tx16_inverse(cp, b, 1, one_qp, sptr)
@@ -297,7 +302,7 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
 
     def fwd_per_image():
         for i in range(n2):
-            lib.tx16_forward(ctypes.byref(d2, i * ctypes.sizeof(tx16.tx16_image)), 1,
+            lib.tx16_forward(_at(d2, i), 1,
                              ctypes.c_void_p(co2.data_ptr() + i * nb2 * 1024), sptr)
     for f in (fwd_batched, fwd_per_image):
         for _ in range(3):

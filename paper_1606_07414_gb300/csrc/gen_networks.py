@@ -1,0 +1,329 @@
+"""Generate tx16_pairnet.cuh: the 44-addition network of the 16-point
+approximation (T = P2 M4 M3 M2 P1 M1, Sec. 2.2 of the paper) as straight-line
+code on float2 pairs (two blocks at once, Blackwell packed-FP32 builtins).
+
+The generator does symbolically what a compiler cannot do through the packed
+builtins:
+  * negations (the -I blocks of M3/M4 and the butterflies' minus signs) are
+    folded into the adds: every value carries a compile-time sign, a + b is
+    emitted as add, sub (an fma by -1, one rounding) or add with the sign
+    flipped, so no instruction is spent on a negation;
+  * zonal pruning: inputs known to be zero are dropped and only the outputs
+    that are used are computed.
+
+Each emitted stage output is one IEEE operation on two stage inputs, exactly as
+in the factorisation, so binary32 results are those of the factorisation
+evaluated stage by stage.
+
+Run:  python gen_networks.py  (rewrites tx16_pairnet.cuh beside this file)
+"""
+from __future__ import annotations
+
+import os
+import random
+
+# --- the factorisation, 0-indexed (Sec. 2.2) ---------------------------------
+G1 = [0, 1, 2, 3, 4, 5, 6, 7, 8, 11, 12, 15, 14, 13, 10, 9]   # P1: b[i] = a[G1[i]]
+G2 = [0, 8, 7, 11, 3, 9, 5, 15, 1, 13, 6, 10, 2, 12, 4, 14]   # P2: y[i] = e[G2[i]]
+ZERO = None
+
+
+class Net:
+    """Symbolic DAG builder.  A value is ZERO or (node_id, sign)."""
+
+    def __init__(self):
+        self.nodes = []  # (kind, a_id, b_id) kind in add/sub ; leaves: ("in", name)
+
+    def leaf(self, name):
+        self.nodes.append(("in", name))
+        return (len(self.nodes) - 1, 1)
+
+    def _new(self, kind, a, b):
+        self.nodes.append((kind, a, b))
+        return len(self.nodes) - 1
+
+    def add(self, x, y):
+        if x is ZERO:
+            return y
+        if y is ZERO:
+            return x
+        (a, sa), (b, sb) = x, y
+        if sa == 1 and sb == 1:
+            return (self._new("add", a, b), 1)
+        if sa == 1 and sb == -1:
+            return (self._new("sub", a, b), 1)
+        if sa == -1 and sb == 1:
+            return (self._new("sub", b, a), 1)
+        return (self._new("add", a, b), -1)
+
+    def neg(self, x):
+        return ZERO if x is ZERO else (x[0], -x[1])
+
+    def sub(self, x, y):
+        return self.add(x, self.neg(y))
+
+    # -- stages --
+    def m1(self, x):
+        a = [None] * 16
+        for i in range(8):
+            a[i] = self.add(x[i], x[15 - i])
+            a[8 + i] = self.sub(x[7 - i], x[8 + i])
+        return a
+
+    def m2(self, b):
+        c = [None] * 16
+        for h in (0, 8):
+            for i in range(4):
+                c[h + i] = self.add(b[h + i], b[h + 7 - i])
+                c[h + 4 + i] = self.sub(b[h + 3 - i], b[h + 4 + i])
+        return c
+
+    def m3(self, c):
+        n = self.neg
+        return [self.add(c[0], c[3]), self.add(c[1], c[2]), self.sub(c[1], c[2]), self.sub(c[0], c[3]),
+                n(c[4]), n(c[5]), n(c[6]), n(c[7]),
+                self.add(c[8], c[11]), self.add(c[9], c[10]), self.sub(c[9], c[10]), self.sub(c[8], c[11]),
+                n(c[12]), n(c[13]), n(c[14]), n(c[15])]
+
+    def m4(self, d):
+        n = self.neg
+        return [self.add(d[0], d[1]), self.sub(d[0], d[1]), n(d[2]), d[3], d[4], d[5], d[6], n(d[7]),
+                self.add(d[8], d[9]), self.sub(d[8], d[9]), n(d[10]), n(d[11]), n(d[12]), n(d[13]),
+                d[14], n(d[15])]
+
+    def forward(self, x):
+        a = self.m1(x)
+        b = [a[g] for g in G1]
+        e = self.m4(self.m3(self.m2(b)))
+        return [e[g] for g in G2]
+
+    def inverse(self, y):
+        # T^t = M1 P1^t M2 M3 M4 P2^t (M1..M4 symmetric)
+        e = [None] * 16
+        for i in range(16):
+            e[G2[i]] = y[i]
+        c = self.m2(self.m3(self.m4(e)))
+        a = [None] * 16
+        for i in range(16):
+            a[G1[i]] = c[i]
+        return self.m1(a)
+
+
+def emit(net, outputs, in_names, out_name, materialize):
+    """C++ statements computing the needed outputs.  Returns (lines, signs)
+    where signs[k] is the sign of output k (0: known zero); with
+    `materialize`, negative outputs are negated (one fma by -1) so all
+    emitted outputs are the true values."""
+    live = set()
+    stack = [o[0] for o in outputs if o is not ZERO]
+    while stack:
+        k = stack.pop()
+        if k in live:
+            continue
+        live.add(k)
+        if net.nodes[k][0] != "in":
+            stack += [net.nodes[k][1], net.nodes[k][2]]
+    names = {}
+    lines = []
+    for k in sorted(live):
+        kind = net.nodes[k][0]
+        if kind == "in":
+            names[k] = in_names[net.nodes[k][1]]
+            continue
+        a, b = names[net.nodes[k][1]], names[net.nodes[k][2]]
+        t = f"t{k}"
+        if kind == "add":
+            lines.append(f"const float2 {t} = __fadd2_rn({a}, {b});")
+        else:  # a - b with one rounding: fma(b, -1, a)
+            lines.append(f"const float2 {t} = __ffma2_rn({b}, pm1(), {a});")
+        names[k] = t
+    signs = []
+    for idx, o in enumerate(outputs):
+        if o is ZERO:
+            lines.append(f"{out_name}[{idx}] = make_float2(0.f, 0.f);")
+            signs.append(0)
+            continue
+        k, s = o
+        if materialize and s < 0:
+            lines.append(f"{out_name}[{idx}] = __fmul2_rn({names[k]}, pm1());")
+            signs.append(1)
+        else:
+            lines.append(f"{out_name}[{idx}] = {names[k]};")
+            signs.append(s)
+    adds = sum(1 for k in live if net.nodes[k][0] != "in")
+    leaves = {net.nodes[k][1] for k in live if net.nodes[k][0] == "in"}
+    return lines, signs, adds, leaves
+
+
+def check(net, outputs, inputs_value, expect):
+    """Evaluate the DAG numerically and compare with the expected outputs."""
+    val = {}
+    for k, nd in enumerate(net.nodes):
+        if nd[0] == "in":
+            val[k] = inputs_value[nd[1]]
+        elif nd[0] == "add":
+            val[k] = val[nd[1]] + val[nd[2]]
+        else:
+            val[k] = val[nd[1]] - val[nd[2]]
+    for o, want in zip(outputs, expect):
+        got = 0 if o is ZERO else o[1] * val[o[0]]
+        assert got == want, (got, want)
+
+
+def matrix_from_network(inverse=False):
+    """The 16x16 matrix the network realises (column j = image of e_j)."""
+    M = [[0] * 16 for _ in range(16)]
+    for j in range(16):
+        net = Net()
+        x = [net.leaf(i) for i in range(16)]
+        y = net.inverse(x) if inverse else net.forward(x)
+        vals = [1 if i == j else 0 for i in range(16)]
+        val = {}
+        for k, nd in enumerate(net.nodes):
+            val[k] = vals[nd[1]] if nd[0] == "in" else (
+                val[nd[1]] + val[nd[2]] if nd[0] == "add" else val[nd[1]] - val[nd[2]])
+        for i in range(16):
+            M[i][j] = 0 if y[i] is ZERO else y[i][1] * val[y[i][0]]
+    return M
+
+
+ZONES = [(3, 4), (5, 6), (7, 8), (11, 10), (16, 16)]  # (rows U, columns V) kept
+
+
+def sign_fn(signs):
+    neg = sum(1 << i for i, x in enumerate(signs) if x < 0)
+    zero = sum(1 << i for i, x in enumerate(signs) if x == 0)
+    return (f"  __host__ __device__ static constexpr int sign(int i) {{ return sign_of(0x{neg:04x}u, "
+            f"0x{zero:04x}u, i); }}")
+
+
+def main():
+    T = matrix_from_network(False)
+    Tt = matrix_from_network(True)
+    assert all(Tt[i][j] == T[j][i] for i in range(16) for j in range(16)), "inverse is not T^t"
+    rnd = random.Random(1606)
+    out = []
+    w = out.append
+    w("// GENERATED by gen_networks.py -- do not edit.  The 44-addition network of")
+    w("// T = P2 M4 M3 M2 P1 M1 (Sec. 2.2) on float2 pairs, negations folded into the")
+    w("// additions and pruned to the zonal extents used by the fused codec.")
+    w("#pragma once")
+    w("#include <cuda_runtime.h>")
+    w("namespace tx16 {")
+    w("namespace pairnet {")
+    w("__device__ __forceinline__ float2 pm1() { return make_float2(-1.f, -1.f); }")
+    w("__device__ __forceinline__ float2 pbias() { return make_float2(-16777216.f, -16777216.f); }  // -2^24")
+    w("// sign of output i encoded as bit masks (negative / known zero)")
+    w("__host__ __device__ constexpr int sign_of(unsigned neg, unsigned zero, int i) {")
+    w("  return ((zero >> i) & 1u) ? 0 : (((neg >> i) & 1u) ? -1 : 1);")
+    w("}")
+    w("")
+    # forward row pass: inputs are biased samples X = 2^23 + x.  M1 is special:
+    #   x_i + x_j = (X_i - 2^24) + X_j  (both steps exact), x_i - x_j = X_i - X_j.
+    fwd_sign = None
+    for V in sorted({v for _, v in ZONES}):
+        # M1 on biased inputs is emitted by hand below; the rest symbolically
+        net2 = Net()
+        aa = [net2.leaf(i) for i in range(16)]  # a[0..15] as leaves
+        b = [aa[g] for g in G1]
+        e = net2.m4(net2.m3(net2.m2(b)))
+        y = [e[g] for g in G2]
+        outs = y[:V] + [ZERO] * (16 - V)
+        lines, signs, adds, live_a = emit(net2, outs, [f"a{i}" for i in range(16)], "y", materialize=False)
+        # numeric self-check of the composite (M1 by hand + the rest)
+        for _ in range(20):
+            xs = [rnd.randint(0, 255) for _ in range(16)]
+            av = [xs[i] + xs[15 - i] for i in range(8)] + [xs[7 - i] - xs[8 + i] for i in range(8)]
+            expect = [sum(T[k][m] * xs[m] for m in range(16)) if k < V else 0 for k in range(16)]
+            check(net2, outs, av, expect)
+        w(f"// forward row pass, outputs v < {V}: y[v] = sign[v] * (T x)[v]; {adds} pair additions after M1")
+        w(f"struct FwdRow{V} {{")
+        w(sign_fn(signs))
+        w("  __device__ static __forceinline__ void run(const float2 (&X)[16], float2 (&y)[16]) {")
+        for i in range(8):
+            j = 15 - i
+            if i in live_a:
+                w(f"    const float2 a{i} = __fadd2_rn(__fadd2_rn(X[{i}], pbias()), X[{j}]);")
+            if (8 + (7 - i)) in live_a:
+                # a[8 + k] = x[7 - k] - x[8 + k] with k = 7 - i  ->  x[i] - x[15 - i]
+                w(f"    const float2 a{8 + (7 - i)} = __ffma2_rn(X[{j}], pm1(), X[{i}]);")
+        for ln in lines:
+            w("    " + ln)
+        w("  }")
+        w("};")
+        w("")
+        if V == 16:
+            fwd_sign = signs
+    # forward column pass: 16 plain inputs, outputs u < U
+    col_sign = None
+    for U in sorted({u for u, _ in ZONES}):
+        net = Net()
+        x = [net.leaf(i) for i in range(16)]
+        y = net.forward(x)
+        outs = y[:U] + [ZERO] * (16 - U)
+        lines, signs, adds, _ = emit(net, outs, [f"x[{i}]" for i in range(16)], "y", materialize=False)
+        for _ in range(20):
+            xs = [rnd.randint(-4096, 4096) for _ in range(16)]
+            check(net, outs, xs, [sum(T[k][m] * xs[m] for m in range(16)) if k < U else 0 for k in range(16)])
+        w(f"// forward column pass, outputs u < {U}: y[u] = sign[u] * (T x)[u]; {adds} pair additions")
+        w(f"struct FwdCol{U} {{")
+        w(sign_fn(signs))
+        w("  __device__ static __forceinline__ void run(const float2 (&x)[16], float2 (&y)[16]) {")
+        for ln in lines:
+            w("    " + ln)
+        w("  }")
+        w("};")
+        w("")
+        if U == 16:
+            col_sign = signs
+    # inverse column pass: inputs u < U carry the forward column signs
+    for U in sorted({u for u, _ in ZONES}):
+        net = Net()
+        ins = [(net.leaf(i)[0], col_sign[i]) if i < U else ZERO for i in range(16)]
+        y = net.inverse(ins)
+        lines, signs, adds, _ = emit(net, y, [f"w[{i}]" for i in range(16)], "z", materialize=True)
+        for _ in range(20):
+            # true coefficient W_u = col_sign[u] * (stored node value)
+            ws = [rnd.randint(-5000, 5000) if i < U else 0 for i in range(16)]
+            node_vals = [col_sign[i] * ws[i] for i in range(16)]
+            check(net, y, node_vals, [sum(T[m][k] * ws[m] for m in range(16)) for k in range(16)])
+        w(f"// inverse column pass, inputs u < {U} (node values, signs of the forward column")
+        w(f"// pass), outputs z[i] = (T^t w)[i] materialised; {adds} pair additions")
+        w(f"struct InvCol{U} {{")
+        w("  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&z)[16]) {")
+        for ln in lines:
+            w("    " + ln)
+        w("  }")
+        w("};")
+        w("")
+    # inverse row pass: inputs v < V positive, outputs with signs
+    for V in sorted({v for _, v in ZONES}):
+        net = Net()
+        ins = [net.leaf(i) if i < V else ZERO for i in range(16)]
+        y = net.inverse(ins)
+        lines, signs, adds, _ = emit(net, y, [f"w[{i}]" for i in range(16)], "z", materialize=False)
+        for _ in range(20):
+            ws = [rnd.randint(-5000, 5000) if i < V else 0 for i in range(16)]
+            check(net, y, ws, [sum(T[m][k] * ws[m] for m in range(16)) for k in range(16)])
+        w(f"// inverse row pass, inputs v < {V}: z[j] = sign[j] * (T^t w)[j]; {adds} pair additions")
+        w(f"struct InvRow{V} {{")
+        w(sign_fn(signs))
+        w("  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&z)[16]) {")
+        for ln in lines:
+            w("    " + ln)
+        w("  }")
+        w("};")
+        w("")
+    w(f"// sign of each output of the (unpruned) forward network: row-pass outputs")
+    w(f"// are stored unsigned; the column thread folds this sign into its scale.")
+    w(f"constexpr unsigned kFwdNegMask = 0x{sum(1 << i for i, x in enumerate(fwd_sign) if x < 0):04x}u;")
+    w("}  // namespace pairnet")
+    w("}  // namespace tx16")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tx16_pairnet.cuh")
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+    print("wrote", path)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,10 @@ static ImgParam base_param(const tx16_image& im, int64_t blk0) {
   p.nbx = im.width / 16;
   p.nblk = (im.width / 16) * (im.height / 16);
   p.flags = im.bits;
+  // m = floor(2^32 / nbx) (2^32 - 1 for nbx = 1): for blk < 2^31 the quotient
+  // umulhi(blk, m) is exact or one too small, which the kernels correct
+  p.div_shift = 0;
+  p.div_magic = p.nbx == 1 ? 0xFFFFFFFFu : uint32_t((uint64_t(1) << 32) / uint64_t(p.nbx));
   return p;
 }
 
@@ -199,7 +203,23 @@ tx16_status tx16_codec_batch(const tx16_image* in, const tx16_image* out, int32_
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (sse != nullptr && cudaMemsetAsync(sse, 0, sizeof(uint64_t) * size_t(n), st) != cudaSuccess)
     return TX16_ECUDA;
-  return launch_runs(kOpCodec, in, P, reinterpret_cast<unsigned long long*>(sse), levels, st);
+  // 8-bit runs whose steps suit the fused pair kernel go there; the rest
+  // (16-bit samples, q below kFusedMinQ) take the general block kernel
+  unsigned long long* s64 = reinterpret_cast<unsigned long long*>(sse);
+  int s = 0;
+  while (s < n) {
+    const bool fast = in[s].bits == 8 && (qp[s].q <= 0.f || qp[s].q >= kFusedMinQ);
+    int e = s + 1;
+    while (e < n && (in[e].bits == 8 && (qp[e].q <= 0.f || qp[e].q >= kFusedMinQ)) == fast &&
+           sample_bytes(in[e].bits) == sample_bytes(in[s].bits))
+      ++e;
+    const tx16_status r = fast ? launch_fused_u8(P.data() + s, e - s, s64 ? s64 + s : nullptr, levels, st)
+                               : launch_blocks(kOpCodec, sample_bytes(in[s].bits), P.data() + s, e - s,
+                                               s64 ? s64 + s : nullptr, levels, st);
+    if (r != TX16_OK) return r;
+    s = e;
+  }
+  return TX16_OK;
 }
 
 tx16_status tx16_sse(const tx16_image* a, const tx16_image* b, int32_t n, uint64_t* sse, void* stream) {

@@ -25,6 +25,8 @@ struct ImgParam {
   int32_t nblk;        // blocks in the image
   int32_t tile0;       // first tile of this image within the launch
   int32_t flags;       // bits (low 8) | kQuantFlag
+  uint32_t div_magic;  // blk / nbx = (umulhi(blk, div_magic) >> div_shift), or one more
+  int32_t div_shift;
   float f[5];          // fl32(sqrt2^k / (16 q)), k = e(u) + e(v)   (forward scale)
   float g[5];          // fl32(q sqrt2^k / 16)                      (inverse scale)
   uint8_t colh[16];    // kept rows of column v: |Z_r ∩ column v| (a prefix 0..colh-1)
@@ -51,6 +53,13 @@ bool valid_image(const tx16_image& im);
 int sample_bytes(int bits);
 void zonal_column_heights(int r, uint8_t colh[16]);
 void quant_constants(float q, float f[5], float g[5]);
+
+// Fused 8-bit codec (tx16_fused.cu): needs q >= kFusedMinQ when quantising
+// (|Y f| + 1/2 < 2^23 keeps the rounding trick exact).
+constexpr float kFusedMinQ = 1.0f / 256.0f;
+tx16_status launch_fused_u8(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
+                            cudaStream_t stream);
+int fused_zone_class(const ImgParam* imgs, int n);
 
 // Launchers (tx16_codec.cu).  `imgs` points at `n` ImgParam already filled in
 // (except tile0, set here), all with the same sample size.
