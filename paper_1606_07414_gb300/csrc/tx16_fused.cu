@@ -36,20 +36,21 @@ namespace {
 
 using namespace pairnet;
 
-template <int U_, int V_, class FR, class FC, class IC, class IR>
+template <int U_, int V_, class FR, class FC, class IC, class IR, int MINB>
 struct Zone {
   static constexpr int U = U_;  // kept rows u < U
   static constexpr int V = V_;  // kept columns v < V
+  static constexpr int kMinCtas = MINB;  // resident CTAs per SM the registers are budgeted for
   using FwdRow = FR;
   using FwdCol = FC;
   using InvCol = IC;
   using InvRow = IR;
 };
-using ZoneA = Zone<3, 4, FwdRow4, FwdCol3, InvCol3, InvRow4>;        // r <= 8
-using ZoneB = Zone<5, 6, FwdRow6, FwdCol5, InvCol5, InvRow6>;        // r <= 16
-using ZoneC = Zone<7, 8, FwdRow8, FwdCol7, InvCol7, InvRow8>;        // r <= 32
-using ZoneD = Zone<11, 10, FwdRow10, FwdCol11, InvCol11, InvRow10>;  // r <= 64
-using ZoneE = Zone<16, 16, FwdRow16, FwdCol16, InvCol16, InvRow16>;  // any r
+using ZoneA = Zone<3, 4, FwdRow4, FwdCol3, InvCol3, InvRow4, 8>;        // r <= 8
+using ZoneB = Zone<5, 6, FwdRow6, FwdCol5, InvCol5, InvRow6, 8>;        // r <= 16
+using ZoneC = Zone<7, 8, FwdRow8, FwdCol7, InvCol7, InvRow8, 6>;        // r <= 32
+using ZoneD = Zone<11, 10, FwdRow10, FwdCol11, InvCol11, InvRow10, 5>;  // r <= 64
+using ZoneE = Zone<16, 16, FwdRow16, FwdCol16, InvCol16, InvRow16, 4>;  // any r
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
@@ -72,9 +73,8 @@ struct ImgState {
   int64_t sp, dp, blk0;
   int nbx, nblk, tile0, tile_end;
   unsigned magic;
-  int shift;
   bool quant;
-  // column-thread constants (column v = l): scale by class e(u) = 0, 1, 2
+  // column-task constants (column v of the task): scale by class e(u) = 0, 1, 2
   float2 fs[3];  // quantiser: sign_v * f ; no quantiser: sign_v * D'_u D'_v / 256
   float2 gg[3];  // g
   float2 gc[3];  // -2^23 g
@@ -94,7 +94,6 @@ __device__ __forceinline__ void load_image(const BatchParams<MAXI>& P, int k, in
   S.tile0 = I.tile0;
   S.tile_end = (k + 1 < P.nimg) ? P.img[k + 1].tile0 : P.ntiles;
   S.magic = I.div_magic;
-  S.shift = I.div_shift;
   S.quant = (I.flags & kQuantFlag) != 0;
   const int ev = scale_class(v);
   const float sv = ((kFwdNegMask >> v) & 1u) ? -1.f : 1.f;
@@ -113,15 +112,14 @@ __device__ __forceinline__ void load_image(const BatchParams<MAXI>& P, int k, in
   S.h = I.colh[v];
 }
 
-__device__ __forceinline__ void block_coords(const ImgState& S, int blk, int& by, int& bx) {
-  unsigned q = __umulhi(unsigned(blk), S.magic) >> S.shift;
-  int r = blk - int(q) * S.nbx;
-  if (r >= S.nbx) {
-    ++q;
-    r -= S.nbx;
-  }
-  by = int(q);
-  bx = r;
+// (by, bx) of block blk: umulhi quotient, exact or one short, then corrected
+__device__ __forceinline__ int2 block_coords(unsigned magic, int nbx, int blk) {
+  int q = int(__umulhi(unsigned(blk), magic));
+  int r = blk - q * nbx;
+  const bool over = r >= nbx;
+  q += over ? 1 : 0;
+  r -= over ? nbx : 0;
+  return make_int2(q, r);
 }
 
 __device__ __forceinline__ void flush_sse(unsigned long long* sse, int img, unsigned long long v) {
@@ -130,14 +128,33 @@ __device__ __forceinline__ void flush_sse(unsigned long long* sse, int img, unsi
   if ((threadIdx.x & 31) == 0 && v != 0ull) atomicAdd(sse + img, v);
 }
 
-constexpr int kRowWords = 36;  // 16 float2 + 4 words of padding per row
+constexpr int kSlotWords = 36;  // one column slot: 16 float2 + 4 words of padding
 
-template <int MAXI, class Z>
-__global__ void __launch_bounds__(128) fused_u8_kernel(const __grid_constant__ BatchParams<MAXI> P) {
-  __shared__ __align__(16) float smem[8][16][kRowWords];
-  const int l = threadIdx.x & 15;  // row (row phases) or column v (column phase)
-  const int p = threadIdx.x >> 4;  // block pair: blocks p and p + 8 of the tile
-  float(*Sm)[kRowWords] = smem[p];
+// (image row, byte column) of row l of block blk; row -1 past the image's end
+__device__ __forceinline__ int2 row_pos(unsigned magic, int nbx, int nblk, int blk, int l) {
+  if (blk >= nblk) return make_int2(-1, 0);
+  const int2 c = block_coords(magic, nbx, blk);
+  return make_int2(c.x * 16 + l, c.y * 16);
+}
+
+__device__ __forceinline__ uint4 load_row(const uint8_t* base, int64_t pitch, int2 rc) {
+  return rc.x >= 0 ? __ldcs(reinterpret_cast<const uint4*>(base + int64_t(rc.x) * pitch + rc.y))
+                   : make_uint4(0, 0, 0, 0);
+}
+
+// Kernel template: MAXI images per launch, zone class Z, LEV = write levels,
+// DST = write reconstructed samples.
+template <int MAXI, class Z, bool LEV, bool DST>
+__global__ void __launch_bounds__(128, Z::kMinCtas) fused_u8_kernel(const __grid_constant__ BatchParams<MAXI> P) {
+  // column slots: slot p*V + v holds column v of block pair p (16 float2)
+  __shared__ __align__(16) float smem[8 * Z::V * kSlotWords];
+  constexpr int kTasks = 8 * Z::V;  // column tasks per tile
+  const int l = threadIdx.x & 15;   // row of the block pair (row phases)
+  const int p = threadIdx.x >> 4;   // block pair: blocks p and p + 8 of the tile
+  const int task = threadIdx.x;     // column task: pair task / V, column task % V
+  const int tv = task % Z::V;
+  const bool col_active = task < kTasks;
+  const bool warp_has_cols = (task & ~31) < kTasks;
 
   const int per = (P.ntiles + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * per;
@@ -153,68 +170,44 @@ __global__ void __launch_bounds__(128) fused_u8_kernel(const __grid_constant__ B
     }
   }
   ImgState S;
-  load_image(P, k, l, S);
+  load_image(P, k, tv, S);
   unsigned long long acc = 0;
 
-  // rows of the current tile, prefetched one tile ahead
-  uint4 ra = make_uint4(0, 0, 0, 0), rb = ra;
-  auto row_ptrs = [&](const ImgState& s, int t, const uint8_t*& pa, const uint8_t*& pb) {
-    const int base = (t - s.tile0) * kTileBlocks;
-    int by, bx;
-    pa = nullptr;
-    pb = nullptr;
-    if (base + p < s.nblk) {
-      block_coords(s, base + p, by, bx);
-      pa = s.src + (int64_t(by) * 16 + l) * s.sp + int64_t(bx) * 16;
-    }
-    if (base + p + 8 < s.nblk) {
-      block_coords(s, base + p + 8, by, bx);
-      pb = s.src + (int64_t(by) * 16 + l) * s.sp + int64_t(bx) * 16;
-    }
-  };
+  // rows of the current tile (prefetched one tile ahead) and their offsets
+  uint4 ra, rb;
+  int2 pa_next, pb_next;
   {
-    const uint8_t *pa, *pb;
-    row_ptrs(S, t0, pa, pb);
-    if (pa) ra = __ldcs(reinterpret_cast<const uint4*>(pa));
-    if (pb) rb = __ldcs(reinterpret_cast<const uint4*>(pb));
+    const int base = (t0 - S.tile0) * kTileBlocks;
+    pa_next = row_pos(S.magic, S.nbx, S.nblk, base + p, l);
+    pb_next = row_pos(S.magic, S.nbx, S.nblk, base + p + 8, l);
+    ra = load_row(S.src, S.sp, pa_next);
+    rb = load_row(S.src, S.sp, pb_next);
   }
 
   for (int t = t0; t < t1; ++t) {
-    if (t >= S.tile_end) {  // uniform: next image
+    if (t >= S.tile_end) {  // uniform over the CTA: next image
       if (P.sse) flush_sse(P.sse, k, acc);
       acc = 0;
-      while (t >= S.tile_end) {
+      do {
         ++k;
-        S.tile_end = (k + 1 < P.nimg) ? P.img[k + 1].tile0 : P.ntiles;
-      }
-      load_image(P, k, l, S);
+      } while (k + 1 < P.nimg && P.img[k + 1].tile0 <= t);
+      load_image(P, k, tv, S);
     }
     const uint4 ca = ra, cb = rb;
-    // prefetch the next tile's rows (possibly of the next image)
+    const int2 pa = pa_next, pb = pb_next;
+    // prefetch the next tile's rows (they may belong to the next image)
     if (t + 1 < t1) {
-      const uint8_t *pa, *pb;
-      if (t + 1 < S.tile_end) {
-        row_ptrs(S, t + 1, pa, pb);
-      } else {
-        int kn = k;
+      int kn = k;
+      if (t + 1 >= S.tile_end) {
         while (kn + 1 < P.nimg && P.img[kn + 1].tile0 <= t + 1) ++kn;
-        ImgState Sn;
-        const ImgParam& In = P.img[kn];
-        Sn.src = static_cast<const uint8_t*>(In.src);
-        Sn.sp = In.src_pitch;
-        Sn.nbx = In.nbx;
-        Sn.nblk = In.nblk;
-        Sn.tile0 = In.tile0;
-        Sn.magic = In.div_magic;
-        Sn.shift = In.div_shift;
-        row_ptrs(Sn, t + 1, pa, pb);
       }
-      ra = pa ? __ldcs(reinterpret_cast<const uint4*>(pa)) : make_uint4(0, 0, 0, 0);
-      rb = pb ? __ldcs(reinterpret_cast<const uint4*>(pb)) : make_uint4(0, 0, 0, 0);
+      const ImgParam& In = P.img[kn];
+      const int base = (t + 1 - In.tile0) * kTileBlocks;
+      pa_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p, l);
+      pb_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p + 8, l);
+      ra = load_row(static_cast<const uint8_t*>(In.src), In.src_pitch, pa_next);
+      rb = load_row(static_cast<const uint8_t*>(In.src), In.src_pitch, pb_next);
     }
-    const int base = (t - S.tile0) * kTileBlocks;
-    const bool va = base + p < S.nblk;
-    const bool vb = base + p + 8 < S.nblk;
 
     // ---- row phase: forward transform of row l of both blocks ----
     {
@@ -226,82 +219,101 @@ __global__ void __launch_bounds__(128) fused_u8_kernel(const __grid_constant__ B
       float2 y[16];
       Z::FwdRow::run(X, y);
 #pragma unroll
-      for (int v = 0; v < Z::V; v += 2)
-        *reinterpret_cast<float4*>(&Sm[l][2 * v]) = make_float4(y[v].x, y[v].y, y[v + 1].x, y[v + 1].y);
+      for (int v = 0; v < Z::V; ++v)
+        *reinterpret_cast<float2*>(&smem[(p * Z::V + v) * kSlotWords + 2 * l]) = y[v];
+      if (LEV) {  // columns v >= V hold no kept coefficient: level 0 (row l of both blocks)
+        const int base = (t - S.tile0) * kTileBlocks;
+        int* ra_ = P.coeffs + (S.blk0 + base + p) * 256 + l * 16;
+#pragma unroll
+        for (int v = Z::V; v < 16; ++v) {
+          if (pa.x >= 0) __stcs(ra_ + v, 0);
+          if (pb.x >= 0) __stcs(ra_ + 8 * 256 + v, 0);
+        }
+      }
     }
-    __syncwarp();
+    __syncthreads();
 
-    // ---- column phase: thread v = l ----
-    {
+    // ---- column phase: task (pair task / V, column tv) ----
+    if (warp_has_cols) {
+      // lanes past the last task (a partly used warp) read slot 0 and write nothing
+      float* slot = &smem[(col_active ? task : 0) * kSlotWords];
       float2 x[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) x[u] = *reinterpret_cast<const float2*>(&Sm[u][2 * l]);
+      for (int u = 0; u < 16; u += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(slot + 2 * u);
+        x[u] = make_float2(q.x, q.y);
+        x[u + 1] = make_float2(q.z, q.w);
+      }
       float2 n[16];
-      Z::FwdCol::run(x, n);  // n[u] = FwdCol::sign(u) * (row-pass sign of v) * Y[u][v]
+      Z::FwdCol::run(x, n);  // n[u] = FwdCol::sign(u) * (row-pass sign of tv) * Y[u][tv]
       float2 w[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) w[u] = make_float2(0.f, 0.f);
-      int* lev = P.coeffs;
+      const int tp = task / Z::V;
+      const int tbase = (t - S.tile0) * kTileBlocks;
+      const bool tva = col_active && tbase + tp < S.nblk;
+      const bool tvb = col_active && tbase + tp + 8 < S.nblk;
+      int* lev_a = LEV ? P.coeffs + (S.blk0 + tbase + tp) * 256 + tv : nullptr;
+      int* lev_b = LEV ? lev_a + 8 * 256 : nullptr;
       if (S.quant) {
 #pragma unroll
         for (int u = 0; u < Z::U; ++u) {
           const int e = scale_class(u);
-          const float2 t = __fmul2_rn(n[u], S.fs[e]);
-          const float2 a = make_float2(fabsf(t.x), fabsf(t.y));
+          const float2 tq = __fmul2_rn(n[u], S.fs[e]);
+          const float2 a = make_float2(fabsf(tq.x), fabsf(tq.y));
           const float2 m = __fadd2_rd(__fadd2_rd(a, f2(0.5f)), f2(8388608.f));  // 2^23 + floor(|t| + 1/2)
           float2 q = __ffma2_rn(m, S.gg[e], S.gc[e]);                          // fl32(level * g)
-          q.x = __uint_as_float(__float_as_uint(q.x) | (__float_as_uint(t.x) & 0x80000000u));
-          q.y = __uint_as_float(__float_as_uint(q.y) | (__float_as_uint(t.y) & 0x80000000u));
-          if (u < S.h) w[u] = q;
-          if (lev != nullptr) {
+          q.x = __uint_as_float(__float_as_uint(q.x) | (__float_as_uint(tq.x) & 0x80000000u));
+          q.y = __uint_as_float(__float_as_uint(q.y) | (__float_as_uint(tq.y) & 0x80000000u));
+          const bool keep = u < S.h;
+          w[u] = keep ? q : make_float2(0.f, 0.f);
+          if (LEV) {
             // level = sign(FwdCol) * sign(t) * floor(|t| + 1/2)
+            const unsigned flip = Z::FwdCol::sign(u) < 0 ? 1u : 0u;
             int la = int(__float_as_uint(m.x) - 0x4B000000u), lb = int(__float_as_uint(m.y) - 0x4B000000u);
-            if ((__float_as_uint(t.x) >> 31) != (Z::FwdCol::sign(u) < 0 ? 1u : 0u)) la = -la;
-            if ((__float_as_uint(t.y) >> 31) != (Z::FwdCol::sign(u) < 0 ? 1u : 0u)) lb = -lb;
-            if (u >= S.h) la = lb = 0;
-            if (va) __stcs(lev + (S.blk0 + base + p) * 256 + u * 16 + l, la);
-            if (vb) __stcs(lev + (S.blk0 + base + p + 8) * 256 + u * 16 + l, lb);
+            la = ((__float_as_uint(tq.x) >> 31) != flip) ? -la : la;
+            lb = ((__float_as_uint(tq.y) >> 31) != flip) ? -lb : lb;
+            if (tva) __stcs(lev_a + u * 16, keep ? la : 0);
+            if (tvb) __stcs(lev_b + u * 16, keep ? lb : 0);
           }
         }
       } else {
 #pragma unroll
         for (int u = 0; u < Z::U; ++u) {
           const float2 q = __fmul2_rn(n[u], S.fs[scale_class(u)]);
-          if (u < S.h) w[u] = q;
-          if (lev != nullptr) {
-            const float sgn = float(Z::FwdCol::sign(u)) * (((kFwdNegMask >> l) & 1u) ? -1.f : 1.f);
-            const int la = u < S.h ? __float2int_rn(sgn * n[u].x) : 0;
-            const int lb = u < S.h ? __float2int_rn(sgn * n[u].y) : 0;
-            if (va) __stcs(lev + (S.blk0 + base + p) * 256 + u * 16 + l, la);
-            if (vb) __stcs(lev + (S.blk0 + base + p + 8) * 256 + u * 16 + l, lb);
+          const bool keep = u < S.h;
+          w[u] = keep ? q : make_float2(0.f, 0.f);
+          if (LEV) {
+            const float sgn = float(Z::FwdCol::sign(u)) * (((kFwdNegMask >> tv) & 1u) ? -1.f : 1.f);
+            if (tva) __stcs(lev_a + u * 16, keep ? __float2int_rn(sgn * n[u].x) : 0);
+            if (tvb) __stcs(lev_b + u * 16, keep ? __float2int_rn(sgn * n[u].y) : 0);
           }
         }
       }
-      if (lev != nullptr) {
+      if (LEV) {
 #pragma unroll
         for (int u = Z::U; u < 16; ++u) {
-          if (va) __stcs(lev + (S.blk0 + base + p) * 256 + u * 16 + l, 0);
-          if (vb) __stcs(lev + (S.blk0 + base + p + 8) * 256 + u * 16 + l, 0);
+          if (tva) __stcs(lev_a + u * 16, 0);
+          if (tvb) __stcs(lev_b + u * 16, 0);
         }
       }
       float2 z[16];
-      Z::InvCol::run(w, z);  // z[i] = (T^t W)[i][v]
+      Z::InvCol::run(w, z);  // z[i] = (T^t W)[i][tv]
+      if (col_active) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) *reinterpret_cast<float2*>(&Sm[i][2 * l]) = z[i];
+        for (int i = 0; i < 16; i += 2)
+          *reinterpret_cast<float4*>(slot + 2 * i) = make_float4(z[i].x, z[i].y, z[i + 1].x, z[i + 1].y);
+      }
     }
-    __syncwarp();
+    __syncthreads();
 
     // ---- row phase: inverse row transform, rounding, store, SSE ----
     {
       float2 w[16];
 #pragma unroll
-      for (int v = 0; v < 16; ++v) w[v] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int v = 0; v < Z::V; v += 2) {
-        const float4 q = *reinterpret_cast<const float4*>(&Sm[l][2 * v]);
-        w[v] = make_float2(q.x, q.y);
-        w[v + 1] = make_float2(q.z, q.w);
-      }
+      for (int v = 0; v < 16; ++v)
+        w[v] = v < Z::V ? *reinterpret_cast<const float2*>(&smem[(p * Z::V + v) * kSlotWords + 2 * l])
+                        : make_float2(0.f, 0.f);
       float2 z[16];
       Z::InvRow::run(w, z);  // z[j] = sign[j] * X_tilde[l][j]
       // sample = clip(floor(X + 1/2), 0, 255): the low byte of the binary16
@@ -312,56 +324,46 @@ __global__ void __launch_bounds__(128) fused_u8_kernel(const __grid_constant__ B
       for (int j = 0; j < 16; ++j) {
         const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(1024.5f))
                                                  : __ffma2_rd(z[j], pm1(), f2(1024.5f));
-        __half2 hv;
         const unsigned raw = cvt_rz_h2(r);
-        hv = *reinterpret_cast<const __half2*>(&raw);
+        __half2 hv = *reinterpret_cast<const __half2*>(&raw);
         hv = __hmin2(__hmax2(hv, lo), hi);
         h[j] = *reinterpret_cast<const unsigned*>(&hv);
       }
-      unsigned oa[4], ob[4];
+      unsigned xa[4], xb[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const unsigned t01 = __byte_perm(h[4 * q], h[4 * q + 1], 0x6240u);
         const unsigned t23 = __byte_perm(h[4 * q + 2], h[4 * q + 3], 0x6240u);
-        oa[q] = __byte_perm(t01, t23, 0x5410u);
-        ob[q] = __byte_perm(t01, t23, 0x7632u);
+        xa[q] = __byte_perm(t01, t23, 0x5410u);
+        xb[q] = __byte_perm(t01, t23, 0x7632u);
       }
-      if (S.dst != nullptr) {
-        int by, bx;
-        if (va) {
-          block_coords(S, base + p, by, bx);
-          __stcs(reinterpret_cast<uint4*>(S.dst + (int64_t(by) * 16 + l) * S.dp + int64_t(bx) * 16),
-                 make_uint4(oa[0], oa[1], oa[2], oa[3]));
-        }
-        if (vb) {
-          block_coords(S, base + p + 8, by, bx);
-          __stcs(reinterpret_cast<uint4*>(S.dst + (int64_t(by) * 16 + l) * S.dp + int64_t(bx) * 16),
-                 make_uint4(ob[0], ob[1], ob[2], ob[3]));
-        }
+      if (DST) {
+        if (pa.x >= 0)
+          __stcs(reinterpret_cast<uint4*>(S.dst + int64_t(pa.x) * S.dp + pa.y), make_uint4(xa[0], xa[1], xa[2], xa[3]));
+        if (pb.x >= 0)
+          __stcs(reinterpret_cast<uint4*>(S.dst + int64_t(pb.x) * S.dp + pb.y), make_uint4(xb[0], xb[1], xb[2], xb[3]));
       }
-      // SSE = sum x^2 + sum y^2 - 2 sum x y over the row's bytes (dp4a)
+      // SSE = sum x^2 + sum y^2 - 2 sum x y over the row's bytes (dp4a).  A
+      // block past the end of the image was loaded as zeros and reconstructs
+      // to zeros, so it adds nothing.
       const unsigned ia[4] = {ca.x, ca.y, ca.z, ca.w}, ib[4] = {cb.x, cb.y, cb.z, cb.w};
-      unsigned sxx = 0, syy = 0, sxy = 0;
+      unsigned s1 = 0, s2 = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (va) {
-          sxx = __dp4a(ia[q], ia[q], sxx);
-          syy = __dp4a(oa[q], oa[q], syy);
-          sxy = __dp4a(ia[q], oa[q], sxy);
-        }
-        if (vb) {
-          sxx = __dp4a(ib[q], ib[q], sxx);
-          syy = __dp4a(ob[q], ob[q], syy);
-          sxy = __dp4a(ib[q], ob[q], sxy);
-        }
+        s1 = __dp4a(ia[q], ia[q], s1);
+        s1 = __dp4a(xa[q], xa[q], s1);
+        s1 = __dp4a(ib[q], ib[q], s1);
+        s1 = __dp4a(xb[q], xb[q], s1);
+        s2 = __dp4a(ia[q], xa[q], s2);
+        s2 = __dp4a(ib[q], xb[q], s2);
       }
-      acc += (unsigned long long)(sxx + syy - 2u * sxy);
+      acc += (unsigned long long)(s1 - 2u * s2);
     }
   }
   if (P.sse) flush_sse(P.sse, k, acc);
 }
 
-template <int MAXI, class Z>
+template <int MAXI, class Z, bool LEV, bool DST>
 tx16_status launch_fused(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                          cudaStream_t stream) {
   BatchParams<MAXI> P;
@@ -378,25 +380,41 @@ tx16_status launch_fused(const ImgParam* imgs, int n, unsigned long long* sse, i
   static int occ = 0;
   if (occ == 0) {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_u8_kernel<MAXI, Z>, 128, 0) != cudaSuccess || o < 1)
+    // prefer shared memory over L1 so the register limit, not the carveout,
+    // sets the resident CTAs per SM
+    cudaFuncSetAttribute(fused_u8_kernel<MAXI, Z, LEV, DST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_u8_kernel<MAXI, Z, LEV, DST>, 128, 0) !=
+            cudaSuccess || o < 1)
       o = 1;
     occ = o;
   }
   const int grid = std::max(1, std::min(tiles, occ * device_sm_count()));
-  fused_u8_kernel<MAXI, Z><<<grid, 128, 0, stream>>>(P);
+  fused_u8_kernel<MAXI, Z, LEV, DST><<<grid, 128, 0, stream>>>(P);
   return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
 }
 
-template <int MAXI>
+template <int MAXI, bool LEV, bool DST>
 tx16_status launch_fused_zone(int zone, const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                               cudaStream_t stream) {
   switch (zone) {
-    case 0: return launch_fused<MAXI, ZoneA>(imgs, n, sse, levels, stream);
-    case 1: return launch_fused<MAXI, ZoneB>(imgs, n, sse, levels, stream);
-    case 2: return launch_fused<MAXI, ZoneC>(imgs, n, sse, levels, stream);
-    case 3: return launch_fused<MAXI, ZoneD>(imgs, n, sse, levels, stream);
-    default: return launch_fused<MAXI, ZoneE>(imgs, n, sse, levels, stream);
+    case 0: return launch_fused<MAXI, ZoneA, LEV, DST>(imgs, n, sse, levels, stream);
+    case 1: return launch_fused<MAXI, ZoneB, LEV, DST>(imgs, n, sse, levels, stream);
+    case 2: return launch_fused<MAXI, ZoneC, LEV, DST>(imgs, n, sse, levels, stream);
+    case 3: return launch_fused<MAXI, ZoneD, LEV, DST>(imgs, n, sse, levels, stream);
+    default: return launch_fused<MAXI, ZoneE, LEV, DST>(imgs, n, sse, levels, stream);
   }
+}
+
+template <int MAXI>
+tx16_status launch_fused_modes(int zone, const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
+                               cudaStream_t stream) {
+  const bool dst = imgs[0].dst != nullptr;
+  if (levels != nullptr)
+    return dst ? launch_fused_zone<MAXI, true, true>(zone, imgs, n, sse, levels, stream)
+               : launch_fused_zone<MAXI, true, false>(zone, imgs, n, sse, levels, stream);
+  return dst ? launch_fused_zone<MAXI, false, true>(zone, imgs, n, sse, levels, stream)
+             : launch_fused_zone<MAXI, false, false>(zone, imgs, n, sse, levels, stream);
 }
 
 }  // namespace
@@ -421,9 +439,9 @@ tx16_status launch_fused_u8(const ImgParam* imgs, int n, unsigned long long* sse
   for (int s = 0; s < n; s += kMaxImg) {
     const int m = std::min(kMaxImg, n - s);
     const int zone = fused_zone_class(imgs + s, m);
-    const tx16_status st = m <= 8 ? launch_fused_zone<8>(zone, imgs + s, m, sse ? sse + s : nullptr, levels, stream)
-                                  : launch_fused_zone<kMaxImg>(zone, imgs + s, m, sse ? sse + s : nullptr, levels,
-                                                               stream);
+    const tx16_status st = m <= 8 ? launch_fused_modes<8>(zone, imgs + s, m, sse ? sse + s : nullptr, levels, stream)
+                                  : launch_fused_modes<kMaxImg>(zone, imgs + s, m, sse ? sse + s : nullptr, levels,
+                                                                stream);
     if (st != TX16_OK) return st;
   }
   return TX16_OK;
