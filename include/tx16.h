@@ -148,6 +148,51 @@ tx16_status tx16_sse(const tx16_image* a, const tx16_image* b, int32_t n, uint64
  */
 tx16_status tx16_psnr(const uint64_t* sse, const tx16_image* imgs, int32_t n, double* psnr);
 
+/* ------------------------------------------------------------------------ */
+/* Batch plans: uneven-size batches in one persistent launch per zonal class */
+/* ------------------------------------------------------------------------ */
+
+/* A plan holds a device-side work list for one batch: the per-image
+ * descriptors of the codec (the same computation as tx16_codec_batch, Sec. 3.1
+ * of the paper) in device memory, grouped by the extent of each image's zone
+ * Z_r, plus one tile counter per group.  Running it launches one persistent
+ * fused kernel per group whose CTAs claim tiles of 16 blocks from the counter,
+ * so uneven image sizes and zones balance across the SMs.  The plan owns its
+ * device memory (allocated once, at creation); the images' sample buffers
+ * stay the caller's and must outlive the plan. */
+typedef struct tx16_plan tx16_plan;
+
+/* Build a plan for n images (host descriptor arrays, as for tx16_codec_batch;
+ * out may be NULL).  Errors: TX16_EINVAL (arguments), TX16_ENOMEM (device
+ * allocation), TX16_ECUDA.  Synchronous. */
+tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_t n, const tx16_qparams* qp,
+                             tx16_plan** plan);
+
+/* Run the plan on `stream`.  sse: device uint64[n] (zeroed by the run) or
+ * NULL; levels: device int32, block-major over the n images, or NULL.
+ * Results equal tx16_codec_batch's on the same images.  Runs of one plan are
+ * ordered by their stream; two runs of one plan must not overlap in time. */
+tx16_status tx16_plan_run(tx16_plan* plan, uint64_t* sse, int32_t* levels, void* stream);
+
+/* As tx16_plan_run, through a CUDA graph captured on first use (and again
+ * when sse/levels change or after autotuning), replayed on `stream`. */
+tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels, void* stream);
+
+/* Time the schedule candidates (resident CTAs per SM, tiles per claim) of
+ * each group on the plan's own data and keep the fastest.  cache_path: a
+ * text file of tuned schedules keyed by device, group and size class (read
+ * and extended), or NULL.  Synchronous on `stream`; writes the outputs. */
+tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* stream);
+
+/* Introspection: number of groups and, for the first max_runs of them, the
+ * zone class (0..4, -1 = general kernel), tiles, CTAs per SM (0 = all that
+ * fit) and tiles per claim.  Host arrays; any of them may be NULL. */
+tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, int32_t* tiles,
+                           int32_t* ctas_per_sm, int32_t* chunk, int32_t max_runs);
+
+/* Free the plan's device memory and graph.  NULL is ignored. */
+void tx16_plan_destroy(tx16_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

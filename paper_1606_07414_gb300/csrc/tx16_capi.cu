@@ -65,9 +65,10 @@ void quant_constants(float q, float f[5], float g[5]) {
   }
 }
 
-static bool valid_qp(const tx16_qparams& qp) {
+bool valid_qparams(const tx16_qparams& qp) {
   return qp.r >= 1 && qp.r <= 256 && std::isfinite(qp.q);
 }
+static bool valid_qp(const tx16_qparams& qp) { return valid_qparams(qp); }
 
 static void fill_quant(ImgParam& p, const tx16_qparams& qp) {
   quant_constants(qp.q, p.f, p.g);
@@ -86,8 +87,20 @@ static ImgParam base_param(const tx16_image& im, int64_t blk0) {
   p.flags = im.bits;
   // m = floor(2^32 / nbx) (2^32 - 1 for nbx = 1): for blk < 2^31 the quotient
   // umulhi(blk, m) is exact or one too small, which the kernels correct
-  p.div_shift = 0;
+  p.out_index = 0;
   p.div_magic = p.nbx == 1 ? 0xFFFFFFFFu : uint32_t((uint64_t(1) << 32) / uint64_t(p.nbx));
+  return p;
+}
+
+// Descriptor of one codec image: input, optional output, quantiser, and the
+// index of its first block in the coefficient/level layout.
+ImgParam make_param(const tx16_image& in, const tx16_image* out, const tx16_qparams& qp, int64_t blk0) {
+  ImgParam p = base_param(in, blk0);
+  if (out != nullptr) {
+    p.dst = out->data;
+    p.dst_pitch = out->pitch_bytes;
+  }
+  fill_quant(p, qp);
   return p;
 }
 

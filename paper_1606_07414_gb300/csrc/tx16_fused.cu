@@ -73,6 +73,7 @@ struct ImgState {
   int64_t sp, dp, blk0;
   int nbx, nblk, tile0, tile_end;
   unsigned magic;
+  int out;  // index into sse[]
   bool quant;
   // column-task constants (column v of the task): scale by class e(u) = 0, 1, 2
   float2 fs[3];  // quantiser: sign_v * f ; no quantiser: sign_v * D'_u D'_v / 256
@@ -81,9 +82,9 @@ struct ImgState {
   int h;         // kept rows in column v
 };
 
-template <int MAXI>
-__device__ __forceinline__ void load_image(const BatchParams<MAXI>& P, int k, int v, ImgState& S) {
-  const ImgParam& I = P.img[k];
+__device__ __forceinline__ void load_image(const ImgParam* imgs, int nimg, int ntiles, int k, int v,
+                                           ImgState& S) {
+  const ImgParam& I = imgs[k];
   S.src = static_cast<const uint8_t*>(I.src);
   S.dst = static_cast<uint8_t*>(I.dst);
   S.sp = I.src_pitch;
@@ -92,8 +93,9 @@ __device__ __forceinline__ void load_image(const BatchParams<MAXI>& P, int k, in
   S.nbx = I.nbx;
   S.nblk = I.nblk;
   S.tile0 = I.tile0;
-  S.tile_end = (k + 1 < P.nimg) ? P.img[k + 1].tile0 : P.ntiles;
+  S.tile_end = (k + 1 < nimg) ? imgs[k + 1].tile0 : ntiles;
   S.magic = I.div_magic;
+  S.out = I.out_index;
   S.quant = (I.flags & kQuantFlag) != 0;
   const int ev = scale_class(v);
   const float sv = ((kFwdNegMask >> v) & 1u) ? -1.f : 1.f;
@@ -142,10 +144,58 @@ __device__ __forceinline__ uint4 load_row(const uint8_t* base, int64_t pitch, in
                    : make_uint4(0, 0, 0, 0);
 }
 
-// Kernel template: MAXI images per launch, zone class Z, LEV = write levels,
-// DST = write reconstructed samples.
-template <int MAXI, class Z, bool LEV, bool DST>
-__global__ void __launch_bounds__(128, Z::kMinCtas) fused_u8_kernel(const __grid_constant__ BatchParams<MAXI> P) {
+// The image whose tile range holds tile t (binary search; tile0 ascending).
+__device__ __forceinline__ int image_of_tile(const ImgParam* imgs, int nimg, int t) {
+  int lo = 0, hi = nimg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (imgs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Tile schedules.  StaticRange: a contiguous range per CTA (grid sized to the
+// SMs).  Dynamic: CTAs take chunks of `chunk` tiles from a device counter of
+// the work list, the next chunk claimed one chunk ahead so prefetching never
+// stalls on the atomic.  Both are called uniformly by the whole CTA.
+struct StaticRange {
+  int t0, t1;
+  __device__ __forceinline__ int first() const { return t0 < t1 ? t0 : -1; }
+  __device__ __forceinline__ int next(int t) const { return t + 1 < t1 ? t + 1 : -1; }
+};
+
+struct DynamicChunks {
+  unsigned* counter;
+  int ntiles, chunk, cur_end, next_start;
+  int* slot;  // shared-memory broadcast slot
+  __device__ __forceinline__ int grab() {
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = int(atomicAdd(counter, unsigned(chunk)));
+    __syncthreads();
+    return *slot;
+  }
+  __device__ __forceinline__ int first() {
+    const int s = grab();
+    if (s >= ntiles) return -1;
+    cur_end = min(s + chunk, ntiles);
+    next_start = grab();
+    return s;
+  }
+  __device__ __forceinline__ int next(int t) {
+    if (t + 1 < cur_end) return t + 1;
+    const int s = next_start;
+    if (s >= ntiles) return -1;
+    cur_end = min(s + chunk, ntiles);
+    next_start = grab();
+    return s;
+  }
+};
+
+// The fused codec over the tiles a schedule hands out.  imgs: descriptors of
+// the launch (tile0 ascending), in parameter space or in a device work list.
+template <class Z, bool LEV, bool DST, class Sched>
+__device__ __forceinline__ void codec_tiles(const ImgParam* imgs, int nimg, int ntiles,
+                                            unsigned long long* sse, int* levels, Sched& sched) {
   // column slots: slot p*V + v holds column v of block pair p (16 float2)
   __shared__ __align__(16) float smem[8 * Z::V * kSlotWords];
   constexpr int kTasks = 8 * Z::V;  // column tasks per tile
@@ -156,53 +206,39 @@ __global__ void __launch_bounds__(128, Z::kMinCtas) fused_u8_kernel(const __grid
   const bool col_active = task < kTasks;
   const bool warp_has_cols = (task & ~31) < kTasks;
 
-  const int per = (P.ntiles + gridDim.x - 1) / gridDim.x;
-  const int t0 = blockIdx.x * per;
-  const int t1 = min(t0 + per, P.ntiles);
-  if (t0 >= t1) return;
-
-  int k = 0;
-  {
-    int hi = P.nimg - 1;
-    while (k < hi) {
-      const int mid = (k + hi + 1) >> 1;
-      if (P.img[mid].tile0 <= t0) k = mid; else hi = mid - 1;
-    }
-  }
+  int t = sched.first();
+  if (t < 0) return;
+  int k = image_of_tile(imgs, nimg, t);
   ImgState S;
-  load_image(P, k, tv, S);
+  load_image(imgs, nimg, ntiles, k, tv, S);
   unsigned long long acc = 0;
 
-  // rows of the current tile (prefetched one tile ahead) and their offsets
+  // rows of the current tile (prefetched one tile ahead) and their positions
   uint4 ra, rb;
   int2 pa_next, pb_next;
   {
-    const int base = (t0 - S.tile0) * kTileBlocks;
+    const int base = (t - S.tile0) * kTileBlocks;
     pa_next = row_pos(S.magic, S.nbx, S.nblk, base + p, l);
     pb_next = row_pos(S.magic, S.nbx, S.nblk, base + p + 8, l);
     ra = load_row(S.src, S.sp, pa_next);
     rb = load_row(S.src, S.sp, pb_next);
   }
 
-  for (int t = t0; t < t1; ++t) {
-    if (t >= S.tile_end) {  // uniform over the CTA: next image
-      if (P.sse) flush_sse(P.sse, k, acc);
+  while (t >= 0) {
+    const int tn = sched.next(t);  // uniform over the CTA
+    if (t < S.tile0 || t >= S.tile_end) {  // uniform: another image
+      if (sse) flush_sse(sse, S.out, acc);
       acc = 0;
-      do {
-        ++k;
-      } while (k + 1 < P.nimg && P.img[k + 1].tile0 <= t);
-      load_image(P, k, tv, S);
+      k = image_of_tile(imgs, nimg, t);
+      load_image(imgs, nimg, ntiles, k, tv, S);
     }
     const uint4 ca = ra, cb = rb;
     const int2 pa = pa_next, pb = pb_next;
-    // prefetch the next tile's rows (they may belong to the next image)
-    if (t + 1 < t1) {
-      int kn = k;
-      if (t + 1 >= S.tile_end) {
-        while (kn + 1 < P.nimg && P.img[kn + 1].tile0 <= t + 1) ++kn;
-      }
-      const ImgParam& In = P.img[kn];
-      const int base = (t + 1 - In.tile0) * kTileBlocks;
+    // prefetch the next tile's rows (they may belong to another image)
+    if (tn >= 0) {
+      const int kn = (tn >= S.tile0 && tn < S.tile_end) ? k : image_of_tile(imgs, nimg, tn);
+      const ImgParam& In = imgs[kn];
+      const int base = (tn - In.tile0) * kTileBlocks;
       pa_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p, l);
       pb_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p + 8, l);
       ra = load_row(static_cast<const uint8_t*>(In.src), In.src_pitch, pa_next);
@@ -223,7 +259,7 @@ __global__ void __launch_bounds__(128, Z::kMinCtas) fused_u8_kernel(const __grid
         *reinterpret_cast<float2*>(&smem[(p * Z::V + v) * kSlotWords + 2 * l]) = y[v];
       if (LEV) {  // columns v >= V hold no kept coefficient: level 0 (row l of both blocks)
         const int base = (t - S.tile0) * kTileBlocks;
-        int* ra_ = P.coeffs + (S.blk0 + base + p) * 256 + l * 16;
+        int* ra_ = levels + (S.blk0 + base + p) * 256 + l * 16;
 #pragma unroll
         for (int v = Z::V; v < 16; ++v) {
           if (pa.x >= 0) __stcs(ra_ + v, 0);
@@ -253,7 +289,7 @@ __global__ void __launch_bounds__(128, Z::kMinCtas) fused_u8_kernel(const __grid
       const int tbase = (t - S.tile0) * kTileBlocks;
       const bool tva = col_active && tbase + tp < S.nblk;
       const bool tvb = col_active && tbase + tp + 8 < S.nblk;
-      int* lev_a = LEV ? P.coeffs + (S.blk0 + tbase + tp) * 256 + tv : nullptr;
+      int* lev_a = LEV ? levels + (S.blk0 + tbase + tp) * 256 + tv : nullptr;
       int* lev_b = LEV ? lev_a + 8 * 256 : nullptr;
       if (S.quant) {
 #pragma unroll
@@ -359,8 +395,30 @@ __global__ void __launch_bounds__(128, Z::kMinCtas) fused_u8_kernel(const __grid
       }
       acc += (unsigned long long)(s1 - 2u * s2);
     }
+    t = tn;
   }
-  if (P.sse) flush_sse(P.sse, k, acc);
+  if (sse) flush_sse(sse, S.out, acc);
+}
+
+// By-value launch: descriptors in the kernel parameters, a static tile range
+// per CTA.  MAXI images per launch, zone class Z, LEV = write levels, DST =
+// write reconstructed samples.
+template <int MAXI, class Z, bool LEV, bool DST>
+__global__ void __launch_bounds__(128, Z::kMinCtas) fused_u8_kernel(const __grid_constant__ BatchParams<MAXI> P) {
+  const int per = (P.ntiles + gridDim.x - 1) / gridDim.x;
+  StaticRange sched{int(blockIdx.x) * per, min(int(blockIdx.x) * per + per, P.ntiles)};
+  codec_tiles<Z, LEV, DST>(P.img, P.nimg, P.ntiles, P.sse, P.coeffs, sched);
+}
+
+// Work-list launch: descriptors in device memory, tiles handed out in chunks
+// from a device counter (reset to 0 before the launch).
+template <class Z, bool LEV, bool DST>
+__global__ void __launch_bounds__(128, Z::kMinCtas)
+    fused_u8_list_kernel(const ImgParam* __restrict__ imgs, int nimg, int ntiles, unsigned* counter, int chunk,
+                         unsigned long long* sse, int* levels) {
+  __shared__ int slot;
+  DynamicChunks sched{counter, ntiles, chunk, 0, 0, &slot};
+  codec_tiles<Z, LEV, DST>(imgs, nimg, ntiles, sse, levels, sched);
 }
 
 template <int MAXI, class Z, bool LEV, bool DST>
@@ -374,6 +432,7 @@ tx16_status launch_fused(const ImgParam* imgs, int n, unsigned long long* sse, i
   for (int i = 0; i < n; ++i) {
     P.img[i] = imgs[i];
     P.img[i].tile0 = tiles;
+    P.img[i].out_index = i;
     tiles += (imgs[i].nblk + kTileBlocks - 1) / kTileBlocks;
   }
   P.ntiles = tiles;
@@ -417,7 +476,76 @@ tx16_status launch_fused_modes(int zone, const ImgParam* imgs, int n, unsigned l
              : launch_fused_zone<MAXI, false, false>(zone, imgs, n, sse, levels, stream);
 }
 
+template <class Z, bool LEV, bool DST>
+int list_max_ctas() {
+  static int occ = 0;
+  if (occ == 0) {
+    int o = 0;
+    cudaFuncSetAttribute(fused_u8_list_kernel<Z, LEV, DST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_u8_list_kernel<Z, LEV, DST>, 128, 0) !=
+            cudaSuccess || o < 1)
+      o = 1;
+    occ = o;
+  }
+  return occ;
+}
+
+template <class Z, bool LEV, bool DST>
+tx16_status launch_list(const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter, int chunk, int ctas_per_sm,
+                        unsigned long long* sse, int32_t* levels, cudaStream_t stream) {
+  const int occ = list_max_ctas<Z, LEV, DST>();
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  const int grid = std::max(1, std::min((ntiles + chunk - 1) / chunk, per_sm * device_sm_count()));
+  fused_u8_list_kernel<Z, LEV, DST><<<grid, 128, 0, stream>>>(d_imgs, nimg, ntiles, counter, chunk, sse, levels);
+  return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
+}
+
+template <class Z>
+tx16_status launch_list_modes(bool lev, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter,
+                              int chunk, int ctas_per_sm, unsigned long long* sse, int32_t* levels,
+                              cudaStream_t stream) {
+  if (lev)
+    return dst ? launch_list<Z, true, true>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream)
+               : launch_list<Z, true, false>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream);
+  return dst ? launch_list<Z, false, true>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream)
+             : launch_list<Z, false, false>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream);
+}
+
+template <class Z>
+int list_max_ctas_modes(bool lev, bool dst) {
+  if (lev) return dst ? list_max_ctas<Z, true, true>() : list_max_ctas<Z, true, false>();
+  return dst ? list_max_ctas<Z, false, true>() : list_max_ctas<Z, false, false>();
+}
+
 }  // namespace
+
+tx16_status launch_fused_list(int zone, bool lev, bool dst, const ImgParam* d_imgs, int nimg, int ntiles,
+                              unsigned* counter, int chunk, int ctas_per_sm, unsigned long long* sse,
+                              int32_t* levels, cudaStream_t stream) {
+  switch (zone) {
+    case 0: return launch_list_modes<ZoneA>(lev, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream);
+    case 1: return launch_list_modes<ZoneB>(lev, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream);
+    case 2: return launch_list_modes<ZoneC>(lev, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream);
+    case 3: return launch_list_modes<ZoneD>(lev, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream);
+    default: return launch_list_modes<ZoneE>(lev, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, levels, stream);
+  }
+}
+
+int fused_list_max_ctas(int zone, bool lev, bool dst) {
+  switch (zone) {
+    case 0: return list_max_ctas_modes<ZoneA>(lev, dst);
+    case 1: return list_max_ctas_modes<ZoneB>(lev, dst);
+    case 2: return list_max_ctas_modes<ZoneC>(lev, dst);
+    case 3: return list_max_ctas_modes<ZoneD>(lev, dst);
+    default: return list_max_ctas_modes<ZoneE>(lev, dst);
+  }
+}
+
+bool fused_eligible(const ImgParam& p) {
+  const int bits = p.flags & 0xff;
+  return bits == 8 && (!(p.flags & kQuantFlag) || p.g[0] * 16.0f >= kFusedMinQ);
+}
 
 // Smallest zone class covering every image of the launch (extents of Z_r).
 int fused_zone_class(const ImgParam* imgs, int n) {

@@ -25,8 +25,8 @@ struct ImgParam {
   int32_t nblk;        // blocks in the image
   int32_t tile0;       // first tile of this image within the launch
   int32_t flags;       // bits (low 8) | kQuantFlag
-  uint32_t div_magic;  // blk / nbx = (umulhi(blk, div_magic) >> div_shift), or one more
-  int32_t div_shift;
+  uint32_t div_magic;  // blk / nbx = umulhi(blk, div_magic), or one more
+  int32_t out_index;   // index of this image's SSE in the caller's sse[] array
   float f[5];          // fl32(sqrt2^k / (16 q)), k = e(u) + e(v)   (forward scale)
   float g[5];          // fl32(q sqrt2^k / 16)                      (inverse scale)
   uint8_t colh[16];    // kept rows of column v: |Z_r ∩ column v| (a prefix 0..colh-1)
@@ -60,6 +60,13 @@ constexpr float kFusedMinQ = 1.0f / 256.0f;
 tx16_status launch_fused_u8(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                             cudaStream_t stream);
 int fused_zone_class(const ImgParam* imgs, int n);
+bool fused_eligible(const ImgParam& p);  // 8-bit samples and q >= kFusedMinQ (or no q)
+// Work-list launch: descriptors in device memory (tile0 relative to the list,
+// ascending), tiles claimed `chunk` at a time from *counter (zeroed before).
+tx16_status launch_fused_list(int zone, bool lev, bool dst, const ImgParam* d_imgs, int nimg, int ntiles,
+                              unsigned* counter, int chunk, int ctas_per_sm, unsigned long long* sse,
+                              int32_t* levels, cudaStream_t stream);
+int fused_list_max_ctas(int zone, bool lev, bool dst);  // resident CTAs per SM
 
 // Launchers (tx16_codec.cu).  `imgs` points at `n` ImgParam already filled in
 // (except tile0, set here), all with the same sample size.

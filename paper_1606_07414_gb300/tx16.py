@@ -50,6 +50,15 @@ _SIGNATURES = {
                                 ctypes.c_void_p, ctypes.c_void_p]),
     "tx16_psnr": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(tx16_image),
                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "tx16_plan_create": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image), ctypes.c_int32,
+                                        ctypes.POINTER(tx16_qparams), ctypes.POINTER(ctypes.c_void_p)]),
+    "tx16_plan_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tx16_plan_run_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tx16_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]),
+    "tx16_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "tx16_plan_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -179,3 +188,57 @@ def tx16_psnr(sse_values: Sequence[int], imgs: Sequence) -> list[float]:
     out = (ctypes.c_double * max(1, n))()
     _check(lib.tx16_psnr(s, arr, n, out), "tx16_psnr")
     return [out[i] for i in range(n)]
+
+
+# ---------------------------------------------------------------------------
+# Batch plans
+# ---------------------------------------------------------------------------
+class Plan:
+    """A tx16_plan: device work list for one batch (see include/tx16.h).
+    Holds references to the descriptors' tensors so they outlive the plan."""
+
+    def __init__(self, inp: Sequence, out: Sequence | None, qp: Sequence[tuple[float, int]],
+                 bits: int | None = None):
+        lib = load()
+        self._keep = (list(inp), list(out) if out is not None else None)
+        h = ctypes.c_void_p()
+        out_arr = _images(out, bits) if out is not None else None
+        _check(lib.tx16_plan_create(_images(inp, bits), out_arr, len(inp), _qparams(qp), ctypes.byref(h)),
+               "tx16_plan_create")
+        self.handle = h
+        self.n = len(inp)
+
+    def run(self, sse=None, levels=None, stream=None) -> None:
+        _check(load().tx16_plan_run(self.handle, _ptr(sse), _ptr(levels), _stream(stream)), "tx16_plan_run")
+
+    def run_graph(self, sse=None, levels=None, stream=None) -> None:
+        _check(load().tx16_plan_run_graph(self.handle, _ptr(sse), _ptr(levels), _stream(stream)),
+               "tx16_plan_run_graph")
+
+    def autotune(self, cache_path: str | None = None, stream=None) -> None:
+        _check(load().tx16_plan_autotune(self.handle, cache_path.encode() if cache_path else None, _stream(stream)),
+               "tx16_plan_autotune")
+
+    def info(self) -> list[dict]:
+        lib = load()
+        n = ctypes.c_int32()
+        m = 8
+        z, t, c, k = [(ctypes.c_int32 * m)() for _ in range(4)]
+        _check(lib.tx16_plan_info(self.handle, ctypes.byref(n), z, t, c, k, m), "tx16_plan_info")
+        return [{"zone": z[i], "tiles": t[i], "ctas_per_sm": c[i], "chunk": k[i]} for i in range(min(n.value, m))]
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load().tx16_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def tx16_plan_create(inp: Sequence, out: Sequence | None, qp: Sequence[tuple[float, int]],
+                     bits: int | None = None) -> Plan:
+    return Plan(inp, out, qp, bits)
