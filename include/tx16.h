@@ -193,6 +193,42 @@ tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, 
 /* Free the plan's device memory and graph.  NULL is ignored. */
 void tx16_plan_destroy(tx16_plan* plan);
 
+/* ------------------------------------------------------------------------ */
+/* The work-list codec for callers that cannot allocate device memory        */
+/* ------------------------------------------------------------------------ */
+
+/* Largest batch tx16_codec_batch_static accepts. */
+#define TX16_STATIC_MAX_IMAGES 1024
+
+/*
+ * The same codec as tx16_codec_batch / tx16_plan_run (identical results), run
+ * by the work-list kernel, but allocating nothing: no cudaMalloc, no cudaFree,
+ * no allocating library call.  It is meant for callers that cannot allocate
+ * device memory when they run the codec: a process whose device memory all
+ * belongs to another allocator's pool, a latency-critical loop where an
+ * allocation would synchronise the device, or a service whose memory budget is
+ * fixed at start-up.  (This entry point is a property of this library; the
+ * paper has no counterpart.)
+ *
+ * The work list (image descriptors and tile counters) lives in one fixed
+ * device array inside the library, about 123 KB, which every GPU that loads
+ * the library holds until the process exits.  The caller still passes all
+ * inputs and outputs, with the arguments, layouts and errors of
+ * tx16_codec_batch, except:
+ *   - n may not exceed TX16_STATIC_MAX_IMAGES: larger batches return
+ *     TX16_EINVAL and launch nothing;
+ *   - every call uses the same array, which keeps the last call's contents:
+ *     each call rewrites the descriptors and clears the counters itself, but
+ *     two calls whose work overlaps on the GPU (different streams, or
+ *     different host threads without ordering) race on the array.  Order such
+ *     calls on one stream, or wait for one before issuing the next;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ *     first call before any stream capture.
+ */
+tx16_status tx16_codec_batch_static(const tx16_image* in, const tx16_image* out, int32_t n,
+                                    const tx16_qparams* qp, uint64_t* sse, int32_t* levels, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

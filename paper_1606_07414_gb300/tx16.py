@@ -59,7 +59,12 @@ _SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "tx16_plan_destroy": (None, [ctypes.c_void_p]),
+    "tx16_codec_batch_static": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image),
+                                               ctypes.c_int32, ctypes.POINTER(tx16_qparams), ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
 }
+
+TX16_STATIC_MAX_IMAGES = 1024
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
@@ -170,6 +175,17 @@ def tx16_codec_batch(inp: Sequence, out: Sequence | None, qp: Sequence[tuple[flo
     out_arr = _images(out, bits) if out is not None else None
     _check(lib.tx16_codec_batch(_images(inp, bits), out_arr, len(inp), _qparams(qp), _ptr(sse),
                                 _ptr(levels), _stream(stream)), "tx16_codec_batch")
+
+
+def tx16_codec_batch_static(inp: Sequence, out: Sequence | None, qp: Sequence[tuple[float, int]], sse=None,
+                            levels=None, stream=None, bits: int | None = None) -> None:
+    """tx16_codec_batch without any device allocation: for callers that cannot
+    allocate device memory where they run the codec.  At most
+    TX16_STATIC_MAX_IMAGES images; calls must not overlap on the GPU."""
+    lib = load()
+    out_arr = _images(out, bits) if out is not None else None
+    _check(lib.tx16_codec_batch_static(_images(inp, bits), out_arr, len(inp), _qparams(qp), _ptr(sse),
+                                       _ptr(levels), _stream(stream)), "tx16_codec_batch_static")
 
 
 def tx16_sse(a: Sequence, b: Sequence, sse, stream=None, bits: int | None = None) -> None:
