@@ -194,6 +194,60 @@ tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, 
 void tx16_plan_destroy(tx16_plan* plan);
 
 /* ------------------------------------------------------------------------ */
+/* Serving loop                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* A server codes requests (one image each, any size and bit depth accepted
+ * by tx16_codec_batch, each with its own quantiser; Sec. 3.1 codec) as they
+ * arrive.  A worker thread admits queued requests in arrival order while its
+ * device arena has room for their planes, launches each admitted group as ONE
+ * fused batch on one of several streams, and keeps admitting new requests
+ * while earlier groups run: continuous batching, copies of one group
+ * overlapping the kernel of another.  All device memory is allocated at
+ * creation.  (The serving loop is a property of this library; the paper
+ * codes images one at a time.) */
+typedef struct tx16_server tx16_server;
+
+/* json_cfg: NULL or a flat JSON object of numbers:
+ *   "device_pool_mb"  device arena for request planes (default: a quarter of
+ *                     the free HBM, at most 4096); fails with TX16_ENOMEM
+ *                     when it exceeds the free HBM
+ *   "streams"         groups in flight (default 3, 1..16)
+ *   "max_batch"       requests per group (default 256)
+ *   "max_queue"       queued requests before submit returns TX16_EBUSY
+ * The server uses the device current at creation. */
+tx16_status tx16_serve_create(const char* json_cfg, tx16_server** server);
+
+/* Queue one request: host_pixels (w x h samples, uint8 for bits = 8, uint16
+ * for 9..12, rows contiguous) must stay valid until the request is done;
+ * host_recon (same size) receives the reconstruction, or NULL.  Pinned host
+ * memory gives direct DMA.  *ticket identifies the request.
+ * Errors: TX16_EINVAL (shape, bits, qp), TX16_ENOMEM (larger than the arena:
+ * never admissible), TX16_EBUSY (queue full). */
+tx16_status tx16_serve_submit(tx16_server* server, const void* host_pixels, int32_t w, int32_t h, int32_t bits,
+                              tx16_qparams qp, void* host_recon, uint64_t* ticket);
+
+/* Wait up to timeout_ms for a request; on success the ticket is released and
+ * *psnr (dB, Sec. 3.1 PSNR) and *latency_us (submit to completion) are set
+ * (either may be NULL).  TX16_ETIMEOUT leaves the ticket valid. */
+tx16_status tx16_serve_wait(tx16_server* server, uint64_t ticket, int32_t timeout_ms, double* psnr,
+                            double* latency_us);
+
+/* Latency percentiles (microseconds, over a uniform reservoir of completed
+ * requests) and coded Mblocks/s from the first submit to the last
+ * completion since creation or the last reset. */
+tx16_status tx16_serve_stats(tx16_server* server, double* p50_us, double* p99_us, double* p999_us,
+                             double* mblocks_per_s);
+tx16_status tx16_serve_reset_stats(tx16_server* server);
+
+/* Hold (paused != 0) or resume admission; queued requests wait while held
+ * (for draining or maintenance).  Requests already admitted finish. */
+tx16_status tx16_serve_pause(tx16_server* server, int32_t paused);
+
+/* Finish admitted and queued work, then free everything.  NULL is ignored. */
+void tx16_serve_destroy(tx16_server* server);
+
+/* ------------------------------------------------------------------------ */
 /* The work-list codec for callers that cannot allocate device memory        */
 /* ------------------------------------------------------------------------ */
 

@@ -1,0 +1,492 @@
+// Serving loop (tx16_serve_*): requests of different sizes, each with its own
+// quantiser, coded by the fused batch kernels with continuous batching.
+//
+//  submit   validates the request, stamps its arrival time and queues it.
+//  worker   (one host thread) repeatedly
+//             - admits queued requests, in arrival order, while the device
+//               arena has room for their input and output planes and a batch
+//               slot is free ("admission by free HBM");
+//             - puts each admitted group on a free slot's stream: host->device
+//               copies of the inputs, ONE tx16_codec_batch launch over the
+//               group, device->host copies of the reconstructions and SSEs,
+//               then an event;
+//             - retires slots whose event has fired: PSNR, latency, frees the
+//               requests' arena space, wakes their waiters.
+//           Groups on different slots overlap on the GPU (copies of one with
+//           the kernel of another), and requests that arrive while others are
+//           in flight join the next group: the batch is never closed.
+//  wait     blocks (bounded) until a request is done.
+//
+// All device memory (the arena, per-slot SSE arrays) is allocated once at
+// creation; requests never allocate.  Host buffers are the caller's: the input
+// must stay valid until the request is done (pinned memory gives direct DMA).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tx16_internal.h"
+
+using Clock = std::chrono::steady_clock;
+using tx16::valid_image;
+
+namespace {
+
+// First-fit arena over one device allocation, 256-byte granules.
+class Arena {
+ public:
+  bool init(size_t bytes) {
+    if (cudaMalloc(&base_, bytes) != cudaSuccess) return false;
+    size_ = bytes;
+    free_[0] = bytes;
+    return true;
+  }
+  void release() {
+    if (base_) cudaFree(base_);
+    base_ = nullptr;
+  }
+  size_t capacity() const { return size_; }
+  char* alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first, len = it->second;
+        free_.erase(it);
+        if (len > bytes) free_[off + bytes] = len - bytes;
+        used_[off] = bytes;
+        return static_cast<char*>(base_) + off;
+      }
+    }
+    return nullptr;
+  }
+  void free(char* p) {
+    if (p == nullptr) return;
+    const size_t off = size_t(p - static_cast<char*>(base_));
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    auto it = free_.emplace(off, u->second).first;
+    used_.erase(u);
+    auto nx = std::next(it);  // merge with the following free range
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {  // and with the preceding one
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+ private:
+  void* base_ = nullptr;
+  size_t size_ = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+  std::map<size_t, size_t> used_;
+};
+
+struct Request {
+  uint64_t ticket;
+  const void* host_in;
+  void* host_out;  // may be null
+  int w, h, bits;
+  tx16_qparams qp;
+  size_t bytes;  // per plane
+  int64_t blocks;
+  Clock::time_point t_submit;
+  char* d_in = nullptr;
+  char* d_out = nullptr;
+  bool done = false;
+  tx16_status status = TX16_OK;
+  double psnr = 0.0;
+  double latency_us = 0.0;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t event = nullptr;
+  uint64_t* d_sse = nullptr;
+  uint64_t* h_sse = nullptr;  // pinned
+  std::vector<Request*> reqs;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct tx16_server {
+  int device = 0;
+  int max_batch = 256;
+  size_t max_queue = 1 << 20;
+  Arena arena;
+  std::vector<Slot> slots;
+  std::mutex mu;
+  std::condition_variable cv_work;  // worker: new requests / stop
+  std::condition_variable cv_done;  // waiters
+  std::deque<Request*> queue;
+  std::map<uint64_t, Request*> live;  // ticket -> request (until waited)
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  bool paused = false;  // admission held (tx16_serve_pause)
+  std::thread worker;
+  // statistics
+  std::vector<double> lat;  // reservoir of latencies (us)
+  size_t lat_seen = 0;
+  uint64_t rng = 0x9E3779B97F4A7C15ull;
+  double blocks_done = 0;
+  Clock::time_point t_first{}, t_last{};
+  bool any = false;
+  std::string error;
+};
+
+namespace {
+
+constexpr size_t kReservoir = 1 << 20;
+
+double now_us(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+// Parse a flat JSON object of numbers: {"key": 12.5, ...}.  Unknown keys are
+// ignored; returns false on malformed input.
+bool parse_cfg(const char* s, std::map<std::string, double>& out) {
+  if (s == nullptr || *s == 0) return true;
+  const char* p = s;
+  auto ws = [&] { while (*p == ' ' || *p == '\n' || *p == '\t' || *p == '\r') ++p; };
+  ws();
+  if (*p != '{') return false;
+  ++p;
+  for (;;) {
+    ws();
+    if (*p == '}') return true;
+    if (*p != '"') return false;
+    const char* k0 = ++p;
+    while (*p && *p != '"') ++p;
+    if (*p != '"') return false;
+    std::string key(k0, p - k0);
+    ++p;
+    ws();
+    if (*p != ':') return false;
+    ++p;
+    ws();
+    char* end = nullptr;
+    const double v = std::strtod(p, &end);
+    if (end == p) return false;
+    out[key] = v;
+    p = end;
+    ws();
+    if (*p == ',') {
+      ++p;
+      continue;
+    }
+    if (*p == '}') return true;
+    return false;
+  }
+}
+
+void record_latency(tx16_server* s, double us) {
+  ++s->lat_seen;
+  if (s->lat.size() < kReservoir) {
+    s->lat.push_back(us);
+  } else {  // reservoir sampling keeps a uniform sample of every latency seen
+    s->rng ^= s->rng << 13;
+    s->rng ^= s->rng >> 7;
+    s->rng ^= s->rng << 17;
+    const size_t j = size_t(s->rng % s->lat_seen);
+    if (j < kReservoir) s->lat[j] = us;
+  }
+}
+
+// Put one admitted group on a slot: copies in, one batched launch, copies out.
+tx16_status launch_group(tx16_server* s, Slot& slot) {
+  const int n = int(slot.reqs.size());
+  std::vector<tx16_image> in(n), out(n);
+  std::vector<tx16_qparams> qp(n);
+  for (int i = 0; i < n; ++i) {
+    Request* r = slot.reqs[i];
+    const int64_t pitch = int64_t(r->w) * (r->bits == 8 ? 1 : 2);
+    if (cudaMemcpyAsync(r->d_in, r->host_in, r->bytes, cudaMemcpyHostToDevice, slot.stream) != cudaSuccess)
+      return TX16_ECUDA;
+    in[i] = tx16_image{r->d_in, r->w, r->h, pitch, r->bits};
+    out[i] = tx16_image{r->d_out, r->w, r->h, pitch, r->bits};
+    qp[i] = r->qp;
+  }
+  const tx16_status st = tx16_codec_batch(in.data(), out.data(), n, qp.data(), slot.d_sse, nullptr, slot.stream);
+  if (st != TX16_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    Request* r = slot.reqs[i];
+    if (r->host_out != nullptr &&
+        cudaMemcpyAsync(r->host_out, r->d_out, r->bytes, cudaMemcpyDeviceToHost, slot.stream) != cudaSuccess)
+      return TX16_ECUDA;
+  }
+  if (cudaMemcpyAsync(slot.h_sse, slot.d_sse, sizeof(uint64_t) * size_t(n), cudaMemcpyDeviceToHost, slot.stream) !=
+          cudaSuccess ||
+      cudaEventRecord(slot.event, slot.stream) != cudaSuccess)
+    return TX16_ECUDA;
+  return TX16_OK;
+}
+
+void retire(tx16_server* s, Slot& slot, tx16_status st) {
+  const Clock::time_point t = Clock::now();
+  for (size_t i = 0; i < slot.reqs.size(); ++i) {
+    Request* r = slot.reqs[i];
+    r->status = st;
+    if (st == TX16_OK) {
+      tx16_image d{r->d_in, r->w, r->h, int64_t(r->w) * (r->bits == 8 ? 1 : 2), r->bits};
+      tx16_psnr(&slot.h_sse[i], &d, 1, &r->psnr);
+      s->blocks_done += double(r->blocks);
+    }
+    r->latency_us = now_us(r->t_submit, t);
+    record_latency(s, r->latency_us);
+    s->arena.free(r->d_in);
+    s->arena.free(r->d_out);
+    r->d_in = r->d_out = nullptr;
+    r->done = true;
+  }
+  s->t_last = t;
+  slot.reqs.clear();
+  slot.busy = false;
+}
+
+void worker_main(tx16_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    // retire finished groups
+    bool progressed = false;
+    for (Slot& slot : s->slots) {
+      if (!slot.busy) continue;
+      const cudaError_t q = cudaEventQuery(slot.event);
+      if (q == cudaErrorNotReady) continue;
+      retire(s, slot, q == cudaSuccess ? TX16_OK : TX16_ECUDA);
+      progressed = true;
+    }
+    if (progressed) s->cv_done.notify_all();
+    // admit and launch: one group per free slot
+    for (Slot& slot : s->slots) {
+      if (slot.busy || s->queue.empty() || s->paused) continue;
+      while (!s->queue.empty() && int(slot.reqs.size()) < s->max_batch) {
+        Request* r = s->queue.front();
+        r->d_in = s->arena.alloc(r->bytes);
+        r->d_out = r->d_in ? s->arena.alloc(r->bytes) : nullptr;
+        if (r->d_out == nullptr) {  // no room now: wait for a group to retire
+          s->arena.free(r->d_in);
+          r->d_in = nullptr;
+          break;
+        }
+        s->queue.pop_front();
+        slot.reqs.push_back(r);
+      }
+      if (slot.reqs.empty()) break;
+      slot.busy = true;
+      // issue copies and the launch without holding the lock (submit stays cheap)
+      lk.unlock();
+      const tx16_status st = launch_group(s, slot);
+      if (st != TX16_OK) cudaStreamSynchronize(slot.stream);
+      lk.lock();
+      if (st != TX16_OK) {
+        retire(s, slot, st);
+        s->cv_done.notify_all();
+      }
+      progressed = true;
+    }
+    const bool inflight = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot& x) { return x.busy; });
+    if (s->stop && s->queue.empty() && !inflight) break;
+    if (!progressed) {
+      if (inflight) {
+        // poll the in-flight events without holding the lock
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
+      } else {
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
+  if (out == nullptr) return TX16_EINVAL;
+  *out = nullptr;
+  std::map<std::string, double> cfg;
+  if (!parse_cfg(json_cfg, cfg)) return TX16_EINVAL;
+  tx16_server* s = new tx16_server();
+  cudaGetDevice(&s->device);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    delete s;
+    return TX16_ECUDA;
+  }
+  const double pool_mb = cfg.count("device_pool_mb") ? cfg["device_pool_mb"]
+                                                      : std::min(4096.0, double(free_b) / 4.0 / (1 << 20));
+  const int nslots = cfg.count("streams") ? int(cfg["streams"]) : 3;
+  s->max_batch = cfg.count("max_batch") ? int(cfg["max_batch"]) : 256;
+  s->max_queue = cfg.count("max_queue") ? size_t(cfg["max_queue"]) : size_t(1) << 20;
+  const size_t pool = size_t(pool_mb * (1 << 20));
+  if (pool < 4096 || nslots < 1 || nslots > 16 || s->max_batch < 1 || s->max_batch > 4096 || s->max_queue < 1) {
+    delete s;
+    return TX16_EINVAL;
+  }
+  if (pool > free_b || !s->arena.init(pool)) {  // admission is bounded by free HBM
+    delete s;
+    return TX16_ENOMEM;
+  }
+  s->slots.resize(nslots);
+  for (Slot& slot : s->slots) {
+    if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&slot.event, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&slot.d_sse, sizeof(uint64_t) * size_t(s->max_batch)) != cudaSuccess ||
+        cudaMallocHost(&slot.h_sse, sizeof(uint64_t) * size_t(s->max_batch)) != cudaSuccess) {
+      tx16_serve_destroy(s);
+      return TX16_ENOMEM;
+    }
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return TX16_OK;
+}
+
+tx16_status tx16_serve_submit(tx16_server* s, const void* host_pixels, int32_t w, int32_t h, int32_t bits,
+                              tx16_qparams qp, void* host_recon, uint64_t* ticket) {
+  if (s == nullptr || host_pixels == nullptr || ticket == nullptr) return TX16_EINVAL;
+  tx16_image probe{const_cast<void*>(host_pixels), w, h, int64_t(w) * (bits == 8 ? 1 : 2), bits};
+  if ((reinterpret_cast<uintptr_t>(host_pixels) & 15u) != 0) probe.data = reinterpret_cast<void*>(16);
+  if (!valid_image(probe) || qp.r < 1 || qp.r > 256 || !std::isfinite(qp.q)) return TX16_EINVAL;
+  const size_t bytes = size_t(w) * size_t(h) * (bits == 8 ? 1 : 2);
+  if (2 * ((bytes + 255) & ~size_t(255)) > s->arena.capacity()) return TX16_ENOMEM;  // can never be admitted
+  Request* r = new Request();
+  r->host_in = host_pixels;
+  r->host_out = host_recon;
+  r->w = w;
+  r->h = h;
+  r->bits = bits;
+  r->qp = qp;
+  r->bytes = bytes;
+  r->blocks = int64_t(w / 16) * (h / 16);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      delete r;
+      return TX16_EINVAL;
+    }
+    if (s->queue.size() >= s->max_queue) {
+      delete r;
+      return TX16_EBUSY;
+    }
+    r->ticket = s->next_ticket++;
+    r->t_submit = Clock::now();
+    if (!s->any) {
+      s->t_first = r->t_submit;
+      s->any = true;
+    }
+    s->queue.push_back(r);
+    s->live[r->ticket] = r;
+    *ticket = r->ticket;
+  }
+  s->cv_work.notify_one();
+  return TX16_OK;
+}
+
+tx16_status tx16_serve_wait(tx16_server* s, uint64_t ticket, int32_t timeout_ms, double* psnr, double* latency_us) {
+  if (s == nullptr) return TX16_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->live.find(ticket);
+  if (it == s->live.end()) return TX16_EINVAL;
+  Request* r = it->second;
+  const auto deadline = Clock::now() + std::chrono::milliseconds(std::max(0, timeout_ms));
+  while (!r->done) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !r->done) return TX16_ETIMEOUT;
+  }
+  if (psnr) *psnr = r->psnr;
+  if (latency_us) *latency_us = r->latency_us;
+  const tx16_status st = r->status;
+  s->live.erase(it);
+  delete r;
+  return st;
+}
+
+tx16_status tx16_serve_stats(tx16_server* s, double* p50_us, double* p99_us, double* p999_us,
+                             double* mblocks_per_s) {
+  if (s == nullptr) return TX16_EINVAL;
+  std::vector<double> v;
+  double blocks = 0, span = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    v = s->lat;
+    blocks = s->blocks_done;
+    span = s->any ? now_us(s->t_first, s->t_last) : 0.0;
+  }
+  auto pct = [&](double f) {
+    if (v.empty()) return 0.0;
+    size_t k = std::min(v.size() - 1, size_t(f * double(v.size())));
+    std::nth_element(v.begin(), v.begin() + long(k), v.end());
+    return v[k];
+  };
+  if (p50_us) *p50_us = pct(0.50);
+  if (p99_us) *p99_us = pct(0.99);
+  if (p999_us) *p999_us = pct(0.999);
+  if (mblocks_per_s) *mblocks_per_s = span > 0 ? blocks / span : 0.0;  // blocks per us = Mblocks/s
+  return TX16_OK;
+}
+
+tx16_status tx16_serve_pause(tx16_server* s, int32_t paused) {
+  if (s == nullptr) return TX16_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv_work.notify_all();
+  return TX16_OK;
+}
+
+tx16_status tx16_serve_reset_stats(tx16_server* s) {
+  if (s == nullptr) return TX16_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat.clear();
+  s->lat_seen = 0;
+  s->blocks_done = 0;
+  s->any = false;
+  return TX16_OK;
+}
+
+void tx16_serve_destroy(tx16_server* s) {
+  if (s == nullptr) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = false;  // let queued work drain
+  }
+  if (s->worker.joinable()) s->worker.join();
+  for (Slot& slot : s->slots) {
+    if (slot.stream) cudaStreamSynchronize(slot.stream);
+    if (slot.event) cudaEventDestroy(slot.event);
+    if (slot.stream) cudaStreamDestroy(slot.stream);
+    if (slot.d_sse) cudaFree(slot.d_sse);
+    if (slot.h_sse) cudaFreeHost(slot.h_sse);
+  }
+  for (auto& kv : s->live) delete kv.second;
+  s->arena.release();
+  delete s;
+}
+
+}  // extern "C"

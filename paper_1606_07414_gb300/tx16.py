@@ -59,6 +59,16 @@ _SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "tx16_plan_destroy": (None, [ctypes.c_void_p]),
+    "tx16_serve_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "tx16_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, tx16_qparams, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "tx16_serve_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "tx16_serve_stats": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 4),
+    "tx16_serve_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "tx16_serve_pause": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "tx16_serve_destroy": (None, [ctypes.c_void_p]),
     "tx16_codec_batch_static": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image),
                                                ctypes.c_int32, ctypes.POINTER(tx16_qparams), ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
@@ -258,3 +268,72 @@ class Plan:
 def tx16_plan_create(inp: Sequence, out: Sequence | None, qp: Sequence[tuple[float, int]],
                      bits: int | None = None) -> Plan:
     return Plan(inp, out, qp, bits)
+
+
+# ---------------------------------------------------------------------------
+# Serving loop
+# ---------------------------------------------------------------------------
+class Server:
+    """tx16_server: continuous-batching request loop (see include/tx16.h).
+    Host buffers must be numpy arrays (pinned memory through torch is faster);
+    a request's input must stay alive until its wait() returns."""
+
+    def __init__(self, cfg: dict | None = None):
+        import json
+
+        h = ctypes.c_void_p()
+        _check(load().tx16_serve_create(json.dumps(cfg).encode() if cfg else None, ctypes.byref(h)),
+               "tx16_serve_create")
+        self.handle = h
+        self._inflight = {}
+
+    def submit_ptr(self, in_ptr: int, w: int, h: int, bits: int, q, r: int, out_ptr: int = 0) -> int:
+        t = ctypes.c_uint64()
+        st = load().tx16_serve_submit(self.handle, ctypes.c_void_p(in_ptr), w, h, bits,
+                                      tx16_qparams(0.0 if q is None else float(q), int(r)),
+                                      ctypes.c_void_p(out_ptr), ctypes.byref(t))
+        _check(st, "tx16_serve_submit")
+        return t.value
+
+    def submit(self, pixels, q, r: int, out=None, bits: int | None = None) -> int:
+        """pixels/out: 2-D numpy arrays or CPU torch tensors (uint8, or uint16/int16 storage)."""
+        h, w = pixels.shape[:2]
+        esz = pixels.itemsize if hasattr(pixels, "itemsize") else pixels.element_size()
+        bits = bits or (8 if esz == 1 else 10)
+        ip = pixels.ctypes.data if hasattr(pixels, "ctypes") else pixels.data_ptr()
+        op = 0 if out is None else (out.ctypes.data if hasattr(out, "ctypes") else out.data_ptr())
+        t = self.submit_ptr(ip, w, h, bits, q, r, op)
+        self._inflight[t] = (pixels, out)
+        return t
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> tuple[float, float]:
+        p = ctypes.c_double()
+        lat = ctypes.c_double()
+        st = load().tx16_serve_wait(self.handle, ticket, timeout_ms, ctypes.byref(p), ctypes.byref(lat))
+        if st != TX16_ETIMEOUT:
+            self._inflight.pop(ticket, None)
+        _check(st, "tx16_serve_wait")
+        return p.value, lat.value
+
+    def stats(self) -> dict:
+        v = [ctypes.c_double() for _ in range(4)]
+        _check(load().tx16_serve_stats(self.handle, *[ctypes.byref(x) for x in v]), "tx16_serve_stats")
+        return {"p50_us": v[0].value, "p99_us": v[1].value, "p999_us": v[2].value, "mblocks_per_s": v[3].value}
+
+    def reset_stats(self) -> None:
+        _check(load().tx16_serve_reset_stats(self.handle), "tx16_serve_reset_stats")
+
+    def pause(self, paused: bool = True) -> None:
+        _check(load().tx16_serve_pause(self.handle, 1 if paused else 0), "tx16_serve_pause")
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load().tx16_serve_destroy(self.handle)
+            self.handle = None
+            self._inflight.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass

@@ -106,3 +106,11 @@ def test_psnr_matches_oracle(lib):
     want = [O.psnr(123456, 512, 512, 8), O.psnr(2048, 32, 64, 10), math.inf]
     for g, w in zip(got, want):
         assert g == pytest.approx(w, rel=1e-15) if math.isfinite(w) else g == w
+
+
+def test_serve_create_rejects_malformed_config_before_any_device_call(lib):
+    import ctypes
+
+    h = ctypes.c_void_p()
+    for bad in (b"{", b"[1]", b'{"streams": }', b'{"streams" 3}', b'{streams: 3}'):
+        assert lib.tx16_serve_create(bad, ctypes.byref(h)) == 1  # TX16_EINVAL
