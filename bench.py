@@ -247,6 +247,30 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                   "ms_per_step": round(e2e_ms, 4), "pipeline": f"{FRAMES // chunk} chunks of {chunk} frames, "
                                                                "copy streams overlapping the kernel"}
 
+    # -- end to end with the kernel reading and writing the pinned host planes
+    #    directly (mapped memory over the CPU-GPU link: no staging copies)
+    hin = (tx16.tx16_image * FRAMES)(*[tx16.tx16_image(h_in[i].data_ptr(), W, H, W, 8) for i in range(FRAMES)])
+    hout = (tx16.tx16_image * FRAMES)(*[tx16.tx16_image(h_out[i].data_ptr(), W, H, W, 8) for i in range(FRAMES)])
+
+    def zc_step():
+        st = lib.tx16_codec_batch(hin, hout, FRAMES, qp, ctypes.c_void_p(sse_ptr), None, sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_codec_batch")
+        h_sse.copy_(d_sse, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(2):
+        zc_step()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        zc_step()
+    zc_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    out["e2e_zero_copy"] = {"value": round(blocks / (zc_ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                            "h2d_bytes_per_step": h_in.numel(), "d2h_bytes_per_step": h_out.numel() + 8 * FRAMES,
+                            "ms_per_step": round(zc_ms, 4),
+                            "pipeline": "one launch; the kernel loads the pinned host frames and stores the "
+                                        "reconstruction into pinned host memory over the CPU-GPU link"}
+
     # -- q x r sweep of the fused kernel (the workload's full parameter grid)
     sweep = []
     for q in (8.0, 16.0, 32.0):
@@ -318,10 +342,172 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                                                   "GB_s": round(gb / (ms_p * 1e-3), 1)}}
     del co2, imgs2
 
+    # -- uneven-size batch (2000 images, sides 64..4096): plan vs per-image launches
+    if not args.no_uneven:
+        out["uneven_batch"] = _uneven_batch(lib, tx16, torch, np, stream, sptr, peak)
+
+    # -- serving: Poisson arrivals, continuous batching vs one request at a time
+    if not args.no_serve:
+        out["serving"] = _serving(tx16, torch, np, args)
+
     # -- CPU baseline: the oracle on a bounded sample, all host cores
     if not args.no_cpu:
         frames_np = h_in[: args.cpu_frames].numpy()
         out["cpu_baseline"] = cpu_oracle_rate(frames_np, args.q, args.r)
+    return out
+
+
+def _gen_field(job):
+    seed, n, rho = job
+    from paper_1606_07414_gb300 import synth
+
+    return synth.ar1_image(seed, n, n, rho)
+
+
+def _uneven_batch(lib, tx16, torch, np, stream, sptr, peak):
+    """2000 images with sides drawn independently from the multiples of 16 in
+    [64, 4096], zonal r drawn from {8, 32, 128}, q = 16.  Inputs are crops of
+    10 seeded 4096 x 4096 AR(1) fields (rho 0.80 .. 0.98), so many images
+    re-read the same field: part of the input traffic is served by L2."""
+    import multiprocessing as mp
+    from paper_1606_07414_gb300 import synth
+
+    n, side, nb = 2000, 4096, 10
+    rhos = [0.80 + 0.02 * i for i in range(nb)]
+    with mp.get_context("spawn").Pool(min(nb, os.cpu_count() or 1)) as pool:
+        bases = pool.map(_gen_field, [(SEED + 700 + i, side, rhos[i]) for i in range(nb)])
+    d_bases = [torch.from_numpy(b).cuda() for b in bases]
+    Hs, Ws = synth.uneven_sizes(SEED + 9, n)
+    rs = synth.choice(SEED + 10, n, [8, 32, 128])
+    u = synth.uniforms(SEED + 11, 2 * n)
+    total = int(np.sum(Hs.astype(np.int64) * Ws))
+    d_out = torch.empty(total, dtype=torch.uint8, device="cuda")
+    ins = (tx16.tx16_image * n)()
+    outs = (tx16.tx16_image * n)()
+    qp = (tx16.tx16_qparams * n)()
+    off = 0
+    for i in range(n):
+        H, W = int(Hs[i]), int(Ws[i])
+        base = d_bases[i % nb]
+        oy = int(u[2 * i] * (side - H + 1))
+        ox = int(u[2 * i + 1] * ((side - W) // 16 + 1)) * 16
+        ins[i] = tx16.tx16_image(base.data_ptr() + oy * side + ox, W, H, side, 8)
+        outs[i] = tx16.tx16_image(d_out.data_ptr() + off, W, H, W, 8)
+        off += H * W
+        qp[i] = tx16.tx16_qparams(16.0, int(rs[i]))
+    blocks = total // 256
+    sse = torch.zeros(n, dtype=torch.int64, device="cuda")
+    plan = tx16.Plan(list(ins), list(outs), [(16.0, int(r)) for r in rs])
+    plan.autotune(None)
+    res = {"workload": f"{n} images, sides uniform over multiples of 16 in [64, 4096], r in {{8, 32, 128}}, "
+                       f"q = 16, crops of {nb} AR(1) fields 4096^2 (rho 0.80..0.98)",
+           "blocks": blocks, "schedule": plan.info()}
+
+    def run_graph():
+        plan.run_graph(sse=sse, stream=stream)
+
+    def run_batch():
+        lib.tx16_codec_batch(ins, outs, n, qp, ctypes.c_void_p(sse.data_ptr()), None, sptr)
+
+    def run_per_image():
+        for i in range(n):
+            lib.tx16_codec_batch(_at(ins, i), _at(outs, i), 1, _at(qp, i),
+                                 ctypes.c_void_p(sse.data_ptr() + 8 * i), None, sptr)
+    for name, f, k in (("plan_graph", run_graph, 10), ("codec_batch", run_batch, 10),
+                       ("per_image_launches", run_per_image, 3)):
+        for _ in range(2):
+            f()
+        ms = _events_time(f, k, stream)
+        res[name] = {"Mblocks_s": round(blocks / (ms * 1e-3) / 1e6, 1), "ms": round(ms, 3),
+                     "GB_s": round(blocks * BYTES_PER_BLOCK_CODEC / (ms * 1e-3) / 1e9, 1)}
+    plan.close()
+    del d_out, d_bases
+    return res
+
+
+def _serving(tx16, torch, np, args):
+    """Poisson request streams: 60 % 256 x 256 8-bit, 30 % 1920 x 1088 8-bit,
+    10 % 3840 x 2160 10-bit (uint16), q from {8, 16, 32}, r from {4, 16, 64,
+    256} per request; pinned host buffers.  The server's continuous batching
+    against the plain form that codes one request at a time as it arrives."""
+    from paper_1606_07414_gb300 import synth
+
+    kinds = [(256, 256, 8), (1088, 1920, 8), (2160, 3840, 10)]
+    pools = []
+    for ki, (H, W, bits) in enumerate(kinds):
+        k = 8 if ki < 2 else 3
+        src = synth.video_frames(SEED + 50 + ki, k, H, W, bits=bits)
+        dt = torch.uint8 if bits == 8 else torch.int16
+        ins = [torch.from_numpy(f.view(np.int16) if bits > 8 else f).pin_memory() for f in src]
+        outs = [torch.empty_like(t).pin_memory() for t in ins]
+        pools.append((H, W, bits, ins, outs))
+    srv = tx16.Server({"device_pool_mb": 16384, "streams": 3, "max_batch": 256})
+    rates = [int(x) for x in args.serve_rates.split(",")]
+    out = {"workload": "Poisson arrivals; 60% 256x256 u8, 30% 1920x1088 u8, 10% 3840x2160 10-bit; "
+                       "q in {8,16,32}, r in {4,16,64,256}; pinned host buffers", "rates": []}
+    for rate in rates:
+        n = max(200, min(int(rate * args.serve_seconds), 60000))
+        u = synth.uniforms(SEED + rate, 4 * n)
+        gaps = -np.log(u[:n]) / rate
+        kind = np.where(u[n:2 * n] < 0.6, 0, np.where(u[n:2 * n] < 0.9, 1, 2))
+        qs = np.array([8.0, 16.0, 32.0])[np.minimum((u[2 * n:3 * n] * 3).astype(int), 2)]
+        rs = np.array([4, 16, 64, 256])[np.minimum((u[3 * n:] * 4).astype(int), 3)]
+        reqs = []
+        for i in range(n):
+            H, W, bits, ins, outs = pools[kind[i]]
+            j = i % len(ins)
+            reqs.append((ins[j].data_ptr(), outs[j].data_ptr(), W, H, bits, float(qs[i]), int(rs[i]), H * W))
+        blocks = sum(r[7] for r in reqs) / 256
+        # continuous batching
+        srv.reset_stats()
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for i, (ip, op, W, H, bits, q, r, _) in enumerate(reqs):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            tickets.append(srv.submit_ptr(ip, W, H, bits, q, r, op))
+        for t in tickets:
+            srv.wait(t)
+        st = srv.stats()
+        achieved = n / (time.perf_counter() - t0)
+        line = {"rate": rate, "requests": n, "offered_Mblocks_s": round(blocks * rate / n / 1e6, 1),
+                "batched": {"p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+                            "p999_us": round(st["p999_us"], 1), "Mblocks_s": round(st["mblocks_per_s"], 1),
+                            "req_per_s": round(achieved, 1)}}
+        # the plain form: each request coded alone (copy in, one launch, copy out) as it arrives
+        m = min(n, max(200, int(rate * 0.5)))
+        dev_in = {k: torch.empty((H, W), dtype=torch.uint8 if b == 8 else torch.int16, device="cuda")
+                  for k, (H, W, b) in enumerate(kinds)}
+        dev_out = {k: torch.empty_like(v) for k, v in dev_in.items()}
+        sse = torch.zeros(1, dtype=torch.int64, device="cuda")
+        lat = []
+        t0 = time.perf_counter()
+        due = t0
+        done_blocks = 0
+        for i in range(m):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            H, W, bits, ins, outs = pools[kind[i]]
+            j = i % len(ins)
+            di, do = dev_in[kind[i]], dev_out[kind[i]]
+            di.copy_(ins[j], non_blocking=True)
+            tx16.tx16_codec_batch([tx16.image(di, bits)], [tx16.image(do, bits)], [(float(qs[i]), int(rs[i]))],
+                                  sse=sse)
+            outs[j].copy_(do, non_blocking=True)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - due) * 1e6)
+            done_blocks += H * W / 256
+        span = time.perf_counter() - t0
+        lat = np.sort(np.array(lat))
+        line["plain_per_request"] = {"requests": m, "p50_us": round(float(np.percentile(lat, 50)), 1),
+                                     "p99_us": round(float(np.percentile(lat, 99)), 1),
+                                     "p999_us": round(float(np.percentile(lat, 99.9)), 1),
+                                     "Mblocks_s": round(done_blocks / span / 1e6, 1)}
+        out["rates"].append(line)
+    srv.close()
     return out
 
 
@@ -367,8 +553,9 @@ def run_reference(args):
     rank, _, world = _env_rank()
     if rank != 0:
         return
-    frames = synth.video_frames(SEED, args.cpu_frames, H, W, rho=0.95)
     cores = os.cpu_count() or 1
+    # one frame per host core per step keeps any --steps K run to ~0.3 s a step
+    frames = synth.video_frames(SEED, cores, H, W, rho=0.95)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
     pool = mp.get_context("spawn").Pool(cores)
@@ -389,8 +576,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64", "data": "synthetic",
             "config": _workload(args.q, args.r), "impl": "reference",
             "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step: {len(frames)} frames of the workload through the float64 "
-                                       f"oracle on {cores} single-threaded processes"},
+                             "sample": f"each step: {len(frames)} of the workload's frames (one per core) through "
+                                       f"the float64 oracle on {cores} single-threaded processes"},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -433,8 +620,12 @@ def main():
     ap.add_argument("--impl", default="tx16", choices=["tx16", "reference"])
     ap.add_argument("--q", type=float, default=16.0)
     ap.add_argument("--r", type=int, default=16)
-    ap.add_argument("--cpu-frames", type=int, default=32)
+    ap.add_argument("--cpu-frames", type=int, default=96)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rates", default="1000,5000,20000,50000")
+    ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--quick", action="store_true", help="headline number only")
     ap.add_argument("--frames", type=int, default=FRAMES, help="smaller cases for profiling")
     args = ap.parse_args()

@@ -122,6 +122,9 @@ struct Slot {
   uint64_t* h_sse = nullptr;  // pinned
   std::vector<Request*> reqs;
   bool busy = false;
+  bool finished = false;  // set by the stream's host callback
+  Clock::time_point t_finished;
+  struct tx16_server* server = nullptr;
 };
 
 }  // namespace
@@ -209,6 +212,20 @@ void record_latency(tx16_server* s, double us) {
   }
 }
 
+// Runs on the CUDA runtime's callback thread when a slot's stream has passed
+// its last copy: stamps the completion time and wakes the worker (no CUDA
+// calls are allowed here).
+void CUDART_CB slot_done(void* arg) {
+  Slot* slot = static_cast<Slot*>(arg);
+  tx16_server* s = slot->server;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    slot->finished = true;
+    slot->t_finished = Clock::now();
+  }
+  s->cv_work.notify_one();
+}
+
 // Put one admitted group on a slot: copies in, one batched launch, copies out.
 tx16_status launch_group(tx16_server* s, Slot& slot) {
   const int n = int(slot.reqs.size());
@@ -233,13 +250,14 @@ tx16_status launch_group(tx16_server* s, Slot& slot) {
   }
   if (cudaMemcpyAsync(slot.h_sse, slot.d_sse, sizeof(uint64_t) * size_t(n), cudaMemcpyDeviceToHost, slot.stream) !=
           cudaSuccess ||
-      cudaEventRecord(slot.event, slot.stream) != cudaSuccess)
+      cudaEventRecord(slot.event, slot.stream) != cudaSuccess ||
+      cudaLaunchHostFunc(slot.stream, slot_done, &slot) != cudaSuccess)
     return TX16_ECUDA;
   return TX16_OK;
 }
 
 void retire(tx16_server* s, Slot& slot, tx16_status st) {
-  const Clock::time_point t = Clock::now();
+  const Clock::time_point t = slot.finished ? slot.t_finished : Clock::now();
   for (size_t i = 0; i < slot.reqs.size(); ++i) {
     Request* r = slot.reqs[i];
     r->status = st;
@@ -258,19 +276,19 @@ void retire(tx16_server* s, Slot& slot, tx16_status st) {
   s->t_last = t;
   slot.reqs.clear();
   slot.busy = false;
+  slot.finished = false;
 }
 
 void worker_main(tx16_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    // retire finished groups
+    // retire groups whose host callback has fired
     bool progressed = false;
     for (Slot& slot : s->slots) {
-      if (!slot.busy) continue;
-      const cudaError_t q = cudaEventQuery(slot.event);
-      if (q == cudaErrorNotReady) continue;
-      retire(s, slot, q == cudaSuccess ? TX16_OK : TX16_ECUDA);
+      if (!slot.busy || !slot.finished) continue;
+      const cudaError_t q = cudaEventQuery(slot.event);  // reports an error of the group's work
+      retire(s, slot, (q == cudaSuccess || q == cudaErrorNotReady) ? TX16_OK : TX16_ECUDA);
       progressed = true;
     }
     if (progressed) s->cv_done.notify_all();
@@ -291,6 +309,7 @@ void worker_main(tx16_server* s) {
       }
       if (slot.reqs.empty()) break;
       slot.busy = true;
+      slot.finished = false;
       // issue copies and the launch without holding the lock (submit stays cheap)
       lk.unlock();
       const tx16_status st = launch_group(s, slot);
@@ -305,14 +324,8 @@ void worker_main(tx16_server* s) {
     const bool inflight = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot& x) { return x.busy; });
     if (s->stop && s->queue.empty() && !inflight) break;
     if (!progressed) {
-      if (inflight) {
-        // poll the in-flight events without holding the lock
-        lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
-        lk.lock();
-      } else {
-        s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
-      }
+      // sleep until a callback, a submit, a resume or stop (bounded: re-check)
+      s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
     }
   }
 }
@@ -349,6 +362,7 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
   }
   s->slots.resize(nslots);
   for (Slot& slot : s->slots) {
+    slot.server = s;
     if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&slot.event, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&slot.d_sse, sizeof(uint64_t) * size_t(s->max_batch)) != cudaSuccess ||
