@@ -213,8 +213,10 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
     ClassRun& r = plan->runs[i];
     if (r.zone < 0) continue;
     const int bucket = int(std::log2(double(std::max(1, r.ntiles))));
+    std::string dev(prop.name);
+    std::replace(dev.begin(), dev.end(), ' ', '_');  // keys are single words in the cache file
     char key[320];
-    std::snprintf(key, sizeof key, "%s|%d|%d|%d", prop.name, r.zone, int(plan->has_dst), bucket);
+    std::snprintf(key, sizeof key, "%s|%d|%d|%d", dev.c_str(), r.zone, int(plan->has_dst), bucket);
     bool hit = false;
     for (const std::string& c : cache) {
       int ctas = 0, chunk = 0;
