@@ -236,13 +236,20 @@ __device__ __forceinline__ void codec_tiles(const ImgParam* imgs, int nimg, int 
     const int2 pa = pa_next, pb = pb_next;
     // prefetch the next tile's rows (they may belong to another image)
     if (tn >= 0) {
-      const int kn = (tn >= S.tile0 && tn < S.tile_end) ? k : image_of_tile(imgs, nimg, tn);
-      const ImgParam& In = imgs[kn];
-      const int base = (tn - In.tile0) * kTileBlocks;
-      pa_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p, l);
-      pb_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p + 8, l);
-      ra = load_row(static_cast<const uint8_t*>(In.src), In.src_pitch, pa_next);
-      rb = load_row(static_cast<const uint8_t*>(In.src), In.src_pitch, pb_next);
+      if (tn >= S.tile0 && tn < S.tile_end) {  // same image: everything is in registers
+        const int base = (tn - S.tile0) * kTileBlocks;
+        pa_next = row_pos(S.magic, S.nbx, S.nblk, base + p, l);
+        pb_next = row_pos(S.magic, S.nbx, S.nblk, base + p + 8, l);
+        ra = load_row(S.src, S.sp, pa_next);
+        rb = load_row(S.src, S.sp, pb_next);
+      } else {  // uniform: the next tile starts another image
+        const ImgParam& In = imgs[image_of_tile(imgs, nimg, tn)];
+        const int base = (tn - In.tile0) * kTileBlocks;
+        pa_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p, l);
+        pb_next = row_pos(In.div_magic, In.nbx, In.nblk, base + p + 8, l);
+        ra = load_row(static_cast<const uint8_t*>(In.src), In.src_pitch, pa_next);
+        rb = load_row(static_cast<const uint8_t*>(In.src), In.src_pitch, pb_next);
+      }
     }
 
     // ---- row phase: forward transform of row l of both blocks ----
