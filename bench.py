@@ -94,6 +94,25 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def max_over_ranks(value: float, world: int) -> float:
+    """The largest value over all ranks (the job time is the slowest rank's);
+    works with any torch.distributed backend (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(blocks_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job Mblocks/s: every rank's blocks over the slowest rank's time."""
+    return world * blocks_per_rank / (ms * 1e-3) / 1e6
+
+
 def _at(arr, i):
     """Pointer to element i of a ctypes array of descriptors."""
     t = arr._type_
@@ -157,11 +176,9 @@ def run_gpu(args):
     ms = _events_time(step, args.steps, stream)
     if world > 1:
         dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     blocks = FRAMES * BLOCKS_PER_FRAME
-    value = world * blocks / (ms * 1e-3) / 1e6
+    value = job_throughput(blocks, world, ms)
 
     # Per-frame PSNR of the last step (reported, from the library's host helper)
     sse_host = d_sse.cpu().tolist()
