@@ -359,6 +359,26 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                                                   "GB_s": round(gb / (ms_p * 1e-3), 1)}}
     del co2, imgs2
 
+    # -- zonal sweep (the paper's Fig. 2 experiment): PSNR for ten r values
+    #    from one forward per block, no quantiser
+    r_list = [1, 2, 4, 8, 16, 32, 64, 100, 128, 150]
+    rl = (ctypes.c_int32 * len(r_list))(*r_list)
+    sw = torch.zeros(FRAMES * len(r_list), dtype=torch.int64, device="cuda")
+
+    def sweep():
+        lib.tx16_zonal_sweep(ins, FRAMES, rl, len(r_list), ctypes.c_void_p(sw.data_ptr()), sptr)
+    for _ in range(2):
+        sweep()
+    ms_sw = _events_time(sweep, 5, stream)
+    sse_r = sw.view(FRAMES, len(r_list)).sum(0).cpu().tolist()
+    npx = FRAMES * H * W
+    psnr_r = [10 * math.log10(255.0 ** 2 * npx / s) if s else float("inf") for s in sse_r]
+    out["zonal_sweep"] = {"workload": f"{FRAMES} frames 1920x1088, r in {r_list}, no quantiser, exact inverse",
+                          "block_r_per_s_M": round(blocks * len(r_list) / (ms_sw * 1e-3) / 1e6, 1),
+                          "ms": round(ms_sw, 3),
+                          "psnr_db": [round(p, 3) for p in psnr_r],
+                          "psnr_per_addition": [round(p / 44.0, 4) for p in psnr_r]}
+
     # -- uneven-size batch (2000 images, sides 64..4096): plan vs per-image launches
     if not args.no_uneven:
         out["uneven_batch"] = _uneven_batch(lib, tx16, torch, np, stream, sptr, peak)

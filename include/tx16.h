@@ -148,6 +148,21 @@ tx16_status tx16_sse(const tx16_image* a, const tx16_image* b, int32_t n, uint64
  */
 tx16_status tx16_psnr(const uint64_t* sse, const tx16_image* imgs, int32_t n, double* psnr);
 
+/*
+ * Zonal sweep: the paper's image experiment (Sec. 3.1, no quantiser; Fig. 2
+ * plots PSNR per additive cost against r) for nr values of r at once.  Each
+ * block is transformed forward once; for every r_list[j] the coefficients
+ * outside Z_r are zeroed and the block is reconstructed exactly (256 X_tilde =
+ * T^t (D' Y D') T over Z_r), rounded, clipped and compared with the input.
+ *   imgs    host array of n input descriptors (any sample depth)
+ *   r_list  host array of nr values in 1..256, 1 <= nr <= 16
+ *   sse     device uint64[n * nr], sse[i * nr + j] = squared error of image i
+ *           coded with r_list[j]; zeroed by the call
+ * PSNR follows with tx16_psnr.  Nothing else is written.
+ */
+tx16_status tx16_zonal_sweep(const tx16_image* imgs, int32_t n, const int32_t* r_list, int32_t nr, uint64_t* sse,
+                             void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batch plans: uneven-size batches in one persistent launch per zonal class */
 /* ------------------------------------------------------------------------ */

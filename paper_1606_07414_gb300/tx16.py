@@ -59,6 +59,8 @@ _SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "tx16_plan_destroy": (None, [ctypes.c_void_p]),
+    "tx16_zonal_sweep": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "tx16_serve_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
     "tx16_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, tx16_qparams, ctypes.c_void_p,
@@ -196,6 +198,14 @@ def tx16_codec_batch_static(inp: Sequence, out: Sequence | None, qp: Sequence[tu
     out_arr = _images(out, bits) if out is not None else None
     _check(lib.tx16_codec_batch_static(_images(inp, bits), out_arr, len(inp), _qparams(qp), _ptr(sse),
                                        _ptr(levels), _stream(stream)), "tx16_codec_batch_static")
+
+
+def tx16_zonal_sweep(imgs: Sequence, r_list: Sequence[int], sse, stream=None, bits: int | None = None) -> None:
+    """sse: int64/uint64 CUDA tensor of len(imgs) * len(r_list), [image][r]."""
+    lib = load()
+    rl = (ctypes.c_int32 * len(r_list))(*[int(r) for r in r_list])
+    _check(lib.tx16_zonal_sweep(_images(imgs, bits), len(imgs), rl, len(r_list), _ptr(sse), _stream(stream)),
+           "tx16_zonal_sweep")
 
 
 def tx16_sse(a: Sequence, b: Sequence, sse, stream=None, bits: int | None = None) -> None:
