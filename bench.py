@@ -379,6 +379,31 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                           "psnr_db": [round(p, 3) for p in psnr_r],
                           "psnr_per_addition": [round(p / 44.0, 4) for p in psnr_r]}
 
+    # -- real 1920 x 1080 frames (1080 = 67.5 block rows): the any-size codec,
+    #    interior through the fused kernel, the ragged last block row apart
+    H1080 = 1080
+    ins_a = (tx16.tx16_image * FRAMES)(*[tx16.tx16_image(d_in[i].data_ptr(), W, H1080, W, 8)
+                                         for i in range(FRAMES)])
+    outs_a = (tx16.tx16_image * FRAMES)(*[tx16.tx16_image(d_out[i].data_ptr(), W, H1080, W, 8)
+                                          for i in range(FRAMES)])
+    qpa = qparams(args.q, args.r)
+
+    def any_size():
+        st = lib.tx16_codec_any_size(ins_a, outs_a, FRAMES, qpa, ctypes.c_void_p(sse_ptr), sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_codec_any_size")
+    for _ in range(3):
+        any_size()
+    ms_a = _events_time(any_size, 10, stream)
+    blocks_a = FRAMES * ((H1080 + 15) // 16) * (W // 16)
+    gbs_a = FRAMES * H1080 * W * 2 / (ms_a * 1e-3) / 1e9
+    out["any_size_1080"] = {"workload": f"{FRAMES} frames {W}x{H1080} uint8, q={args.q:g}, r={args.r}; "
+                                        "edge-replicated last block row",
+                            "Mblocks_s": round(blocks_a / (ms_a * 1e-3) / 1e6, 1),
+                            "Gpixels_s": round(FRAMES * H1080 * W / (ms_a * 1e-3) / 1e9, 1),
+                            "GB_s": round(gbs_a, 1), "frac": round(gbs_a / peak, 4), "ms": round(ms_a, 4),
+                            "launches_per_step": 3}
+
     # -- uneven-size batch (2000 images, sides 64..4096): plan vs per-image launches
     if not args.no_uneven:
         out["uneven_batch"] = _uneven_batch(lib, tx16, torch, np, stream, sptr, peak)

@@ -163,6 +163,32 @@ tx16_status tx16_psnr(const uint64_t* sse, const tx16_image* imgs, int32_t n, do
 tx16_status tx16_zonal_sweep(const tx16_image* imgs, int32_t n, const int32_t* r_list, int32_t nr, uint64_t* sse,
                              void* stream);
 
+/*
+ * Codec of images of any size, and of colour images plane by plane.  The
+ * paper codes images whose sides are multiples of 16 (Sec. 3.1: the image is
+ * split into 16x16 blocks); it does not say what happens at a ragged edge.
+ * Here the last row and the last column are repeated out to the next
+ * multiple of 16 (edge replication), the padded blocks go through the
+ * Sec. 3.1 codec exactly as in tx16_codec_batch, and only the image's own
+ * width x height samples are written and counted in the squared error.  A
+ * colour image is n = 3 (or more) descriptors, one per plane, each with its
+ * own quantiser (Sec. 3.1 codes each channel separately).
+ *   in      host array of n input descriptors: width, height >= 1 (not
+ *           necessarily multiples of 16); data 16-byte aligned; pitch_bytes a
+ *           multiple of 16 and >= width x sample size; bits 8..12
+ *   out     host array of n output descriptors of the same widths, heights and
+ *           bits (same rules), or NULL; only the width x height samples of
+ *           each output are written, the pitch padding is left untouched
+ *   qp      host array of n quantisers
+ *   sse     device uint64[n] or NULL: squared error over the width x height
+ *           samples of each image; zeroed by the call
+ * Images whose sides are multiples of 16 give the results of
+ * tx16_codec_batch.  PSNR follows with tx16_psnr, whose W x H is the
+ * unpadded size.  Returns TX16_EINVAL (nothing launched) for a bad argument.
+ */
+tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_image* out, int32_t n,
+                                const tx16_qparams* qp, uint64_t* sse, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batch plans: uneven-size batches in one persistent launch per zonal class */
 /* ------------------------------------------------------------------------ */

@@ -487,3 +487,37 @@ def transform_efficiency(A: np.ndarray, rho: float = 0.95) -> float:
     n = A.shape[0]
     RY = A @ ar1_covariance(rho, n) @ A.T
     return float(100.0 * np.sum(np.abs(np.diag(RY))) / np.sum(np.abs(RY)))
+
+
+# ---------------------------------------------------------------------------
+# Sizes that are not multiples of 16, and colour.
+# ---------------------------------------------------------------------------
+def pad_to_blocks(img: np.ndarray) -> np.ndarray:
+    """Extend an image to the next multiple of 16 in both directions by
+    repeating its last row and last column.
+
+    Reading: the paper's images are 512 x 512 and split exactly into 16 x 16
+    blocks (Sec. 3.1); for other sizes we take the usual block-codec practice
+    of edge replication."""
+    H, W = img.shape
+    Hp, Wp = -(-H // N) * N, -(-W // N) * N
+    return np.pad(np.asarray(img), ((0, Hp - H), (0, Wp - W)), mode="edge")
+
+
+def codec_image_any_size(img: np.ndarray, q: float | None, r: int, bits: int = 8,
+                         precision: str = "fp64") -> dict:
+    """The Sec. 3.1 codec on an image of any size: pad by edge replication
+    (``pad_to_blocks``), code, keep the original H x W region; SSE and PSNR
+    over the original pixels only."""
+    H, W = img.shape
+    res = codec_image(pad_to_blocks(img), q, r, bits, precision)
+    rec = res["recon"][:H, :W]
+    e = sse(img, rec)
+    return {"recon": rec, "sse": e, "psnr": psnr(e, H, W, bits), "levels": res["levels"]}
+
+
+def codec_colour(planes: list[np.ndarray], q: float | None, r: int, bits: int = 8,
+                 precision: str = "fp64") -> list[dict]:
+    """Colour images: each channel coded separately (Sec. 3.1, 'Color images
+    could be treated similarly by processing each channel separately')."""
+    return [codec_image_any_size(p, q, r, bits, precision) for p in planes]

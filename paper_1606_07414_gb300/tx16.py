@@ -71,6 +71,8 @@ _SIGNATURES = {
     "tx16_serve_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "tx16_serve_pause": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "tx16_serve_destroy": (None, [ctypes.c_void_p]),
+    "tx16_codec_any_size": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image), ctypes.c_int32,
+                                           ctypes.POINTER(tx16_qparams), ctypes.c_void_p, ctypes.c_void_p]),
     "tx16_codec_batch_static": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image),
                                                ctypes.c_int32, ctypes.POINTER(tx16_qparams), ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
@@ -206,6 +208,18 @@ def tx16_zonal_sweep(imgs: Sequence, r_list: Sequence[int], sse, stream=None, bi
     rl = (ctypes.c_int32 * len(r_list))(*[int(r) for r in r_list])
     _check(lib.tx16_zonal_sweep(_images(imgs, bits), len(imgs), rl, len(r_list), _ptr(sse), _stream(stream)),
            "tx16_zonal_sweep")
+
+
+def tx16_codec_any_size(inp: Sequence, out: Sequence | None, qp: Sequence[tuple[float, int]], sse=None,
+                        stream=None, bits: int | None = None) -> None:
+    """Codec of images of any width and height (edge-replicated to whole
+    blocks; only the image's own samples written and counted).  Row pitches
+    must be multiples of 16 bytes: slice a wider tensor, e.g.
+    ``torch.empty(h, (w + 15) // 16 * 16, dtype=torch.uint8)[:, :w]``."""
+    lib = load()
+    out_arr = _images(out, bits) if out is not None else None
+    _check(lib.tx16_codec_any_size(_images(inp, bits), out_arr, len(inp), _qparams(qp), _ptr(sse),
+                                   _stream(stream)), "tx16_codec_any_size")
 
 
 def tx16_sse(a: Sequence, b: Sequence, sse, stream=None, bits: int | None = None) -> None:

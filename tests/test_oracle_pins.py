@@ -273,6 +273,28 @@ def check_psnr_closed_forms(o):
     assert o.sse(a, b) == 9 + 25 + 4
 
 
+def check_any_size_codec(o):
+    """Edge replication: on sizes that are multiples of 16 it is the plain
+    codec; otherwise the padded pixels repeat the last row/column (numpy's
+    edge mode, a library routine) and the error counts original pixels only."""
+    img = synth.ar1_image(31, 48, 64, 0.95).astype(np.int64)
+    a = o.codec_image_any_size(img, 16.0, 16, 8, "fp32")
+    b = o.codec_image(img, 16.0, 16, 8, "fp32")
+    assert np.array_equal(a["recon"], b["recon"]) and a["sse"] == b["sse"]
+    odd = synth.ar1_image(32, 37, 50, 0.95).astype(np.int64)
+    P = o.pad_to_blocks(odd)
+    assert P.shape == (48, 64)
+    assert np.array_equal(P[:37, :50], odd)
+    assert np.all(P[37:, :50] == odd[36]) and np.all(P[:37, 50:] == odd[:, 49:50])
+    assert np.all(P[37:, 50:] == odd[36, 49])
+    c = o.codec_image_any_size(odd, None, 256, 8)  # lossless zone: exact on any size
+    assert c["sse"] == 0 and c["recon"].shape == odd.shape
+    d = o.codec_image_any_size(odd, 16.0, 4, 8, "fp32")
+    full = o.codec_image(P, 16.0, 4, 8, "fp32")
+    assert np.array_equal(d["recon"], full["recon"][:37, :50])
+    assert d["psnr"] == o.psnr(o.sse(odd, d["recon"]), 37, 50, 8)
+
+
 ALL_CHECKS = [v for k, v in sorted(globals().items()) if k.startswith("check_")]
 
 
