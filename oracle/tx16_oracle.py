@@ -521,3 +521,66 @@ def codec_colour(planes: list[np.ndarray], q: float | None, r: int, bits: int = 
     """Colour images: each channel coded separately (Sec. 3.1, 'Color images
     could be treated similarly by processing each channel separately')."""
     return [codec_image_any_size(p, q, r, bits, precision) for p in planes]
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1, Fig. 2(b) and Fig. 3: SSIM, the paper's second quality measure.
+# The paper cites Wang, Bovik, Sheikh and Simoncelli (2004) without fixing the
+# window or constants.  Reading: that article's own choices -- an 11 x 11
+# circular-symmetric Gaussian window with standard deviation 1.5, normalised
+# to unit sum; K1 = 0.01, K2 = 0.03, L = 2^bits - 1; local statistics at every
+# position where the window lies wholly inside the image (no padding); no
+# downsampling; the mean over those positions (MSSIM).
+# ---------------------------------------------------------------------------
+SSIM_SIZE = 11
+SSIM_SIGMA = 1.5
+SSIM_K1 = 0.01
+SSIM_K2 = 0.03
+
+
+def ssim_window(size: int = SSIM_SIZE, sigma: float = SSIM_SIGMA) -> np.ndarray:
+    """w(a, b) proportional to exp(-(a^2 + b^2) / (2 sigma^2)), a, b in
+    -(size-1)/2 .. (size-1)/2, normalised so that the weights sum to 1."""
+    h = (size - 1) // 2
+    a = np.arange(-h, h + 1, dtype=np.float64)
+    w = np.exp(-(a[:, None] ** 2 + a[None, :] ** 2) / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def window_mean(img: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Weighted local mean at every position where the window fits:
+    out[i, j] = sum_{a, b} w[a, b] img[i + a, j + b] (the 2-D window applied
+    directly, one shifted copy of the image per weight)."""
+    img = np.asarray(img, dtype=np.float64)
+    k = w.shape[0]
+    H, W = img.shape
+    out = np.zeros((H - k + 1, W - k + 1))
+    for a in range(k):
+        for b in range(k):
+            out += w[a, b] * img[a:a + H - k + 1, b:b + W - k + 1]
+    return out
+
+
+def ssim_map(x: np.ndarray, y: np.ndarray, bits: int = 8) -> np.ndarray:
+    """Local SSIM (Wang et al. 2004, eq. 13 with the window's weighted
+    statistics): ((2 mu_x mu_y + C1)(2 s_xy + C2)) /
+    ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)), C1 = (K1 L)^2,
+    C2 = (K2 L)^2; s_x^2 = E_w[x^2] - mu_x^2, s_xy = E_w[x y] - mu_x mu_y."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if min(x.shape) < SSIM_SIZE or x.shape != y.shape:
+        raise ValueError("SSIM needs two images of equal shape, both sides >= 11")
+    L = float((1 << bits) - 1)
+    C1 = (SSIM_K1 * L) ** 2
+    C2 = (SSIM_K2 * L) ** 2
+    w = ssim_window()
+    mx, my = window_mean(x, w), window_mean(y, w)
+    sxx = window_mean(x * x, w) - mx * mx
+    syy = window_mean(y * y, w) - my * my
+    sxy = window_mean(x * y, w) - mx * my
+    return ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+
+
+def ssim(x: np.ndarray, y: np.ndarray, bits: int = 8) -> float:
+    """Mean SSIM over all window positions (MSSIM)."""
+    return float(np.mean(ssim_map(x, y, bits)))

@@ -142,11 +142,88 @@ def _m1_wrong_half(m):
     m._butterfly = bf
 
 
+def _ssim_k2_too_large(m):
+    m.SSIM_K2 = 0.3
+
+
+def _ssim_structure_drops_two(m):
+    orig = m.window_mean
+
+    def ssim_map(x, y, bits=8):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        L = float((1 << bits) - 1)
+        C1, C2 = (m.SSIM_K1 * L) ** 2, (m.SSIM_K2 * L) ** 2
+        w = m.ssim_window()
+        mx, my = orig(x, w), orig(y, w)
+        sxx = orig(x * x, w) - mx * mx
+        syy = orig(y * y, w) - my * my
+        sxy = orig(x * y, w) - mx * my
+        return ((2 * mx * my + C1) * (sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    m.ssim_map = ssim_map
+
+
+def _ssim_sigma_one(m):
+    m.SSIM_SIGMA = 1.0
+    orig = m.ssim_window
+    m.ssim_window = lambda size=11, sigma=1.0: orig(size, sigma)
+
+
+def _ssim_raw_second_moments(m):
+    orig = m.window_mean
+
+    def ssim_map(x, y, bits=8):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        L = float((1 << bits) - 1)
+        C1, C2 = (m.SSIM_K1 * L) ** 2, (m.SSIM_K2 * L) ** 2
+        w = m.ssim_window()
+        mx, my = orig(x, w), orig(y, w)
+        sxx, syy, sxy = orig(x * x, w), orig(y * y, w), orig(x * y, w)  # means not subtracted
+        return ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    m.ssim_map = ssim_map
+
+
+def _ssim_window_unnormalised(m):
+    orig = m.ssim_window
+    m.ssim_window = lambda size=11, sigma=1.5: orig(size, sigma) * 2 * np.pi * sigma * sigma
+
+
+def _ssim_window_one_column_late(m):
+    def wm(img, w):
+        img = np.asarray(img, dtype=np.float64)
+        k = w.shape[0]
+        H, W = img.shape
+        out = np.zeros((H - k + 1, W - k))
+        for a in range(k):
+            for b in range(k):
+                out += w[a, b] * img[a:a + H - k + 1, b + 1:b + 1 + W - k]
+        return out
+    m.window_mean = wm
+
+
+def _ssim_peak_256(m):
+    def ssim_map(x, y, bits=8):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        L = float(1 << bits)  # 2^bits where the peak is 2^bits - 1
+        C1, C2 = (m.SSIM_K1 * L) ** 2, (m.SSIM_K2 * L) ** 2
+        w = m.ssim_window()
+        mx, my = m.window_mean(x, w), m.window_mean(y, w)
+        sxx = m.window_mean(x * x, w) - mx * mx
+        syy = m.window_mean(y * y, w) - my * my
+        sxy = m.window_mean(x * y, w) - mx * my
+        return ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    m.ssim_map = ssim_map
+
+
 MUTANTS = [_flip_T_sign, _swap_S_entries, _reverse_P1, _M3_plus_identity,
            _transposed_forward, _zigzag_wrong_direction, _bankers_rounding,
            _quantiser_divides_by_s, _exact_inverse_wrong_D, _psnr_peak_256,
            _dequantise_drops_q, _dct_without_dc_norm, _coding_gain_arith_mean,
-           _inverse_fp32_rows_use_T, _blocks_column_order, _m1_wrong_half]
+           _inverse_fp32_rows_use_T, _blocks_column_order, _m1_wrong_half,
+           _ssim_k2_too_large, _ssim_structure_drops_two, _ssim_sigma_one, _ssim_raw_second_moments,
+           _ssim_window_unnormalised, _ssim_window_one_column_late, _ssim_peak_256]
 
 
 @pytest.mark.parametrize("mutate", MUTANTS, ids=[f.__name__.strip("_") for f in MUTANTS])

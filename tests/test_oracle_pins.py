@@ -295,6 +295,80 @@ def check_any_size_codec(o):
     assert d["psnr"] == o.psnr(o.sse(odd, d["recon"]), 37, 50, 8)
 
 
+# ----------------------------------------------------------------------------
+# SSIM (Sec. 3.1, Fig. 2(b); Wang et al. 2004 window and constants)
+# ----------------------------------------------------------------------------
+def check_ssim_window(o):
+    """The window is scipy's 11-point Gaussian of standard deviation 1.5, as
+    an outer product, normalised to unit sum; the local means are scipy's
+    'valid' 2-D correlation with it."""
+    import scipy.signal
+
+    w = o.ssim_window()
+    g = scipy.signal.windows.gaussian(11, std=1.5)
+    ref = np.outer(g, g) / np.outer(g, g).sum()
+    assert w.shape == (11, 11)
+    assert np.allclose(w, ref, rtol=1e-14, atol=0)
+    img = synth.ar1_image(41, 30, 27, 0.9).astype(np.float64)
+    got = o.window_mean(img, w)
+    want = scipy.signal.correlate2d(img, ref, mode="valid")
+    assert got.shape == (20, 17)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-9)
+
+
+def check_ssim_identity_symmetry_constants(o):
+    x = synth.ar1_image(42, 40, 36, 0.95)
+    y = o.codec_image(synth.ar1_image(42, 48, 48, 0.95)[:48, :48], 16.0, 8, 8)["recon"][:40, :36]
+    assert o.ssim(x, x) == pytest.approx(1.0, abs=1e-12)
+    assert o.ssim(x, y) == pytest.approx(o.ssim(y, x), abs=1e-12)
+    assert o.ssim_map(x, y).shape == (30, 26)
+    # constant images: the structure term is C2 / C2, the luminance term is
+    # (2ab + C1) / (a^2 + b^2 + C1), C1 = (0.01 L)^2
+    for a, b, bits in ((100, 140, 8), (0, 255, 8), (700, 650, 10)):
+        L = (1 << bits) - 1
+        C1 = (0.01 * L) ** 2
+        want = (2 * a * b + C1) / (a * a + b * b + C1)
+        got = o.ssim(np.full((16, 20), a), np.full((16, 20), b), bits)
+        assert got == pytest.approx(want, rel=1e-12)
+
+
+def check_ssim_checkerboard_closed_form(o):
+    """x = m + d (-1)^(i+j), y = n + e (-1)^(i+j).  For a window at (i0, j0)
+    with sign t = (-1)^(i0+j0) and s = sum_k g_k (-1)^k over the normalised
+    1-D Gaussian g: mu_x = m + t d s^2, s_x^2 = d^2 (1 - s^4),
+    s_xy = d e (1 - s^4); half the positions have t = +1."""
+    k = np.arange(11) - 5.0
+    g = np.exp(-k * k / (2 * 1.5 ** 2))
+    g /= g.sum()
+    s2 = float(np.sum(g * (-1.0) ** np.arange(11))) ** 2
+    m, d, n, e = 120.0, 30.0, 100.0, -12.0
+    H, W = 30, 40  # 20 x 30 window positions: half with each sign
+    i, j = np.indices((H, W))
+    sgn = (-1.0) ** (i + j)
+    x = m + d * sgn
+    y = n + e * sgn
+    C1, C2 = (0.01 * 255) ** 2, (0.03 * 255) ** 2
+    cs = (2 * d * e * (1 - s2 * s2) + C2) / ((d * d + e * e) * (1 - s2 * s2) + C2)
+    lum = [(2 * (m + t * d * s2) * (n + t * e * s2) + C1) / ((m + t * d * s2) ** 2 + (n + t * e * s2) ** 2 + C1)
+           for t in (1.0, -1.0)]
+    assert o.ssim(x, y) == pytest.approx(0.5 * (lum[0] + lum[1]) * cs, rel=1e-12)
+
+
+def check_ssim_one_window_by_weighted_covariance(o):
+    """One window position against numpy's weighted mean and weighted
+    covariance (np.average, np.cov with aweights, bias=True)."""
+    x = synth.ar1_image(43, 11, 11, 0.8).astype(np.float64)
+    y = synth.ar1_image(44, 11, 11, 0.8).astype(np.float64)
+    w = o.ssim_window().ravel()
+    mx, my = np.average(x.ravel(), weights=w), np.average(y.ravel(), weights=w)
+    c = np.cov(np.stack([x.ravel(), y.ravel()]), aweights=w, bias=True)
+    C1, C2 = (0.01 * 255) ** 2, (0.03 * 255) ** 2
+    want = ((2 * mx * my + C1) * (2 * c[0, 1] + C2)) / ((mx * mx + my * my + C1) * (c[0, 0] + c[1, 1] + C2))
+    got = o.ssim_map(x, y)
+    assert got.shape == (1, 1)
+    assert got[0, 0] == pytest.approx(want, rel=1e-10)
+
+
 ALL_CHECKS = [v for k, v in sorted(globals().items()) if k.startswith("check_")]
 
 
