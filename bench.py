@@ -33,6 +33,10 @@ BLOCKS_PER_FRAME = (H // 16) * (W // 16)
 BYTES_PER_BLOCK_CODEC = 512    # 256 B samples in + 256 B reconstructed samples out
 BYTES_PER_BLOCK_FORWARD = 1280  # 256 B samples in + 1024 B int32 coefficients out
 SEED = 2016
+# SSIM: binary32 operations per window position (11-tap row pass of five
+# moments 77, column pass 55, the index 14) and the GB300's binary32 lanes
+SSIM_OPS_PER_POSITION = 146
+ALU_LANES_PER_SM, SM_COUNT, SM_MAX_MHZ = 128, 152, 2070
 
 
 def _env_rank():
@@ -403,6 +407,32 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                             "Gpixels_s": round(FRAMES * H1080 * W / (ms_a * 1e-3) / 1e9, 1),
                             "GB_s": round(gbs_a, 1), "frac": round(gbs_a / peak, 4), "ms": round(ms_a, 4),
                             "launches_per_step": 3}
+
+    # -- SSIM of every frame against its reconstruction (the paper's second
+    #    measure): arithmetic-bound, 146 binary32 operations per window position
+    ms_t = torch.zeros(FRAMES, dtype=torch.float64, device="cuda")
+
+    def ssim():
+        st = lib.tx16_ssim(ins, outs, FRAMES, ctypes.c_void_p(ms_t.data_ptr()), None, sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_ssim")
+    lib.tx16_codec_batch(ins, outs, FRAMES, qp, ctypes.c_void_p(sse_ptr), None, sptr)
+    for _ in range(3):
+        ssim()
+    ms_s = _events_time(ssim, 10, stream)
+    positions = FRAMES * (H - 10) * (W - 10)
+    ops = positions * SSIM_OPS_PER_POSITION
+    alu_peak = ALU_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6
+    out["ssim"] = {"workload": f"{FRAMES} frames {W}x{H} uint8 vs their q={args.q:g}, r={args.r} reconstruction; "
+                               "11x11 Gaussian window (sigma 1.5), mean over window positions",
+                   "Gpositions_s": round(positions / (ms_s * 1e-3) / 1e9, 2), "ms": round(ms_s, 4),
+                   "mean_ssim": round(float(ms_t.mean().item()), 6),
+                   "roofline": {"bound": "alu", "achieved": round(ops / (ms_s * 1e-3) / 1e12, 2),
+                                "peak": round(alu_peak / 1e12, 2), "unit": "Tops/s",
+                                "frac": round(ops / (ms_s * 1e-3) / alu_peak, 4),
+                                "ops_per_position": SSIM_OPS_PER_POSITION,
+                                "peak_source": f"{ALU_LANES_PER_SM} binary32 lanes x {SM_COUNT} SMs x "
+                                               f"{SM_MAX_MHZ} MHz (one fma, add or mul per lane per clock)"}}
 
     # -- uneven-size batch (2000 images, sides 64..4096): plan vs per-image launches
     if not args.no_uneven:

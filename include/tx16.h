@@ -189,6 +189,32 @@ tx16_status tx16_zonal_sweep(const tx16_image* imgs, int32_t n, const int32_t* r
 tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_image* out, int32_t n,
                                 const tx16_qparams* qp, uint64_t* sse, void* stream);
 
+/*
+ * SSIM, the paper's second quality measure (Sec. 3.1: Fig. 2(b) plots SSIM per
+ * additive cost, Fig. 3 quotes it per image).  The paper cites Wang, Bovik,
+ * Sheikh and Simoncelli (2004) without fixing window or constants; this
+ * library takes that article's: an 11 x 11 Gaussian window, standard
+ * deviation 1.5, normalised to unit sum; C1 = (0.01 L)^2, C2 = (0.03 L)^2,
+ * L = 2^bits - 1; local weighted statistics at every position where the window
+ * lies inside the image (no padding, no downsampling); the index
+ *   ((2 mu_a mu_b + C1)(2 s_ab + C2)) / ((mu_a^2 + mu_b^2 + C1)(s_a^2 + s_b^2 + C2))
+ * averaged over the (H - 10) x (W - 10) positions (MSSIM).
+ *   a, b    host arrays of n descriptors of equal size and bits (typically the
+ *           input and the reconstruction of tx16_codec_batch); width and
+ *           height >= 11, any value; data 16-byte aligned; pitch a multiple of
+ *           16 bytes and >= width x sample size
+ *   mssim   device double[n]: the mean index of each pair; zeroed by the call
+ *   map     device float array of sum_i (H_i - 10)(W_i - 10) elements, or
+ *           NULL: image i's local indices, row-major, after those of images
+ *           0 .. i-1
+ * Arithmetic is binary32 with samples centred on 2^(bits-1); the difference
+ * from the binary64 definition is bounded per position by the rounding of
+ * the two 11-tap passes (see the tests).  Returns TX16_EINVAL for a bad
+ * argument, nothing launched.
+ */
+tx16_status tx16_ssim(const tx16_image* a, const tx16_image* b, int32_t n, double* mssim, float* map,
+                      void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batch plans: uneven-size batches in one persistent launch per zonal class */
 /* ------------------------------------------------------------------------ */

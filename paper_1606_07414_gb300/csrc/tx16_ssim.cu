@@ -1,0 +1,318 @@
+// SSIM (tx16_ssim): the paper's second quality measure (Sec. 3.1, Fig. 2(b),
+// Fig. 3), with the window and constants of the article it cites (Wang, Bovik,
+// Sheikh and Simoncelli, 2004): an 11 x 11 Gaussian window of standard
+// deviation 1.5 normalised to unit sum, K1 = 0.01, K2 = 0.03, L = 2^bits - 1,
+// statistics at every position where the window fits inside the image, and
+// the mean of the local indices (MSSIM).
+//
+// The Gaussian window is the outer product of a normalised 1-D window g, so
+// the five local moments (E x, E y, E x^2, E y^2, E xy) are two 11-tap passes:
+// along rows into shared memory, then along columns in registers.  Samples are
+// centred on 2^(bits-1) before squaring, which keeps E x^2 - (E x)^2 from
+// cancelling more digits than it must; the luminance term adds the centre
+// back.  All arithmetic is binary32; each CTA adds its partial mean into the
+// image's binary64 result with one atomic.
+//
+// Mapping: a CTA owns a strip of 32 output columns and kSegRows output rows of
+// one image and walks down it in chunks of 64 rows.  Per chunk: stage the new
+// input rows (as centred floats), the row pass for 64 (first chunk 74) rows of
+// the five moment planes, then the column pass, one column and 8 rows per
+// thread.  The last 10 rows of the moment planes move to the top for the next
+// chunk.  The kernel is arithmetic-bound: 146 binary32 operations per output
+// (77 in the row pass, 55 in the column pass, 14 in the index) against 2
+// sample reads.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tx16_internal.h"
+
+namespace tx16 {
+namespace {
+
+constexpr int kWin = 11;                   // window side
+constexpr int kHalo = kWin - 1;            // 10
+constexpr int kStripCols = 32;             // output columns per CTA
+constexpr int kChunk = 64;                 // output rows per chunk
+constexpr int kSegRows = 256;              // output rows per CTA
+constexpr int kHRows = kChunk + kHalo;     // 74 moment rows held
+constexpr int kInW = 44;                   // staged input columns (42 used, float4 reads)
+constexpr int kSsimThreads = 256;
+constexpr int kSsimMaxImg = 200;
+constexpr size_t kSsimSmem = sizeof(float) * (2 * kHRows * kInW + 5 * kHRows * kStripCols);
+
+struct SsimImg {
+  const void* a;
+  const void* b;
+  int64_t pa, pb;        // pitches in bytes
+  int64_t map_off;       // first element of this image's map
+  double inv_count;      // 1 / number of window positions
+  int32_t w, h;          // image size
+  int32_t mw, mh;        // map size: w - 10, h - 10
+  int32_t nstrips, unit0;
+  float centre, c1, c2;
+};
+
+template <int MAXI>
+struct SsimParams {
+  int32_t nimg, nunits;
+  double* mssim;
+  float* map;
+  float g[kWin];  // normalised 1-D Gaussian, binary32
+  SsimImg img[MAXI];
+};
+static_assert(sizeof(SsimParams<kSsimMaxImg>) < 32000, "kernel parameters too large");
+
+template <typename Smp>
+__device__ __forceinline__ float sample(const void* base, int64_t pitch, int y, int x) {
+  return float(reinterpret_cast<const Smp*>(static_cast<const char*>(base) + int64_t(y) * pitch)[x]);
+}
+
+template <typename Smp, bool MAP, int MAXI>
+__global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const __grid_constant__ SsimParams<MAXI> P) {
+  extern __shared__ __align__(16) float sm[];
+  float* in_a = sm;                          // [kHRows][kInW]
+  float* in_b = in_a + kHRows * kInW;        // [kHRows][kInW]
+  float* hm = in_b + kHRows * kInW;          // [5][kHRows][kStripCols]
+  const int tid = threadIdx.x;
+
+  // unit -> image (largest k with unit0 <= unit)
+  const int unit = blockIdx.x;
+  int lo = 0, hi = P.nimg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.img[mid].unit0 <= unit) lo = mid;
+    else hi = mid - 1;
+  }
+  const SsimImg& I = P.img[lo];
+  const int u = unit - I.unit0;
+  const int strip = u % I.nstrips;
+  const int seg = u / I.nstrips;
+  const int c0 = strip * kStripCols;
+  const int r_begin = seg * kSegRows;
+  const int r_end = min(r_begin + kSegRows, I.mh);
+
+  float g[kWin];
+#pragma unroll
+  for (int k = 0; k < kWin; ++k) g[k] = P.g[k];
+
+  float sum = 0.f;
+  for (int r0 = r_begin; r0 < r_end; r0 += kChunk) {
+    const bool first = r0 == r_begin;
+    const int nrows = first ? kHRows : kChunk;     // moment rows to compute
+    const int dst0 = first ? 0 : kHalo;            // where they go
+    const int y0 = first ? r0 : r0 + kHalo;        // their first input row
+    if (!first) {
+      // keep the last 10 moment rows: rows 64..73 -> 0..9
+      for (int i = tid; i < 5 * kHalo * kStripCols; i += kSsimThreads) {
+        const int q = i / (kHalo * kStripCols);
+        const int rr = (i / kStripCols) % kHalo;
+        const int cc = i % kStripCols;
+        hm[(q * kHRows + rr) * kStripCols + cc] = hm[(q * kHRows + kChunk + rr) * kStripCols + cc];
+      }
+    }
+    // stage input rows y0 .. y0 + nrows - 1, columns c0 .. c0 + kInW - 1,
+    // clamped to the image (clamped samples feed only masked outputs)
+    for (int i = tid; i < nrows * kInW; i += kSsimThreads) {
+      const int rr = i / kInW;
+      const int cc = i - rr * kInW;
+      const int y = min(y0 + rr, I.h - 1);
+      const int x = min(c0 + cc, I.w - 1);
+      in_a[rr * kInW + cc] = sample<Smp>(I.a, I.pa, y, x) - I.centre;
+      in_b[rr * kInW + cc] = sample<Smp>(I.b, I.pb, y, x) - I.centre;
+    }
+    __syncthreads();
+    // row pass: 4 adjacent columns of one row per task
+    for (int task = tid; task < nrows * (kStripCols / 4); task += kSsimThreads) {
+      const int rr = task >> 3;
+      const int cg = task & 7;
+      float va[16], vb[16];
+      const float4* pa4 = reinterpret_cast<const float4*>(in_a + rr * kInW + 4 * cg);
+      const float4* pb4 = reinterpret_cast<const float4*>(in_b + rr * kInW + 4 * cg);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float4 x4 = pa4[m], y4 = pb4[m];
+        va[4 * m] = x4.x; va[4 * m + 1] = x4.y; va[4 * m + 2] = x4.z; va[4 * m + 3] = x4.w;
+        vb[4 * m] = y4.x; vb[4 * m + 1] = y4.y; vb[4 * m + 2] = y4.z; vb[4 * m + 3] = y4.w;
+      }
+      float hx[4], hy[4], hxx[4], hyy[4], hxy[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        hx[j] = 0.f; hy[j] = 0.f; hxx[j] = 0.f; hyy[j] = 0.f; hxy[j] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+          const float a = va[j + k], b = vb[j + k];
+          const float ga = g[k] * a, gb = g[k] * b;
+          hx[j] += ga;
+          hy[j] += gb;
+          hxx[j] = fmaf(ga, a, hxx[j]);
+          hyy[j] = fmaf(gb, b, hyy[j]);
+          hxy[j] = fmaf(ga, b, hxy[j]);
+        }
+      }
+      const int row = dst0 + rr;
+      float4* o = reinterpret_cast<float4*>(hm + row * kStripCols + 4 * cg);
+      constexpr int kPlane = kHRows * kStripCols / 4;  // float4 per plane
+      o[0] = make_float4(hx[0], hx[1], hx[2], hx[3]);
+      o[kPlane] = make_float4(hy[0], hy[1], hy[2], hy[3]);
+      o[2 * kPlane] = make_float4(hxx[0], hxx[1], hxx[2], hxx[3]);
+      o[3 * kPlane] = make_float4(hyy[0], hyy[1], hyy[2], hyy[3]);
+      o[4 * kPlane] = make_float4(hxy[0], hxy[1], hxy[2], hxy[3]);
+    }
+    __syncthreads();
+    // column pass: column cc, output rows r0 + 8 rg .. r0 + 8 rg + 7
+    {
+      const int cc = tid & (kStripCols - 1);
+      const int rg = tid >> 5;
+      float e[5][8];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        float v[8 + kHalo];
+#pragma unroll
+        for (int m = 0; m < 8 + kHalo; ++m) v[m] = hm[(q * kHRows + 8 * rg + m) * kStripCols + cc];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < kWin; ++k) acc = fmaf(g[k], v[i + k], acc);
+          e[q][i] = acc;
+        }
+      }
+      const int x = c0 + cc;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int y = r0 + 8 * rg + i;
+        const float mxp = e[0][i], myp = e[1][i];
+        const float sxx = fmaf(-mxp, mxp, e[2][i]);
+        const float syy = fmaf(-myp, myp, e[3][i]);
+        const float sxy = fmaf(-mxp, myp, e[4][i]);
+        const float mx = mxp + I.centre, my = myp + I.centre;
+        const float n1 = fmaf(2.f * mx, my, I.c1);
+        const float d1 = fmaf(mx, mx, fmaf(my, my, I.c1));
+        const float n2 = fmaf(2.f, sxy, I.c2);
+        const float d2 = (sxx + syy) + I.c2;
+        const float s = (n1 * n2) / (d1 * d2);
+        if (y < r_end && x < I.mw) {
+          sum += s;
+          if (MAP) P.map[I.map_off + int64_t(y) * I.mw + x] = s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // CTA reduction in binary64, one atomic per CTA
+  double d = double(sum);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  __shared__ double red[kSsimThreads / 32];
+  if ((tid & 31) == 0) red[tid >> 5] = d;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSsimThreads / 32; ++w) t += red[w];
+    atomicAdd(P.mssim + lo, t * I.inv_count);
+  }
+}
+
+template <typename Smp, bool MAP>
+tx16_status launch_ssim(const SsimImg* imgs, int n, const float* g, double* mssim, float* map, cudaStream_t st) {
+  SsimParams<kSsimMaxImg> P;
+  P.nimg = n;
+  P.mssim = mssim;
+  P.map = map;
+  for (int k = 0; k < kWin; ++k) P.g[k] = g[k];
+  int units = 0;
+  for (int i = 0; i < n; ++i) {
+    P.img[i] = imgs[i];
+    P.img[i].unit0 = units;
+    units += imgs[i].nstrips * ((imgs[i].mh + kSegRows - 1) / kSegRows);
+  }
+  P.nunits = units;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(ssim_kernel<Smp, MAP, kSsimMaxImg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(kSsimSmem)) != cudaSuccess)
+      return TX16_ECUDA;
+    attr = true;
+  }
+  ssim_kernel<Smp, MAP, kSsimMaxImg><<<units, kSsimThreads, kSsimSmem, st>>>(P);
+  return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
+}
+
+bool valid_ssim_image(const tx16_image& im) {
+  if (im.data == nullptr || (reinterpret_cast<uintptr_t>(im.data) & 15u) != 0) return false;
+  if (im.bits < 8 || im.bits > 12) return false;
+  if (im.width < kWin || im.height < kWin) return false;
+  if (im.pitch_bytes <= 0 || (im.pitch_bytes % 16) != 0) return false;
+  if (im.pitch_bytes < int64_t(im.width) * sample_bytes(im.bits)) return false;
+  // unit count and map offsets stay within int32 / int64
+  const int64_t strips = (int64_t(im.width) - kHalo + kStripCols - 1) / kStripCols;
+  const int64_t segs = (int64_t(im.height) - kHalo + kSegRows - 1) / kSegRows;
+  return strips * segs < (int64_t(1) << 30);
+}
+
+}  // namespace
+}  // namespace tx16
+
+using namespace tx16;
+
+extern "C" tx16_status tx16_ssim(const tx16_image* a, const tx16_image* b, int32_t n, double* mssim, float* map,
+                                 void* stream) {
+  if (n < 0 || (n > 0 && (a == nullptr || b == nullptr || mssim == nullptr))) return TX16_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(mssim) & 7u) != 0 || (reinterpret_cast<uintptr_t>(map) & 3u) != 0)
+    return TX16_EINVAL;
+  // the normalised 1-D window, formed in binary64 and rounded once
+  double e[kWin], es = 0.0;
+  for (int k = 0; k < kWin; ++k) {
+    const double t = double(k - kHalo / 2);
+    e[k] = std::exp(-t * t / (2.0 * 1.5 * 1.5));
+    es += e[k];
+  }
+  float g[kWin];
+  for (int k = 0; k < kWin; ++k) g[k] = float(e[k] / es);
+  std::vector<SsimImg> I(n);
+  int64_t map_off = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!valid_ssim_image(a[i]) || !valid_ssim_image(b[i])) return TX16_EINVAL;
+    if (a[i].width != b[i].width || a[i].height != b[i].height || a[i].bits != b[i].bits) return TX16_EINVAL;
+    SsimImg& s = I[i];
+    s.a = a[i].data;
+    s.b = b[i].data;
+    s.pa = a[i].pitch_bytes;
+    s.pb = b[i].pitch_bytes;
+    s.w = a[i].width;
+    s.h = a[i].height;
+    s.mw = s.w - kHalo;
+    s.mh = s.h - kHalo;
+    s.nstrips = (s.mw + kStripCols - 1) / kStripCols;
+    s.map_off = map_off;
+    map_off += int64_t(s.mw) * s.mh;
+    s.inv_count = 1.0 / (double(s.mw) * double(s.mh));
+    const double L = double((1 << a[i].bits) - 1);
+    s.centre = float(1 << (a[i].bits - 1));
+    s.c1 = float((0.01 * L) * (0.01 * L));
+    s.c2 = float((0.03 * L) * (0.03 * L));
+  }
+  if (n == 0) return TX16_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(mssim, 0, sizeof(double) * size_t(n), st) != cudaSuccess) return TX16_ECUDA;
+  int s = 0;
+  while (s < n) {
+    int e2 = s + 1;
+    while (e2 < n && e2 - s < kSsimMaxImg && (a[e2].bits == 8) == (a[s].bits == 8)) ++e2;
+    // map offsets are absolute: each launch gets the base map pointer
+    tx16_status r;
+    if (a[s].bits == 8)
+      r = map ? launch_ssim<uint8_t, true>(I.data() + s, e2 - s, g, mssim + s, map, st)
+              : launch_ssim<uint8_t, false>(I.data() + s, e2 - s, g, mssim + s, nullptr, st);
+    else
+      r = map ? launch_ssim<uint16_t, true>(I.data() + s, e2 - s, g, mssim + s, map, st)
+              : launch_ssim<uint16_t, false>(I.data() + s, e2 - s, g, mssim + s, nullptr, st);
+    if (r != TX16_OK) return r;
+    s = e2;
+  }
+  return TX16_OK;
+}

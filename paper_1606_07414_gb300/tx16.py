@@ -73,6 +73,8 @@ _SIGNATURES = {
     "tx16_serve_destroy": (None, [ctypes.c_void_p]),
     "tx16_codec_any_size": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image), ctypes.c_int32,
                                            ctypes.POINTER(tx16_qparams), ctypes.c_void_p, ctypes.c_void_p]),
+    "tx16_ssim": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image), ctypes.c_int32,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tx16_codec_batch_static": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image),
                                                ctypes.c_int32, ctypes.POINTER(tx16_qparams), ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
@@ -220,6 +222,15 @@ def tx16_codec_any_size(inp: Sequence, out: Sequence | None, qp: Sequence[tuple[
     out_arr = _images(out, bits) if out is not None else None
     _check(lib.tx16_codec_any_size(_images(inp, bits), out_arr, len(inp), _qparams(qp), _ptr(sse),
                                    _stream(stream)), "tx16_codec_any_size")
+
+
+def tx16_ssim(a: Sequence, b: Sequence, mssim, map=None, stream=None, bits: int | None = None) -> None:
+    """Mean SSIM of each pair into ``mssim`` (float64 CUDA tensor of len(a));
+    optionally every local index into ``map`` (float32 CUDA tensor holding
+    sum (H - 10)(W - 10) elements, image after image)."""
+    lib = load()
+    _check(lib.tx16_ssim(_images(a, bits), _images(b, bits), len(a), _ptr(mssim), _ptr(map), _stream(stream)),
+           "tx16_ssim")
 
 
 def tx16_sse(a: Sequence, b: Sequence, sse, stream=None, bits: int | None = None) -> None:
