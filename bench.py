@@ -33,9 +33,9 @@ BLOCKS_PER_FRAME = (H // 16) * (W // 16)
 BYTES_PER_BLOCK_CODEC = 512    # 256 B samples in + 256 B reconstructed samples out
 BYTES_PER_BLOCK_FORWARD = 1280  # 256 B samples in + 1024 B int32 coefficients out
 SEED = 2016
-# SSIM: binary32 operations per window position (11-tap row pass of five
-# moments 77, column pass 55, the index 14) and the GB300's binary32 lanes
-SSIM_OPS_PER_POSITION = 146
+# SSIM: binary32 operations per window position (row pass of five moments
+# 65.5, column pass 55, the index 17) and the GB300's binary32 lanes
+SSIM_OPS_PER_POSITION = 137.5
 ALU_LANES_PER_SM, SM_COUNT, SM_MAX_MHZ = 128, 152, 2070
 
 
@@ -409,7 +409,7 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                             "launches_per_step": 3}
 
     # -- SSIM of every frame against its reconstruction (the paper's second
-    #    measure): arithmetic-bound, 146 binary32 operations per window position
+    #    measure): arithmetic-bound, 137.5 binary32 operations per window position
     ms_t = torch.zeros(FRAMES, dtype=torch.float64, device="cuda")
 
     def ssim():

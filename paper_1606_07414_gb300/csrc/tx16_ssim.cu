@@ -15,12 +15,13 @@
 //
 // Mapping: a CTA owns a strip of 32 output columns and kSegRows output rows of
 // one image and walks down it in chunks of 64 rows.  Per chunk: stage the new
-// input rows (as centred floats), the row pass for 64 (first chunk 74) rows of
-// the five moment planes, then the column pass, one column and 8 rows per
+// input rows (as centred floats; the words were fetched into registers during
+// the previous chunk's column pass), the row pass for 64 (first chunk 74) rows
+// of the five moment planes, then the column pass, one column and 8 rows per
 // thread.  The last 10 rows of the moment planes move to the top for the next
-// chunk.  The kernel is arithmetic-bound: 146 binary32 operations per output
-// (77 in the row pass, 55 in the column pass, 14 in the index) against 2
-// sample reads.
+// chunk.  The kernel is arithmetic-bound: 137.5 binary32 operations per output
+// (row pass 65.5: 10.5 products and 11 per moment with the window's symmetry;
+// column pass 55; the index 17) against 2 sample reads.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,7 +37,7 @@ constexpr int kWin = 11;                   // window side
 constexpr int kHalo = kWin - 1;            // 10
 constexpr int kStripCols = 32;             // output columns per CTA
 constexpr int kChunk = 64;                 // output rows per chunk
-constexpr int kSegRows = 256;              // output rows per CTA
+constexpr int kSegRows = 512;              // output rows per CTA
 constexpr int kHRows = kChunk + kHalo;     // 74 moment rows held
 constexpr int kInW = 44;                   // staged input columns (42 used, float4 reads)
 constexpr int kSsimThreads = 256;
@@ -65,18 +66,43 @@ struct SsimParams {
 };
 static_assert(sizeof(SsimParams<kSsimMaxImg>) < 32000, "kernel parameters too large");
 
+// Input staging.  Samples travel as aligned 4-sample words (4 bytes for
+// 8-bit planes, 8 bytes for 16-bit ones) and become centred floats through
+// the exponent trick: 0x4B000000 | v is the float 2^23 + v, so subtracting
+// 2^23 + centre gives v - centre exactly.
 template <typename Smp>
-__device__ __forceinline__ float sample(const void* base, int64_t pitch, int y, int x) {
-  return float(reinterpret_cast<const Smp*>(static_cast<const char*>(base) + int64_t(y) * pitch)[x]);
-}
+struct Word;
+template <>
+struct Word<uint8_t> {
+  using T = unsigned;
+  __device__ static __forceinline__ T load(const void* p) { return __ldg(static_cast<const unsigned*>(p)); }
+  __device__ static __forceinline__ float get(T w, int j, float bias) {
+    return __int_as_float(int(__byte_perm(w, 0x4B000000u, 0x7440u | unsigned(j)))) - bias;
+  }
+};
+template <>
+struct Word<uint16_t> {
+  using T = uint2;
+  __device__ static __forceinline__ T load(const void* p) { return __ldg(static_cast<const uint2*>(p)); }
+  __device__ static __forceinline__ float get(T w, int j, float bias) {
+    const unsigned src = j < 2 ? w.x : w.y;
+    const unsigned lo = unsigned(2 * (j & 1));
+    return __int_as_float(int(__byte_perm(src, 0x4B000000u, 0x7400u | ((lo + 1) << 4) | lo))) - bias;
+  }
+};
+
+constexpr int kWords = (kStripCols + kHalo + 3) / 4;   // 11 words of 4 samples per staged row
+constexpr int kStageRows = kSsimThreads / kWords;      // 23 rows per staging pass
+constexpr int kStagePasses = (kHRows + kStageRows - 1) / kStageRows;  // 4
 
 template <typename Smp, bool MAP, int MAXI>
-__global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const __grid_constant__ SsimParams<MAXI> P) {
+__global__ void __launch_bounds__(kSsimThreads, sizeof(Smp) == 1 ? 3 : 2) ssim_kernel(const __grid_constant__ SsimParams<MAXI> P) {
   extern __shared__ __align__(16) float sm[];
   float* in_a = sm;                          // [kHRows][kInW]
   float* in_b = in_a + kHRows * kInW;        // [kHRows][kInW]
   float* hm = in_b + kHRows * kInW;          // [5][kHRows][kStripCols]
   const int tid = threadIdx.x;
+  using Wd = Word<Smp>;
 
   // unit -> image (largest k with unit0 <= unit)
   const int unit = blockIdx.x;
@@ -93,38 +119,67 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const __grid_constan
   const int c0 = strip * kStripCols;
   const int r_begin = seg * kSegRows;
   const int r_end = min(r_begin + kSegRows, I.mh);
+  const float bias = 8388608.f + I.centre;
 
-  float g[kWin];
+  // staging slot of this thread: word sw of rows sr, sr + 23, ...; the word
+  // is read at ws (clamped so that it holds sample w - 1 when it starts past
+  // it) and samples past the image take sample w - 1
+  const bool stager = tid < kStageRows * kWords;
+  const int sr = tid / kWords;
+  const int sw = tid - sr * kWords;
+  const int xw = c0 + 4 * sw;
+  const int ws = min(xw, (I.w - 1) & ~3);
+  int sel[4];
 #pragma unroll
-  for (int k = 0; k < kWin; ++k) g[k] = P.g[k];
+  for (int j = 0; j < 4; ++j) sel[j] = min(xw + j, I.w - 1) - ws;
+  typename Wd::T ra[kStagePasses], rb[kStagePasses];
+  auto fetch = [&](int y0, int nrows) {
+#pragma unroll
+    for (int k = 0; k < kStagePasses; ++k) {
+      const int rr = sr + k * kStageRows;
+      if (stager && rr < nrows) {
+        const int y = min(y0 + rr, I.h - 1);
+        ra[k] = Wd::load(static_cast<const char*>(I.a) + int64_t(y) * I.pa + int64_t(ws) * int64_t(sizeof(Smp)));
+        rb[k] = Wd::load(static_cast<const char*>(I.b) + int64_t(y) * I.pb + int64_t(ws) * int64_t(sizeof(Smp)));
+      }
+    }
+  };
+  auto stage = [&](int nrows) {
+#pragma unroll
+    for (int k = 0; k < kStagePasses; ++k) {
+      const int rr = sr + k * kStageRows;
+      if (stager && rr < nrows) {
+        float4 fa, fb;
+        fa.x = Wd::get(ra[k], sel[0], bias); fa.y = Wd::get(ra[k], sel[1], bias);
+        fa.z = Wd::get(ra[k], sel[2], bias); fa.w = Wd::get(ra[k], sel[3], bias);
+        fb.x = Wd::get(rb[k], sel[0], bias); fb.y = Wd::get(rb[k], sel[1], bias);
+        fb.z = Wd::get(rb[k], sel[2], bias); fb.w = Wd::get(rb[k], sel[3], bias);
+        *reinterpret_cast<float4*>(in_a + rr * kInW + 4 * sw) = fa;
+        *reinterpret_cast<float4*>(in_b + rr * kInW + 4 * sw) = fb;
+      }
+    }
+  };
 
+  fetch(r_begin, kHRows);
   float sum = 0.f;
   for (int r0 = r_begin; r0 < r_end; r0 += kChunk) {
     const bool first = r0 == r_begin;
     const int nrows = first ? kHRows : kChunk;     // moment rows to compute
     const int dst0 = first ? 0 : kHalo;            // where they go
-    const int y0 = first ? r0 : r0 + kHalo;        // their first input row
     if (!first) {
-      // keep the last 10 moment rows: rows 64..73 -> 0..9
-      for (int i = tid; i < 5 * kHalo * kStripCols; i += kSsimThreads) {
-        const int q = i / (kHalo * kStripCols);
-        const int rr = (i / kStripCols) % kHalo;
-        const int cc = i % kStripCols;
-        hm[(q * kHRows + rr) * kStripCols + cc] = hm[(q * kHRows + kChunk + rr) * kStripCols + cc];
+      // keep the last 10 moment rows: rows 64..73 -> 0..9 (float4 moves)
+      constexpr int kPer = kHalo * kStripCols / 4;  // float4 per plane
+      for (int i = tid; i < 5 * kPer; i += kSsimThreads) {
+        const int q = i / kPer;
+        const int o = i - q * kPer;
+        float4* base = reinterpret_cast<float4*>(hm + q * kHRows * kStripCols);
+        base[o] = base[kChunk * kStripCols / 4 + o];
       }
     }
-    // stage input rows y0 .. y0 + nrows - 1, columns c0 .. c0 + kInW - 1,
-    // clamped to the image (clamped samples feed only masked outputs)
-    for (int i = tid; i < nrows * kInW; i += kSsimThreads) {
-      const int rr = i / kInW;
-      const int cc = i - rr * kInW;
-      const int y = min(y0 + rr, I.h - 1);
-      const int x = min(c0 + cc, I.w - 1);
-      in_a[rr * kInW + cc] = sample<Smp>(I.a, I.pa, y, x) - I.centre;
-      in_b[rr * kInW + cc] = sample<Smp>(I.b, I.pb, y, x) - I.centre;
-    }
+    stage(nrows);
     __syncthreads();
-    // row pass: 4 adjacent columns of one row per task
+    // row pass: 4 adjacent columns of one row per task; the window is
+    // symmetric, so each tap pair is added before its weight multiplies it
     for (int task = tid; task < nrows * (kStripCols / 4); task += kSsimThreads) {
       const int rr = task >> 3;
       const int cg = task & 7;
@@ -137,31 +192,28 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const __grid_constan
         va[4 * m] = x4.x; va[4 * m + 1] = x4.y; va[4 * m + 2] = x4.z; va[4 * m + 3] = x4.w;
         vb[4 * m] = y4.x; vb[4 * m + 1] = y4.y; vb[4 * m + 2] = y4.z; vb[4 * m + 3] = y4.w;
       }
-      float hx[4], hy[4], hxx[4], hyy[4], hxy[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        hx[j] = 0.f; hy[j] = 0.f; hxx[j] = 0.f; hyy[j] = 0.f; hxy[j] = 0.f;
-#pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-          const float a = va[j + k], b = vb[j + k];
-          const float ga = g[k] * a, gb = g[k] * b;
-          hx[j] += ga;
-          hy[j] += gb;
-          hxx[j] = fmaf(ga, a, hxx[j]);
-          hyy[j] = fmaf(gb, b, hyy[j]);
-          hxy[j] = fmaf(ga, b, hxy[j]);
-        }
-      }
-      const int row = dst0 + rr;
-      float4* o = reinterpret_cast<float4*>(hm + row * kStripCols + 4 * cg);
+      float4* o = reinterpret_cast<float4*>(hm + (dst0 + rr) * kStripCols + 4 * cg);
       constexpr int kPlane = kHRows * kStripCols / 4;  // float4 per plane
-      o[0] = make_float4(hx[0], hx[1], hx[2], hx[3]);
-      o[kPlane] = make_float4(hy[0], hy[1], hy[2], hy[3]);
-      o[2 * kPlane] = make_float4(hxx[0], hxx[1], hxx[2], hxx[3]);
-      o[3 * kPlane] = make_float4(hyy[0], hyy[1], hyy[2], hyy[3]);
-      o[4 * kPlane] = make_float4(hxy[0], hxy[1], hxy[2], hxy[3]);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        float v[14];
+#pragma unroll
+        for (int i = 0; i < 14; ++i)
+          v[i] = q == 0 ? va[i] : q == 1 ? vb[i] : q == 2 ? va[i] * va[i] : q == 3 ? vb[i] * vb[i] : va[i] * vb[i];
+        float h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float acc = P.g[kHalo / 2] * v[j + kHalo / 2];
+#pragma unroll
+          for (int k = kHalo / 2 - 1; k >= 0; --k) acc = fmaf(P.g[k], v[j + k] + v[j + kHalo - k], acc);
+          h[j] = acc;
+        }
+        o[q * kPlane] = make_float4(h[0], h[1], h[2], h[3]);
+      }
     }
     __syncthreads();
+    // the next chunk's samples are fetched now and land behind the column pass
+    if (r0 + kChunk < r_end) fetch(r0 + kChunk + kHalo, kChunk);
     // column pass: column cc, output rows r0 + 8 rg .. r0 + 8 rg + 7
     {
       const int cc = tid & (kStripCols - 1);
@@ -176,7 +228,7 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const __grid_constan
         for (int i = 0; i < 8; ++i) {
           float acc = 0.f;
 #pragma unroll
-          for (int k = 0; k < kWin; ++k) acc = fmaf(g[k], v[i + k], acc);
+          for (int k = 0; k < kWin; ++k) acc = fmaf(P.g[k], v[i + k], acc);
           e[q][i] = acc;
         }
       }
@@ -193,7 +245,7 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_kernel(const __grid_constan
         const float d1 = fmaf(mx, mx, fmaf(my, my, I.c1));
         const float n2 = fmaf(2.f, sxy, I.c2);
         const float d2 = (sxx + syy) + I.c2;
-        const float s = (n1 * n2) / (d1 * d2);
+        const float s = __fdividef(n1 * n2, d1 * d2);
         if (y < r_end && x < I.mw) {
           sum += s;
           if (MAP) P.map[I.map_off + int64_t(y) * I.mw + x] = s;

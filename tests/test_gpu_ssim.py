@@ -11,8 +11,9 @@ g_n = n u / (1 - n u)).  With samples centred on c = 2^(bits-1)
   * mu = E x' + c: |dmu| <= g_30 W[|x'|] + u |mu|;
   * N1 = 2 mu_x mu_y + C1, D1 = mu_x^2 + mu_y^2 + C1, N2 = 2 s_xy + C2,
     D2 = s_x^2 + s_y^2 + C2 (constants rounded to binary32), the index
-    N1 N2 / (D1 D2) with three more roundings;
-  * |d index| <= |index| (dD1/D1 + dD2/D2 + 3u) + (dN1 |N2| + |N1| dN2) / (D1 D2),
+    N1 N2 / (D1 D2): two rounded products and a fast division (at most 2 ulp,
+    CUDA's documented bound for __fdividef in this range), 7u together;
+  * |d index| <= |index| (dD1/D1 + dD2/D2 + 7u) + (dN1 |N2| + |N1| dN2) / (D1 D2),
     with the denominators reduced by their own error bounds; the test allows
     twice that per position;
   * the mean: the mean of the per-position bounds plus 40 u (binary32 partial
@@ -78,7 +79,7 @@ def _bound(x, y, bits):
     D1l, D2l = D1 - dD1, D2 - dD2
     assert np.all(D1l > 0) and np.all(D2l > 0)
     s = N1 * N2 / (D1 * D2)
-    b = np.abs(s) * (dD1 / D1l + dD2 / D2l + 3 * U) + (dN1 * np.abs(N2) + np.abs(N1) * dN2) / (D1l * D2l)
+    b = np.abs(s) * (dD1 / D1l + dD2 / D2l + 7 * U) + (dN1 * np.abs(N2) + np.abs(N1) * dN2) / (D1l * D2l)
     return 2 * b
 
 
@@ -156,7 +157,7 @@ def test_ssim_map_and_mean(tx, shape, bits):
 def test_ssim_identity_and_symmetry(tx):
     x, y = _pair(77, 96, 130, 8)
     ms, maps = _run(tx, [(x, x), (x, y), (y, x)], [8, 8, 8])
-    assert np.all(np.abs(maps[0] - 1.0) <= 8 * U)
+    assert np.all(np.abs(maps[0] - 1.0) <= 16 * U)
     assert abs(ms[0] - 1.0) <= 1e-6
     assert abs(ms[1] - ms[2]) <= 1e-6
 
