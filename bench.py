@@ -704,6 +704,40 @@ def _traffic_per_launch():
     return int(rec["dram_bytes"] * scale)
 
 
+def run_ssim_only(args):
+    """SSIM of --frames frames against their reconstruction, --steps timed
+    launches after --warmup; prints one short JSON line (not the bench line)."""
+    import torch
+
+    from paper_1606_07414_gb300 import synth, tx16
+
+    lib = tx16.load()
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    d_in = torch.from_numpy(synth.video_frames(SEED, FRAMES, H, W, rho=0.95)).cuda()
+    d_out = torch.empty_like(d_in)
+    ins = (tx16.tx16_image * FRAMES)(*[tx16.image(d_in[i]) for i in range(FRAMES)])
+    outs = (tx16.tx16_image * FRAMES)(*[tx16.image(d_out[i]) for i in range(FRAMES)])
+    qp = (tx16.tx16_qparams * FRAMES)(*[tx16.tx16_qparams(args.q, args.r)] * FRAMES)
+    if lib.tx16_codec_batch(ins, outs, FRAMES, qp, None, None, sptr) != 0:
+        raise RuntimeError("tx16_codec_batch failed")
+    ms_t = torch.zeros(FRAMES, dtype=torch.float64, device="cuda")
+
+    def ssim():
+        st = lib.tx16_ssim(ins, outs, FRAMES, ctypes.c_void_p(ms_t.data_ptr()), None, sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_ssim")
+    for _ in range(args.warmup):
+        ssim()
+    ms = _events_time(ssim, args.steps, stream)
+    positions = FRAMES * (H - 10) * (W - 10)
+    print(json.dumps({"ssim_ms": round(ms, 4), "frames": FRAMES,
+                      "Gpositions_s": round(positions / (ms * 1e-3) / 1e9, 2),
+                      "alu_frac": round(positions * SSIM_OPS_PER_POSITION / (ms * 1e-3)
+                                        / (ALU_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6), 4),
+                      "mean_ssim": round(float(ms_t.mean().item()), 6)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -720,12 +754,16 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--quick", action="store_true", help="headline number only")
     ap.add_argument("--frames", type=int, default=FRAMES, help="smaller cases for profiling")
+    ap.add_argument("--ssim-only", action="store_true",
+                    help="time tx16_ssim alone on --frames frames and their reconstruction (profiling)")
     args = ap.parse_args()
     globals()["FRAMES"] = args.frames
     if args.warmup < 3 and args.impl == "tx16":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.ssim_only:
+        run_ssim_only(args)
     else:
         run_gpu(args)
 
