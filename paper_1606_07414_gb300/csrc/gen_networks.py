@@ -134,8 +134,8 @@ def emit(net, outputs, in_names, out_name, materialize):
         t = f"t{k}"
         if kind == "add":
             lines.append(f"const float2 {t} = __fadd2_rn({a}, {b});")
-        else:  # a - b with one rounding: fma(b, -1, a)
-            lines.append(f"const float2 {t} = __ffma2_rn({b}, pm1(), {a});")
+        else:  # a - b with one rounding
+            lines.append(f"const float2 {t} = sub2({a}, {b});")
         names[k] = t
     signs = []
     for idx, o in enumerate(outputs):
@@ -213,6 +213,10 @@ def main():
     w("namespace pairnet {")
     w("__device__ __forceinline__ float2 pm1() { return make_float2(-1.f, -1.f); }")
     w("__device__ __forceinline__ float2 pbias() { return make_float2(-16777216.f, -16777216.f); }  // -2^24")
+    w("// a - b and RD(a - b) per lane: a packed addition of the negated operand")
+    w("// (one rounding; the negation folds into the instruction)")
+    w("__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }")
+    w("__device__ __forceinline__ float2 sub2_rd(float2 a, float2 b) { return __fadd2_rd(a, make_float2(-b.x, -b.y)); }")
     w("// sign of output i encoded as bit masks (negative / known zero)")
     w("__host__ __device__ constexpr int sign_of(unsigned neg, unsigned zero, int i) {")
     w("  return ((zero >> i) & 1u) ? 0 : (((neg >> i) & 1u) ? -1 : 1);")
@@ -246,7 +250,7 @@ def main():
                 w(f"    const float2 a{i} = __fadd2_rn(__fadd2_rn(X[{i}], pbias()), X[{j}]);")
             if (8 + (7 - i)) in live_a:
                 # a[8 + k] = x[7 - k] - x[8 + k] with k = 7 - i  ->  x[i] - x[15 - i]
-                w(f"    const float2 a{8 + (7 - i)} = __ffma2_rn(X[{j}], pm1(), X[{i}]);")
+                w(f"    const float2 a{8 + (7 - i)} = sub2(X[{i}], X[{j}]);")
         for ln in lines:
             w("    " + ln)
         w("  }")

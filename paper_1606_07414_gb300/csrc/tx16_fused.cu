@@ -30,41 +30,12 @@
 #include "tx16_internal.h"
 #include "tx16_net.cuh"
 #include "tx16_pairnet.cuh"
+#include "tx16_fused_common.cuh"
 
 namespace tx16 {
 namespace {
 
 using namespace pairnet;
-
-template <int U_, int V_, class FR, class FC, class IC, class IR, int MINB>
-struct Zone {
-  static constexpr int U = U_;  // kept rows u < U
-  static constexpr int V = V_;  // kept columns v < V
-  static constexpr int kMinCtas = MINB;  // resident CTAs per SM the registers are budgeted for
-  using FwdRow = FR;
-  using FwdCol = FC;
-  using InvCol = IC;
-  using InvRow = IR;
-};
-using ZoneA = Zone<3, 4, FwdRow4, FwdCol3, InvCol3, InvRow4, 8>;        // r <= 8
-using ZoneB = Zone<5, 6, FwdRow6, FwdCol5, InvCol5, InvRow6, 8>;        // r <= 16
-using ZoneC = Zone<7, 8, FwdRow8, FwdCol7, InvCol7, InvRow8, 6>;        // r <= 32
-using ZoneD = Zone<11, 10, FwdRow10, FwdCol11, InvCol11, InvRow10, 5>;  // r <= 64
-using ZoneE = Zone<16, 16, FwdRow16, FwdCol16, InvCol16, InvRow16, 4>;  // any r
-
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-
-// 2^23 + byte k of w, as a float (exact)
-__device__ __forceinline__ float biased(unsigned w, int k) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | unsigned(k)));
-}
-
-// fl32 pair -> f16 pair with round toward zero; .x goes to the low half
-__device__ __forceinline__ unsigned cvt_rz_h2(float2 v) {
-  unsigned d;
-  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.y), "f"(v.x));
-  return d;
-}
 
 // Per-image state held in registers between image changes.
 struct ImgState {
@@ -114,22 +85,6 @@ __device__ __forceinline__ void load_image(const ImgParam* imgs, int nimg, int n
   S.h = I.colh[v];
 }
 
-// (by, bx) of block blk: umulhi quotient, exact or one short, then corrected
-__device__ __forceinline__ int2 block_coords(unsigned magic, int nbx, int blk) {
-  int q = int(__umulhi(unsigned(blk), magic));
-  int r = blk - q * nbx;
-  const bool over = r >= nbx;
-  q += over ? 1 : 0;
-  r -= over ? nbx : 0;
-  return make_int2(q, r);
-}
-
-__device__ __forceinline__ void flush_sse(unsigned long long* sse, int img, unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0 && v != 0ull) atomicAdd(sse + img, v);
-}
-
 constexpr int kSlotWords = 36;  // one column slot: 16 float2 + 4 words of padding
 
 // (image row, byte column) of row l of block blk; row -1 past the image's end
@@ -142,16 +97,6 @@ __device__ __forceinline__ int2 row_pos(unsigned magic, int nbx, int nblk, int b
 __device__ __forceinline__ uint4 load_row(const uint8_t* base, int64_t pitch, int2 rc) {
   return rc.x >= 0 ? __ldcs(reinterpret_cast<const uint4*>(base + int64_t(rc.x) * pitch + rc.y))
                    : make_uint4(0, 0, 0, 0);
-}
-
-// The image whose tile range holds tile t (binary search; tile0 ascending).
-__device__ __forceinline__ int image_of_tile(const ImgParam* imgs, int nimg, int t) {
-  int lo = 0, hi = nimg - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (imgs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 // Tile schedules.  StaticRange: a contiguous range per CTA (grid sized to the
@@ -366,7 +311,7 @@ __device__ __forceinline__ void codec_tiles(const ImgParam* imgs, int nimg, int 
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(1024.5f))
-                                                 : __ffma2_rd(z[j], pm1(), f2(1024.5f));
+                                                 : sub2_rd(f2(1024.5f), z[j]);
         const unsigned raw = cvt_rz_h2(r);
         __half2 hv = *reinterpret_cast<const __half2*>(&raw);
         hv = __hmin2(__hmax2(hv, lo), hi);
@@ -476,6 +421,8 @@ template <int MAXI>
 tx16_status launch_fused_modes(int zone, const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                                cudaStream_t stream) {
   const bool dst = imgs[0].dst != nullptr;
+  // up to 8 kept columns and no level output: one block per thread in registers
+  if (fused_bt_supports(zone, levels != nullptr)) return launch_fused_bt(zone, dst, imgs, n, sse, stream);
   if (levels != nullptr)
     return dst ? launch_fused_zone<MAXI, true, true>(zone, imgs, n, sse, levels, stream)
                : launch_fused_zone<MAXI, true, false>(zone, imgs, n, sse, levels, stream);

@@ -1,0 +1,387 @@
+// Fused codec for 8-bit planes, one 16x16 block per thread, entirely in
+// registers (zonal classes with at most 8 kept columns, no level output).
+//
+// Mapping.  A warp codes a tile of 32 consecutive blocks of one image, lane l
+// block 32 t + l, so each 16-byte row load of a warp reads 32 horizontally
+// adjacent blocks: 512 contiguous bytes.  Warps take tiles grid-stride.
+//   row pass     the block's rows two at a time: float2 = (row 2p, row 2p+1),
+//                16 samples -> the V kept columns (forward row network)
+//   column pass  the kept columns two at a time: float2 = (column 2c,
+//                column 2c+1), re-paired in registers from the row pass;
+//                forward column network, S-merged quantiser, inverse column
+//                network
+//   row pass     re-paired into (row 2p, row 2p+1) again: inverse row
+//                network, rounding, 16-byte stores, squared error
+// No shared-memory exchange and no barrier.  Shared memory holds each
+// thread's 16 input rows, double-buffered: while a tile is coded, cp.async
+// brings the warp's next tile, and the squared error reads the rows there
+// again.  A small per-warp table holds the quantiser constants of the image
+// being coded (each lane of a column pair has its own column's scale and
+// sign).
+//
+// The arithmetic is that of the two-blocks-per-pair kernel (tx16_fused.cu) on
+// differently paired lanes: the same generated networks, the same binary32
+// quantiser steps and the same exact rounding, so results are identical.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "tx16_fused_common.cuh"
+#include "tx16_internal.h"
+#include "tx16_net.cuh"
+#include "tx16_pairnet.cuh"
+
+namespace tx16 {
+namespace {
+
+constexpr int kWarpTile = 32;  // blocks per warp tile
+
+// Warps per CTA and resident CTAs per SM the registers are budgeted for, per
+// zonal class (compile-time tunable; the register limit per thread is
+// 65536 / (32 * warps * CTAs)).
+#ifndef TX16_BT_WARPS_A
+#define TX16_BT_WARPS_A 4
+#endif
+#ifndef TX16_BT_MINCTAS_A
+#define TX16_BT_MINCTAS_A 3
+#endif
+#ifndef TX16_BT_WARPS_B
+#define TX16_BT_WARPS_B 4
+#endif
+#ifndef TX16_BT_MINCTAS_B
+#define TX16_BT_MINCTAS_B 2
+#endif
+#ifndef TX16_BT_WARPS_C
+#define TX16_BT_WARPS_C 4
+#endif
+#ifndef TX16_BT_MINCTAS_C
+#define TX16_BT_MINCTAS_C 2
+#endif
+template <class Z>
+struct BtLimits;
+template <>
+struct BtLimits<ZoneA> { static constexpr int kWarps = TX16_BT_WARPS_A, kMinCtas = TX16_BT_MINCTAS_A; };
+template <>
+struct BtLimits<ZoneB> { static constexpr int kWarps = TX16_BT_WARPS_B, kMinCtas = TX16_BT_MINCTAS_B; };
+template <>
+struct BtLimits<ZoneC> { static constexpr int kWarps = TX16_BT_WARPS_C, kMinCtas = TX16_BT_MINCTAS_C; };
+
+// Quantiser constants of one image for column pairs c < NP and scale classes
+// e(u) = 0, 1, 2; lane .x is column 2c, lane .y column 2c + 1.
+template <int NP>
+struct PairConsts {
+  float2 fs[3][NP];  // quantiser: sign_v f ; no quantiser: sign_v D'_u D'_v / 256
+  float2 gg[3][NP];  // g
+  float2 gc[3][NP];  // -2^23 g
+};
+
+template <int NP>
+__device__ __forceinline__ void fill_consts(const ImgParam& I, PairConsts<NP>& Q, int lane) {
+  constexpr int kPer = 6 * NP;  // floats per table
+  const bool quant = (I.flags & kQuantFlag) != 0;
+  float* q = reinterpret_cast<float*>(&Q);
+  for (int idx = lane; idx < 3 * kPer; idx += 32) {
+    const int tab = idx / kPer;
+    const int rem = idx - tab * kPer;
+    const int e = rem / (2 * NP);
+    const int v = rem - e * 2 * NP;  // = 2 c + half
+    const int k = e + scale_class(v);
+    const float sv = ((kFwdNegMask >> v) & 1u) ? -1.f : 1.f;
+    float val;
+    if (quant) val = tab == 0 ? sv * I.f[k] : tab == 1 ? I.g[k] : -8388608.f * I.g[k];
+    else val = tab == 0 ? sv * float(1 << k) * (1.f / 256.f) : 0.f;
+    q[idx] = val;
+  }
+  __syncwarp();
+}
+
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros and
+// reads nothing.  The "memory" clobber keeps the compiler from moving shared
+// loads of the buffer being refilled across it.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Input rows: per thread 16 rows of 16 bytes per stage, laid out
+// [stage][row][thread] so that a warp's 16-byte accesses to one row are
+// contiguous.
+template <class Z>
+constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16; }
+
+template <int MAXI, class Z, bool DST>
+__global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCtas)
+    fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
+  constexpr int kBtWarps = BtLimits<Z>::kWarps;
+  constexpr int kBtThreads = 32 * kBtWarps;
+  constexpr int kStageBytes = stage_bytes<Z>();
+  constexpr int V = Z::V;
+  constexpr int NP = V / 2;
+  static_assert(V % 2 == 0, "column pairs");
+  extern __shared__ __align__(16) uint8_t rows_smem[];  // 2 stages
+  __shared__ PairConsts<NP> consts[kBtWarps];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  PairConsts<NP>& Q = consts[wib];
+  const int nw = gridDim.x * kBtWarps;
+  int t = blockIdx.x * kBtWarps + wib;
+  if (t >= P.ntiles) return;
+
+  // prefetch the 16 rows of this thread's block of tile tt (image kk) into
+  // stage st; image fields are read from the parameter bank where used
+  auto prefetch = [&](int kk, int tt, int st) {
+    const ImgParam& I = P.img[kk];
+    const int blk = (tt - I.tile0) * kWarpTile + lane;
+    const bool ok = blk < I.nblk;
+    const int2 c = ok ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
+    const uint8_t* src = static_cast<const uint8_t*>(I.src);
+    const uint8_t* g = src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16;
+    uint8_t* s = rows_smem + st * kStageBytes + threadIdx.x * 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      cp_async16(s + i * (kBtThreads * 16), ok ? g + int64_t(i) * I.src_pitch : src, ok ? 16 : 0);
+    cp_async_commit();
+  };
+  auto tile_end_of = [&](int kk) { return kk + 1 < P.nimg ? P.img[kk + 1].tile0 : P.ntiles; };
+  // column heights of image kk, 5 bits each (V <= 8: 40 bits)
+  auto heights = [&](int kk) {
+    unsigned long long hp = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) hp |= (unsigned long long)(P.img[kk].colh[v]) << (5 * v);
+    return hp;
+  };
+
+  // the image of the tile being coded (k) and of the tile being fetched (kn)
+  int k = image_of_tile(P.img, P.nimg, t);
+  int kn = k;
+  int end_k = tile_end_of(k), end_kn = end_k;
+  prefetch(k, t, 0);
+  unsigned long long hp = heights(k);
+  fill_consts<NP>(P.img[k], Q, lane);
+  unsigned long long acc = 0;
+  int stage = 0;
+
+  for (; t < P.ntiles; t += nw, stage ^= 1) {
+    // fetch the next tile of this warp while this one is coded
+    const int tn = t + nw;
+    if (tn < P.ntiles) {
+      if (tn >= end_kn) {
+        while (kn + 1 < P.nimg && P.img[kn + 1].tile0 <= tn) ++kn;
+        end_kn = tile_end_of(kn);
+      }
+      prefetch(kn, tn, stage ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    if (t >= end_k) {  // warp-uniform: a later image
+      if (P.sse) flush_sse(P.sse, P.img[k].out_index, acc);
+      acc = 0;
+      while (k + 1 < P.nimg && P.img[k + 1].tile0 <= t) ++k;
+      end_k = tile_end_of(k);
+      hp = heights(k);
+      __syncwarp();
+      fill_consts<NP>(P.img[k], Q, lane);
+    }
+    const ImgParam& I = P.img[k];
+    const bool quant = (I.flags & kQuantFlag) != 0;
+    const int blk = (t - I.tile0) * kWarpTile + lane;
+    const bool valid = blk < I.nblk;
+    const int2 c = valid ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
+    const uint8_t* rows = rows_smem + stage * kStageBytes + threadIdx.x * 16;
+
+    // ---- forward row pass: R[p][v] = (row 2p, row 2p + 1) at column v ----
+    float2 R[8][V];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const uint4 a = *reinterpret_cast<const uint4*>(rows + (2 * p) * (kBtThreads * 16));
+      const uint4 b = *reinterpret_cast<const uint4*>(rows + (2 * p + 1) * (kBtThreads * 16));
+      const unsigned wa[4] = {a.x, a.y, a.z, a.w};
+      const unsigned wb[4] = {b.x, b.y, b.z, b.w};
+      float2 X[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) X[j] = make_float2(biased(wa[j >> 2], j & 3), biased(wb[j >> 2], j & 3));
+      float2 y[16];
+      Z::FwdRow::run(X, y);
+#pragma unroll
+      for (int v = 0; v < V; ++v) R[p][v] = y[v];
+    }
+
+    // ---- column pass: column pair cp = (2 cp, 2 cp + 1) ----
+    float2 Cz[16][NP];
+#pragma unroll
+    for (int cp = 0; cp < NP; ++cp) {
+      float2 x[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float2 r0 = R[i >> 1][2 * cp], r1 = R[i >> 1][2 * cp + 1];
+        x[i] = (i & 1) ? make_float2(r0.y, r1.y) : make_float2(r0.x, r1.x);
+      }
+      float2 n[16];
+      Z::FwdCol::run(x, n);  // n[u] = FwdCol::sign(u) * (row-pass sign of v) * Y[u][v]
+      float2 w[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) w[u] = make_float2(0.f, 0.f);
+      const int h0 = int((hp >> (10 * cp)) & 31u), h1 = int((hp >> (10 * cp + 5)) & 31u);
+      static_assert(5 * V <= 64, "column heights packed in 64 bits");
+      if (quant) {
+#pragma unroll
+        for (int u = 0; u < Z::U; ++u) {
+          const int e = scale_class(u);
+          const float2 tq = __fmul2_rn(n[u], Q.fs[e][cp]);
+          const float2 a = make_float2(fabsf(tq.x), fabsf(tq.y));
+          const float2 m = __fadd2_rd(__fadd2_rd(a, f2(0.5f)), f2(8388608.f));  // 2^23 + floor(|t| + 1/2)
+          float2 q = __ffma2_rn(m, Q.gg[e][cp], Q.gc[e][cp]);                 // fl32(level * g)
+          q.x = __uint_as_float(__float_as_uint(q.x) | (__float_as_uint(tq.x) & 0x80000000u));
+          q.y = __uint_as_float(__float_as_uint(q.y) | (__float_as_uint(tq.y) & 0x80000000u));
+          w[u] = make_float2(u < h0 ? q.x : 0.f, u < h1 ? q.y : 0.f);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < Z::U; ++u) {
+          const float2 q = __fmul2_rn(n[u], Q.fs[scale_class(u)][cp]);
+          w[u] = make_float2(u < h0 ? q.x : 0.f, u < h1 ? q.y : 0.f);
+        }
+      }
+      float2 z[16];
+      Z::InvCol::run(w, z);  // z[i] = (T^t W)[i][2 cp .. 2 cp + 1] (with the network's signs)
+#pragma unroll
+      for (int i = 0; i < 16; ++i) Cz[i][cp] = z[i];
+    }
+
+    // ---- inverse row pass, rounding, store, SSE: rows 2p and 2p + 1 ----
+    unsigned s1 = 0, s2 = 0;
+    const __half2 lo = __float2half2_rn(1024.f), hi = __float2half2_rn(1279.f);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      float2 wv[16];
+#pragma unroll
+      for (int v = 0; v < 16; ++v) {
+        if (v < V) {
+          const float2 a = Cz[2 * p][v >> 1], b = Cz[2 * p + 1][v >> 1];
+          wv[v] = (v & 1) ? make_float2(a.y, b.y) : make_float2(a.x, b.x);
+        } else {
+          wv[v] = make_float2(0.f, 0.f);
+        }
+      }
+      float2 z[16];
+      Z::InvRow::run(wv, z);  // z[j] = sign[j] * X_tilde[row][j]
+      // sample = clip(floor(X + 1/2), 0, 255): the low byte of the binary16
+      // value RZ(RD(X + 1024.5)) clamped to [1024, 1279]
+      unsigned hh[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(1024.5f))
+                                                 : sub2_rd(f2(1024.5f), z[j]);
+        const unsigned raw = cvt_rz_h2(r);
+        __half2 hv = *reinterpret_cast<const __half2*>(&raw);
+        hv = __hmin2(__hmax2(hv, lo), hi);
+        hh[j] = *reinterpret_cast<const unsigned*>(&hv);
+      }
+      unsigned xa[4], xb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned t01 = __byte_perm(hh[4 * q], hh[4 * q + 1], 0x6240u);
+        const unsigned t23 = __byte_perm(hh[4 * q + 2], hh[4 * q + 3], 0x6240u);
+        xa[q] = __byte_perm(t01, t23, 0x5410u);
+        xb[q] = __byte_perm(t01, t23, 0x7632u);
+      }
+      if (DST && valid) {
+        const int64_t dp = P.img[k].dst_pitch;
+        uint8_t* drow = static_cast<uint8_t*>(P.img[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 16;
+        __stcs(reinterpret_cast<uint4*>(drow), make_uint4(xa[0], xa[1], xa[2], xa[3]));
+        __stcs(reinterpret_cast<uint4*>(drow + dp), make_uint4(xb[0], xb[1], xb[2], xb[3]));
+      }
+      // SSE = sum x^2 + sum y^2 - 2 sum x y; a block past the image's end
+      // was staged as zeros and reconstructs to zeros
+      const uint4 a = *reinterpret_cast<const uint4*>(rows + (2 * p) * (kBtThreads * 16));
+      const uint4 b = *reinterpret_cast<const uint4*>(rows + (2 * p + 1) * (kBtThreads * 16));
+      const unsigned ia[4] = {a.x, a.y, a.z, a.w}, ib[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s1 = __dp4a(ia[q], ia[q], s1);
+        s1 = __dp4a(xa[q], xa[q], s1);
+        s1 = __dp4a(ib[q], ib[q], s1);
+        s1 = __dp4a(xb[q], xb[q], s1);
+        s2 = __dp4a(ia[q], xa[q], s2);
+        s2 = __dp4a(ib[q], xb[q], s2);
+      }
+    }
+    acc += (unsigned long long)(s1 - 2u * s2);
+  }
+  if (P.sse) flush_sse(P.sse, P.img[k].out_index, acc);
+}
+
+template <int MAXI, class Z, bool DST>
+tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
+  BatchParams<MAXI> P;
+  P.nimg = n;
+  P.sse = sse;
+  P.coeffs = nullptr;
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    P.img[i] = imgs[i];
+    P.img[i].tile0 = tiles;
+    P.img[i].out_index = i;
+    tiles += (imgs[i].nblk + kWarpTile - 1) / kWarpTile;
+  }
+  P.ntiles = tiles;
+  constexpr int kBtWarps = BtLimits<Z>::kWarps;
+  constexpr int kBtThreads = 32 * kBtWarps;
+  constexpr size_t smem = 2 * size_t(stage_bytes<Z>());
+  static int occ = 0;
+  if (occ == 0) {
+    int o = 0;
+    if (cudaFuncSetAttribute(fused_bt_kernel<MAXI, Z, DST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem)) != cudaSuccess)
+      return TX16_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_kernel<MAXI, Z, DST>, kBtThreads, smem) !=
+            cudaSuccess || o < 1)
+      o = 1;
+    occ = o;
+  }
+  const int grid = std::max(1, std::min((tiles + kBtWarps - 1) / kBtWarps, occ * device_sm_count()));
+  fused_bt_kernel<MAXI, Z, DST><<<grid, kBtThreads, smem, stream>>>(P);
+  return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
+}
+
+template <int MAXI, class Z>
+tx16_status launch_bt_dst(bool dst, const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
+  return dst ? launch_bt<MAXI, Z, true>(imgs, n, sse, stream) : launch_bt<MAXI, Z, false>(imgs, n, sse, stream);
+}
+
+template <int MAXI>
+tx16_status launch_bt_zone(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
+                           cudaStream_t stream) {
+  switch (zone) {
+    case 0: return launch_bt_dst<MAXI, ZoneA>(dst, imgs, n, sse, stream);
+    case 1: return launch_bt_dst<MAXI, ZoneB>(dst, imgs, n, sse, stream);
+    case 2: return launch_bt_dst<MAXI, ZoneC>(dst, imgs, n, sse, stream);
+    default: return TX16_EINVAL;
+  }
+}
+
+}  // namespace
+
+// Zonal classes routed to this kernel (bit z for class z; compile-time
+// tunable).  Class C (8 kept columns) spills here and runs faster on the
+// pair kernel, so the default routes classes A and B only.
+#ifndef TX16_BT_ZONE_MASK
+#define TX16_BT_ZONE_MASK 0x3
+#endif
+
+bool fused_bt_supports(int zone, bool levels) {
+  return !levels && zone >= 0 && zone <= 2 && ((TX16_BT_ZONE_MASK >> zone) & 1);
+}
+
+tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
+                            cudaStream_t stream) {
+  if (n <= 8) return launch_bt_zone<8>(zone, dst, imgs, n, sse, stream);
+  return launch_bt_zone<kMaxImg>(zone, dst, imgs, n, sse, stream);
+}
+
+}  // namespace tx16

@@ -261,3 +261,63 @@ def test_wide_and_tall_images(tx):
         ref = O.codec_image(img, 16.0, 16, 8, "fp32")
         assert np.array_equal(from_dev(out, 8), ref["recon"])
         assert int(sse.item()) == ref["sse"]
+
+
+# --------------------------------------------------------------------------
+# Codec without level output (the one-block-per-thread kernel for up to 8
+# kept columns, the pair kernel beyond): several images per launch, tiles
+# that straddle images, and batches large enough that every warp codes
+# tiles of several images in turn.
+# --------------------------------------------------------------------------
+NOLEV_CASES = [(16.0, 8), (None, 8), (16.0, 16), (None, 16), (12.0, 32), (None, 32), (16.0, 64), (8.0, 200)]
+
+
+@pytest.mark.parametrize("q,r", NOLEV_CASES)
+def test_codec_without_levels_batch(tx, q, r):
+    import torch
+
+    shapes = [(16, 16), (80, 272), (48, 528), (16, 512), (160, 640), (32, 32), (32, 48), (64, 16)]
+    imgs = [synth.ar1_image(700 + i + r, h, w, 0.9 + 0.01 * i, 8) for i, (h, w) in enumerate(shapes)]
+    keep = [to_dev(im) for im in imgs]
+    outs = [empty_like_img(h, w, 8, pad=16) for h, w in shapes]
+    sse = torch.full((len(imgs),), -1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_batch([tx.image(d) for d in keep], [tx.image(o) for o in outs], [(q, r)] * len(imgs), sse=sse)
+    torch.cuda.synchronize()
+    for i, (im, (h, w)) in enumerate(zip(imgs, shapes)):
+        ref = oracle_blocks(O.image_to_blocks(im.astype(np.int64)), q, r, 8)
+        rec = from_dev(outs[i], 8)
+        assert np.array_equal(O.image_to_blocks(rec.astype(np.int64)), ref["recon"]), i
+        assert int(sse[i].item()) == O.sse(im, rec), i
+
+
+@pytest.mark.parametrize("q,r,frames", [(16.0, 16, 8), (None, 32, 5), (16.0, 8, 10)])
+def test_codec_without_levels_many_tiles(tx, q, r, frames):
+    """1920 x 1088 frames, enough tiles that each warp moves across images.
+    Sampled blocks (every tile edge of the first and last frames, and 400
+    random blocks of each frame) against the oracle; each frame's SSE
+    against the sum over the GPU's own reconstruction."""
+    import torch
+
+    H, W = 1088, 1920
+    fr = synth.video_frames(77 + r, frames, H, W, rho=0.95)
+    d_in = torch.from_numpy(fr).cuda()
+    d_out = torch.zeros_like(d_in)
+    sse = torch.full((frames,), -1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_batch([tx.image(d_in[i]) for i in range(frames)], [tx.image(d_out[i]) for i in range(frames)],
+                        [(q, r)] * frames, sse=sse)
+    torch.cuda.synchronize()
+    rec = d_out.cpu().numpy()
+    s = sse.cpu().numpy()
+    nbx, nb = W // 16, (H // 16) * (W // 16)
+    rng = np.random.default_rng(r)
+    for i in range(frames):
+        assert int(s[i]) == O.sse(fr[i], rec[i]), i
+        pick = set(rng.integers(0, nb, 400).tolist())
+        if i in (0, frames - 1):
+            pick |= {b for t in range(0, nb, 32) for b in (t, t + 31) if b < nb}
+            pick |= {nb - 1}
+        pick = np.array(sorted(pick))
+        X = np.stack([fr[i][(b // nbx) * 16:(b // nbx) * 16 + 16, (b % nbx) * 16:(b % nbx) * 16 + 16] for b in pick])
+        got = np.stack([rec[i][(b // nbx) * 16:(b // nbx) * 16 + 16, (b % nbx) * 16:(b % nbx) * 16 + 16] for b in pick])
+        ref = oracle_blocks(X.astype(np.int64), q, r, 8)
+        assert np.array_equal(got, ref["recon"]), i
