@@ -207,7 +207,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic", "config": _workload(args.q, args.r),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak["value"], "unit": "GB/s",
                      "frac": round(achieved / peak["value"], 4), "traffic": _traffic_per_launch(),
-                     "peak_source": peak["source"], "kernel": "tx16::block_kernel<uint8_t,256,codec>",
+                     "peak_source": peak["source"], "kernel": _codec_kernel_name(args.r),
                      "algorithmic_bytes_per_launch": blocks * BYTES_PER_BLOCK_CODEC},
         "gpu_launches": args.steps,
         "mean_psnr_db": round(mean_psnr, 4),
@@ -681,6 +681,16 @@ def _measured_peak():
             return {"value": float(json.load(f)["hbm_gbs"]), "source": "measured (copy, MEASURED_PEAKS.json)"}
     except (OSError, KeyError, ValueError):
         return {"value": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def _codec_kernel_name(r):
+    """The fused kernel the library picks for an 8-bit batch with zone Z_r
+    and no level output (one block per thread up to 6 kept columns)."""
+    if r <= 8:
+        return "tx16::fused_bt_kernel<256, Zone<3,4>, DST=true> (one block per thread)"
+    if r <= 16:
+        return "tx16::fused_bt_kernel<256, Zone<5,6>, DST=true> (one block per thread)"
+    return "tx16::fused_u8_kernel<256, Zone, LEV=false, DST=true> (two blocks per thread pair)"
 
 
 def _traffic_per_launch():
