@@ -37,9 +37,12 @@ namespace {
 
 constexpr int kWarpTile = 32;  // blocks per warp tile
 
-// Warps per CTA and resident CTAs per SM the registers are budgeted for, per
-// zonal class (compile-time tunable; the register limit per thread is
-// 65536 / (32 * warps * CTAs)).
+// Warps per CTA, resident CTAs per SM the registers are budgeted for, and
+// column pairs parked in shared memory, per zonal class (compile-time
+// tunable; the register limit per thread is 65536 / (32 * warps * CTAs)).
+// Measured on 1920x1088 frames: class A (4 kept columns) 3 CTAs of 4 warps;
+// classes B and C (6 and 8) 2 CTAs of 4 warps with one column pair parked,
+// which removes their register spills.
 #ifndef TX16_BT_WARPS_A
 #define TX16_BT_WARPS_A 4
 #endif
@@ -58,14 +61,28 @@ constexpr int kWarpTile = 32;  // blocks per warp tile
 #ifndef TX16_BT_MINCTAS_C
 #define TX16_BT_MINCTAS_C 2
 #endif
+#ifndef TX16_BT_CZ_SMEM_B
+#define TX16_BT_CZ_SMEM_B 1
+#endif
+#ifndef TX16_BT_CZ_SMEM_C
+#define TX16_BT_CZ_SMEM_C 1
+#endif
+// kCzSmem: the inverse column results of the first kCzSmem column pairs wait
+// in shared memory (16 float2 per thread and pair) instead of registers.
 template <class Z>
 struct BtLimits;
 template <>
-struct BtLimits<ZoneA> { static constexpr int kWarps = TX16_BT_WARPS_A, kMinCtas = TX16_BT_MINCTAS_A; };
+struct BtLimits<ZoneA> {
+  static constexpr int kWarps = TX16_BT_WARPS_A, kMinCtas = TX16_BT_MINCTAS_A, kCzSmem = 0;
+};
 template <>
-struct BtLimits<ZoneB> { static constexpr int kWarps = TX16_BT_WARPS_B, kMinCtas = TX16_BT_MINCTAS_B; };
+struct BtLimits<ZoneB> {
+  static constexpr int kWarps = TX16_BT_WARPS_B, kMinCtas = TX16_BT_MINCTAS_B, kCzSmem = TX16_BT_CZ_SMEM_B;
+};
 template <>
-struct BtLimits<ZoneC> { static constexpr int kWarps = TX16_BT_WARPS_C, kMinCtas = TX16_BT_MINCTAS_C; };
+struct BtLimits<ZoneC> {
+  static constexpr int kWarps = TX16_BT_WARPS_C, kMinCtas = TX16_BT_MINCTAS_C, kCzSmem = TX16_BT_CZ_SMEM_C;
+};
 
 // Quantiser constants of one image for column pairs c < NP and scale classes
 // e(u) = 0, 1, 2; lane .x is column 2c, lane .y column 2c + 1.
@@ -107,11 +124,27 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Shared-memory float2 through volatile accesses, so that a value parked in
+// shared memory is not forwarded back into registers by the compiler.
+__device__ __forceinline__ void st_shared_f2(void* p, float2 v) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ float2 ld_shared_f2(const void* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+
 // Input rows: per thread 16 rows of 16 bytes per stage, laid out
 // [stage][row][thread] so that a warp's 16-byte accesses to one row are
 // contiguous.
 template <class Z>
 constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16; }
+// bytes of the parked column results: 16 float2 per thread, [row][thread]
+template <class Z>
+constexpr int cz_bytes() { return BtLimits<Z>::kCzSmem * 16 * 32 * BtLimits<Z>::kWarps * 8; }
 
 template <int MAXI, class Z, bool DST>
 __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCtas)
@@ -119,6 +152,8 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
   constexpr int kBtWarps = BtLimits<Z>::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
   constexpr int kStageBytes = stage_bytes<Z>();
+  constexpr int kCzSmem = BtLimits<Z>::kCzSmem;  // parked column pairs
+  static_assert(kCzSmem < Z::V / 2, "at least one column pair stays in registers");
   constexpr int V = Z::V;
   constexpr int NP = V / 2;
   static_assert(V % 2 == 0, "column pairs");
@@ -130,6 +165,7 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
   const int nw = gridDim.x * kBtWarps;
   int t = blockIdx.x * kBtWarps + wib;
   if (t >= P.ntiles) return;
+  uint8_t* const cz_park = rows_smem + 2 * kStageBytes + threadIdx.x * 8;
 
   // prefetch the 16 rows of this thread's block of tile tt (image kk) into
   // stage st; image fields are read from the parameter bank where used
@@ -249,8 +285,13 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
       }
       float2 z[16];
       Z::InvCol::run(w, z);  // z[i] = (T^t W)[i][2 cp .. 2 cp + 1] (with the network's signs)
+      if (cp < kCzSmem) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) Cz[i][cp] = z[i];
+        for (int i = 0; i < 16; ++i) st_shared_f2(cz_park + (cp * 16 + i) * (kBtThreads * 8), z[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) Cz[i][cp] = z[i];
+      }
     }
 
     // ---- inverse row pass, rounding, store, SSE: rows 2p and 2p + 1 ----
@@ -262,7 +303,10 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
 #pragma unroll
       for (int v = 0; v < 16; ++v) {
         if (v < V) {
-          const float2 a = Cz[2 * p][v >> 1], b = Cz[2 * p + 1][v >> 1];
+          const int cp = v >> 1;
+          const bool parked = cp < kCzSmem;
+          const float2 a = parked ? ld_shared_f2(cz_park + (cp * 16 + 2 * p) * (kBtThreads * 8)) : Cz[2 * p][cp];
+          const float2 b = parked ? ld_shared_f2(cz_park + (cp * 16 + 2 * p + 1) * (kBtThreads * 8)) : Cz[2 * p + 1][cp];
           wv[v] = (v & 1) ? make_float2(a.y, b.y) : make_float2(a.x, b.x);
         } else {
           wv[v] = make_float2(0.f, 0.f);
@@ -332,7 +376,7 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
   P.ntiles = tiles;
   constexpr int kBtWarps = BtLimits<Z>::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
-  constexpr size_t smem = 2 * size_t(stage_bytes<Z>());
+  constexpr size_t smem = 2 * size_t(stage_bytes<Z>()) + size_t(cz_bytes<Z>());
   static int occ = 0;
   if (occ == 0) {
     int o = 0;
@@ -368,10 +412,9 @@ tx16_status launch_bt_zone(int zone, bool dst, const ImgParam* imgs, int n, unsi
 }  // namespace
 
 // Zonal classes routed to this kernel (bit z for class z; compile-time
-// tunable).  Class C (8 kept columns) spills here and runs faster on the
-// pair kernel, so the default routes classes A and B only.
+// tunable).
 #ifndef TX16_BT_ZONE_MASK
-#define TX16_BT_ZONE_MASK 0x3
+#define TX16_BT_ZONE_MASK 0x7
 #endif
 
 bool fused_bt_supports(int zone, bool levels) {

@@ -67,8 +67,8 @@ tx16_status launch_fused_list(int zone, bool lev, bool dst, const ImgParam* d_im
                               unsigned* counter, int chunk, int ctas_per_sm, unsigned long long* sse,
                               int32_t* levels, cudaStream_t stream);
 int fused_list_max_ctas(int zone, bool lev, bool dst);  // resident CTAs per SM
-// One-block-per-thread fused kernel (tx16_fused_bt.cu): the zonal classes it
-// is built for (by default those with at most 6 kept columns), no level output.
+// One-block-per-thread fused kernel (tx16_fused_bt.cu): zonal classes with at
+// most 8 kept columns, no level output.
 bool fused_bt_supports(int zone, bool levels);
 tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
                             cudaStream_t stream);
