@@ -584,3 +584,187 @@ def ssim_map(x: np.ndarray, y: np.ndarray, bits: int = 8) -> np.ndarray:
 def ssim(x: np.ndarray, y: np.ndarray, bits: int = 8) -> float:
     """Mean SSIM over all window positions (MSSIM)."""
     return float(np.mean(ssim_map(x, y, bits)))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1 and Sec. 3.2: the 8-point approximation T8 from which T is built
+# (14 additions), the 8x8 block codec it gives, and the mixed tiling of the
+# video experiment's second scenario (8- and 16-point transforms together).
+# ---------------------------------------------------------------------------
+def t8_stages() -> list[tuple[str, np.ndarray]]:
+    """The half of the factorisation that acts on the sums a_j = x_j +
+    x_{15-j} (the first 8 outputs of M1): M2, M3 and M4 are block diagonal
+    across the split of their 16 inputs into 0..7 and 8..15, and their
+    top-left 8 x 8 blocks form the 8-point network.  Returned in the order
+    they act."""
+    F = factor_matrices()
+    out = []
+    for name in ("M2", "M3", "M4"):
+        M = F[name]
+        if np.any(M[:8, 8:]) or np.any(M[8:, :8]):
+            raise AssertionError(f"{name} is not block diagonal across 8")
+        out.append((name, M[:8, :8].copy()))
+    return out
+
+
+def t8_output_order() -> list[int]:
+    """g8[k]: the first-half network output that P2 sends to row 2k of T.
+    The even rows of T are symmetric (T[2k][j] = T[2k][15-j]), i.e. they see
+    only the sums, so they are the 8-point transform in frequency order."""
+    P2 = factor_matrices()["P2"]
+    g8 = []
+    for k in range(8):
+        j = int(np.argmax(P2[2 * k]))  # (P2 e)[2k] = e[j]
+        if j >= 8:
+            raise AssertionError("an even row of T comes from the difference half")
+        g8.append(j)
+    return g8
+
+
+def t8_matrix() -> np.ndarray:
+    """T8 = rows g8 of M4' M3' M2' (the top-left blocks), an 8 x 8 {0, +-1}
+    matrix."""
+    G = np.eye(8, dtype=np.int64)
+    for _, M in t8_stages():
+        G = M @ G
+    return G[t8_output_order()]
+
+
+def t8_factored(x: np.ndarray) -> tuple[np.ndarray, int]:
+    """T8 x through the three stages (last axis), int64; returns (y, adds)."""
+    y = np.asarray(x, dtype=np.int64)
+    adds = 0
+    for _, M in t8_stages():
+        y, a = apply_stage(M, y)
+        adds += a
+    return y[..., t8_output_order()], adds
+
+
+def t8_transpose_factored_fp32(x: np.ndarray) -> np.ndarray:
+    """T8^t x in binary32 through the transposed stages: the inputs go to the
+    network outputs they came from (g8), then M4'^t, M3'^t, M2'^t, each output
+    one rounded addition."""
+    x = np.asarray(x, dtype=np.float32)
+    y = np.zeros_like(x)
+    y[..., t8_output_order()] = x
+    for _, M in reversed(t8_stages()):
+        y, _ = apply_stage(M.T, y, np.float32)
+    return y
+
+
+def s8_diag() -> np.ndarray:
+    """S8 = sqrt((T8 T8^t)^-1), the orthogonalising diagonal of T8 (T8 T8^t
+    is diagonal)."""
+    G = t8_matrix() @ t8_matrix().T
+    if np.any(G - np.diag(np.diag(G))):
+        raise AssertionError("T8 T8^t is not diagonal")
+    return 1.0 / np.sqrt(np.diag(G).astype(np.float64))
+
+
+def image_to_blocks8(img: np.ndarray) -> np.ndarray:
+    """Disjoint 8 x 8 blocks in raster block order, shape (nblk, 8, 8)."""
+    H, W = img.shape
+    b = np.asarray(img).reshape(H // 8, 8, W // 8, 8).transpose(0, 2, 1, 3)
+    return b.reshape(-1, 8, 8)
+
+
+def blocks8_to_image(blocks: np.ndarray, H: int, W: int) -> np.ndarray:
+    b = np.asarray(blocks).reshape(H // 8, W // 8, 8, 8).transpose(0, 2, 1, 3)
+    return b.reshape(H, W)
+
+
+def forward8(blocks: np.ndarray) -> np.ndarray:
+    """Y8 = T8 X T8^t (direct int64 products)."""
+    T8 = t8_matrix()
+    return np.matmul(np.matmul(T8, np.asarray(blocks, np.int64)), T8.T)
+
+
+def quantise8(Y: np.ndarray, q: float | None, r: int, precision: str = "fp64") -> np.ndarray:
+    """The quantiser of ``quantise`` on 8 x 8 blocks: S8 merged, the first r
+    (1..64) zig-zag cells kept; q None keeps s8_u s8_v Y8 inside the zone."""
+    Y = np.asarray(Y, dtype=np.int64)
+    mask = zonal_mask(r, 8)
+    s8 = s8_diag()
+    ss = np.outer(s8, s8)
+    if q is None:
+        return np.where(mask, ss * Y, 0.0)
+    if precision == "fp64":
+        lev = round_half_away(ss * Y / q)
+    else:
+        f32 = (ss / q).astype(np.float32)
+        lev = round_half_away((Y.astype(np.float32) * f32).astype(np.float32))
+    return np.where(mask, lev, 0).astype(np.int64)
+
+
+def inverse8_fp64(levels: np.ndarray, q: float) -> np.ndarray:
+    s8 = s8_diag()
+    W = np.outer(s8, s8) * q * np.asarray(levels, np.float64)
+    T8 = t8_matrix().astype(np.float64)
+    return np.matmul(np.matmul(T8.T, W), T8)
+
+
+def inverse8_fp32(levels: np.ndarray, q: float) -> np.ndarray:
+    """T8^t W T8 in binary32: W = fl32(level * fl32(q s8_u s8_v)), the
+    transposed network on the columns of W, then on the rows."""
+    s8 = s8_diag()
+    g32 = (q * np.outer(s8, s8)).astype(np.float32)
+    W = (np.asarray(levels, np.int64).astype(np.float32) * g32).astype(np.float32)
+    cols = t8_transpose_factored_fp32(np.swapaxes(W, -1, -2))
+    return t8_transpose_factored_fp32(np.swapaxes(cols, -1, -2))
+
+
+def inverse8_exact_zonal(Y: np.ndarray, r: int) -> np.ndarray:
+    """No quantiser: 64 X_tilde = T8^t (mask . D8 Y D8) T8 with D8 = 8 S8^2
+    (integers), returned as int64 numerators."""
+    D8 = np.rint(8.0 * s8_diag() ** 2).astype(np.int64)
+    Wn = np.where(zonal_mask(r, 8), np.asarray(Y, np.int64) * np.outer(D8, D8), 0)
+    T8 = t8_matrix()
+    return np.matmul(np.matmul(T8.T, Wn), T8)
+
+
+def pixels_from_exact64(num64: np.ndarray, bits: int) -> np.ndarray:
+    """round_half_away(num / 64), clipped, exact integers."""
+    n = np.asarray(num64, dtype=np.int64)
+    mag = (np.abs(n) + 32) // 64
+    return np.clip(np.where(n >= 0, mag, -mag), 0, (1 << bits) - 1)
+
+
+def codec_blocks8(blocks: np.ndarray, q: float | None, r: int, bits: int = 8,
+                  precision: str = "fp64") -> np.ndarray:
+    """The Sec. 3.1 codec on 8 x 8 blocks with T8: reconstructed samples."""
+    Y = forward8(blocks)
+    if q is None:
+        return pixels_from_exact64(inverse8_exact_zonal(Y, r), bits)
+    lev = quantise8(Y, q, r, precision)
+    X = inverse8_fp64(lev, q) if precision == "fp64" else inverse8_fp32(lev, q).astype(np.float64)
+    return pixels_from_float(X, bits)
+
+
+def codec_image_mixed(img: np.ndarray, q: float | None, r16: int, r8: int, bits: int = 8,
+                      mode: str = "auto", precision: str = "fp64") -> dict:
+    """Mixed 8/16 tiling (the video experiment's second scenario, Sec. 3.2):
+    every 16 x 16 region is coded either as one block with T or as four 8 x 8
+    blocks with T8.  Reading: the paper leaves the choice to the encoder (HM's
+    rate-distortion search); here it is the tiling with the smaller squared
+    error of the region, ties to 16 x 16 ('auto'), or forced ('16', '8').
+    Returns recon, the split map (one flag per region), SSE and PSNR."""
+    H, W = img.shape
+    x = np.asarray(img, dtype=np.int64)
+    rec16 = codec_image(x, q, r16, bits, precision)["recon"]
+    rec8 = blocks8_to_image(codec_blocks8(image_to_blocks8(x), q, r8, bits, precision), H, W)
+    d16 = (x - rec16) ** 2
+    d8 = (x - rec8) ** 2
+    e16 = d16.reshape(H // 16, 16, W // 16, 16).sum(axis=(1, 3))
+    e8 = d8.reshape(H // 16, 16, W // 16, 16).sum(axis=(1, 3))
+    if mode == "auto":
+        split = e8 < e16
+    elif mode == "16":
+        split = np.zeros_like(e16, dtype=bool)
+    elif mode == "8":
+        split = np.ones_like(e16, dtype=bool)
+    else:
+        raise ValueError(mode)
+    sel = np.kron(split, np.ones((16, 16), dtype=bool))
+    rec = np.where(sel, rec8, rec16)
+    e = sse(x, rec)
+    return {"recon": rec, "split": split, "sse": e, "psnr": psnr(e, H, W, bits)}

@@ -217,13 +217,48 @@ def _ssim_peak_256(m):
     m.ssim_map = ssim_map
 
 
+def _t8_wrong_output_order(m):
+    orig = m.t8_output_order
+    m.t8_output_order = lambda: (lambda g: [g[0], g[2], g[1]] + g[3:])(orig())
+
+
+def _s8_squared(m):
+    orig = m.s8_diag
+    m.s8_diag = lambda: orig() ** 2 * 2.0
+
+
+def _codec8_transposed(m):
+    m.forward8 = lambda blocks: np.matmul(np.matmul(m.t8_matrix().T, np.asarray(blocks, np.int64)), m.t8_matrix())
+
+
+def _mixed_ties_to_8(m):
+    orig = m.codec_image_mixed
+
+    def mixed(img, q, r16, r8, bits=8, mode="auto", precision="fp64"):
+        res = orig(img, q, r16, r8, bits, mode, precision)
+        if mode != "auto":
+            return res
+        a16 = orig(img, q, r16, r8, bits, "16", precision)["recon"]
+        a8 = orig(img, q, r16, r8, bits, "8", precision)["recon"]
+        x = np.asarray(img, np.int64)
+        H, W = x.shape
+        e16 = ((x - a16) ** 2).reshape(H // 16, 16, W // 16, 16).sum(axis=(1, 3))
+        e8 = ((x - a8) ** 2).reshape(H // 16, 16, W // 16, 16).sum(axis=(1, 3))
+        split = e8 <= e16
+        sel = np.kron(split, np.ones((16, 16), dtype=bool))
+        rec = np.where(sel, a8, a16)
+        return {"recon": rec, "split": split, "sse": m.sse(x, rec), "psnr": 0.0}
+    m.codec_image_mixed = mixed
+
+
 MUTANTS = [_flip_T_sign, _swap_S_entries, _reverse_P1, _M3_plus_identity,
            _transposed_forward, _zigzag_wrong_direction, _bankers_rounding,
            _quantiser_divides_by_s, _exact_inverse_wrong_D, _psnr_peak_256,
            _dequantise_drops_q, _dct_without_dc_norm, _coding_gain_arith_mean,
            _inverse_fp32_rows_use_T, _blocks_column_order, _m1_wrong_half,
            _ssim_k2_too_large, _ssim_structure_drops_two, _ssim_sigma_one, _ssim_raw_second_moments,
-           _ssim_window_unnormalised, _ssim_window_one_column_late, _ssim_peak_256]
+           _ssim_window_unnormalised, _ssim_window_one_column_late, _ssim_peak_256,
+           _t8_wrong_output_order, _s8_squared, _codec8_transposed, _mixed_ties_to_8]
 
 
 @pytest.mark.parametrize("mutate", MUTANTS, ids=[f.__name__.strip("_") for f in MUTANTS])

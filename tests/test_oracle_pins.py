@@ -296,6 +296,98 @@ def check_any_size_codec(o):
 
 
 # ----------------------------------------------------------------------------
+# Sec. 2.1 and Sec. 3.2: T8, the 8-point approximation T is built from
+# ----------------------------------------------------------------------------
+def check_t8_from_factorisation(o):
+    """T8 from the first half of M2 M3 M4 equals the printed T's even rows on
+    the first 8 columns; it costs 8 + 4 + 2 = 14 additions, the count Sec. 2.1
+    quotes for the 8-point approximation; the network equals the matrix on
+    every {0,1}^8 input; T on a symmetric input gives 2 T8 x on its even rows
+    and zero on its odd rows."""
+    T8 = o.t8_matrix()
+    assert T8.shape == (8, 8)
+    assert np.array_equal(T8, o.T[0::2, :8])
+    assert [o.stage_additions(M) for _, M in o.t8_stages()] == [8, 4, 2]
+    X = np.array([[(k >> j) & 1 for j in range(8)] for k in range(256)], dtype=np.int64)
+    y, adds = o.t8_factored(X)
+    assert adds == 14
+    assert np.array_equal(y, X @ T8.T)
+    rng = np.random.default_rng(8)
+    x8 = rng.integers(-255, 256, (50, 8))
+    y16 = np.concatenate([x8, x8[:, ::-1]], axis=1) @ o.T.T
+    assert np.array_equal(y16[:, 0::2], 2 * (x8 @ T8.T))
+    assert not np.any(y16[:, 1::2])
+    # transposed network in binary32 on small integers (exact) and on reals
+    z = rng.integers(-1000, 1000, (64, 8)).astype(np.float32)
+    assert np.array_equal(o.t8_transpose_factored_fp32(z).astype(np.float64), z.astype(np.float64) @ T8)
+    zr = rng.normal(0, 100, (64, 8)).astype(np.float32)
+    assert np.allclose(o.t8_transpose_factored_fp32(zr), zr.astype(np.float64) @ T8, rtol=1e-5, atol=1e-3)
+
+
+def check_s8(o):
+    """T8 T8^t is diagonal; S8 relates to the printed S by S[2k] = S8[k]/sqrt2
+    (the even rows of T see each sum twice); C8 = S8 T8 is orthogonal."""
+    s8 = o.s8_diag()
+    assert np.allclose(o.S_DIAG[0::2], s8 / math.sqrt(2), rtol=1e-15)
+    C8 = np.diag(s8) @ o.t8_matrix()
+    assert np.allclose(C8 @ C8.T, np.eye(8), atol=1e-14)
+
+
+def check_codec8(o):
+    """8 x 8 codec: lossless with all 64 cells and no quantiser; r = 1 gives
+    the block mean; the binary32 and float64 paths agree away from ties."""
+    blocks = o.image_to_blocks8(synth.ar1_image(81, 32, 48, 0.9).astype(np.int64))
+    assert np.array_equal(o.codec_blocks8(blocks, None, 64), blocks)
+    mean = o.round_half_away(blocks.mean(axis=(1, 2)))
+    r1 = o.codec_blocks8(blocks, None, 1)
+    assert np.array_equal(r1, np.broadcast_to(mean[:, None, None], r1.shape))
+    img = synth.ar1_image(82, 48, 64, 0.95).astype(np.int64)
+    b = o.image_to_blocks8(img)
+    assert np.array_equal(o.blocks8_to_image(b, 48, 64), img)
+    # levels: binary32 and float64 decisions differ by one at most, and only
+    # where c / q lies within a few binary32 ulps of a rounding tie
+    Y = o.forward8(b)
+    L32, L64 = o.quantise8(Y, 16.0, 10, "fp32"), o.quantise8(Y, 16.0, 10, "fp64")
+    t = np.abs(np.outer(o.s8_diag(), o.s8_diag()) * Y / 16.0)
+    d = L32 != L64
+    assert np.all(np.abs(L32 - L64) <= 1)
+    assert np.all(np.abs(t[d] - np.floor(t[d]) - 0.5) <= 2.0 ** -22 * t[d])
+    # the same levels reconstruct to the same samples in both precisions
+    # unless the float64 value lies near a rounding tie
+    X32 = o.inverse8_fp32(L64, 16.0).astype(np.float64)
+    X64 = o.inverse8_fp64(L64, 16.0)
+    p32, p64 = o.pixels_from_float(X32, 8), o.pixels_from_float(X64, 8)
+    far = np.abs(np.abs(X64) % 1.0 - 0.5) > 1e-3
+    assert np.array_equal(p32[far], p64[far])
+    assert np.max(np.abs(X32 - X64)) < 1e-3
+
+
+def check_mixed_codec(o):
+    """Mixed tiling: forcing 16 x 16 is the plain codec, forcing 8 x 8 is the
+    8 x 8 codec, and the automatic choice keeps, per region, the tiling with
+    the smaller squared error (so its total is at most either forced one)."""
+    img = synth.ar1_image(83, 48, 64, 0.95).astype(np.int64)
+    m16 = o.codec_image_mixed(img, 16.0, 16, 4, 8, "16", "fp32")
+    assert np.array_equal(m16["recon"], o.codec_image(img, 16.0, 16, 8, "fp32")["recon"])
+    m8 = o.codec_image_mixed(img, 16.0, 16, 4, 8, "8", "fp32")
+    want8 = o.blocks8_to_image(o.codec_blocks8(o.image_to_blocks8(img), 16.0, 4, 8, "fp32"), 48, 64)
+    assert np.array_equal(m8["recon"], want8)
+    ma = o.codec_image_mixed(img, 16.0, 16, 4, 8, "auto", "fp32")
+    assert ma["sse"] <= min(m16["sse"], m8["sse"])
+    # flat regions reconstruct exactly either way: a tie, kept as 16 x 16
+    flat = np.full((32, 32), 77, dtype=np.int64)
+    mf = o.codec_image_mixed(flat, None, 1, 1, 8, "auto")
+    assert mf["sse"] == 0 and not np.any(mf["split"])
+    for by in range(3):
+        for bx in range(4):
+            sl = (slice(16 * by, 16 * by + 16), slice(16 * bx, 16 * bx + 16))
+            e16 = o.sse(img[sl], m16["recon"][sl])
+            e8 = o.sse(img[sl], m8["recon"][sl])
+            assert bool(ma["split"][by, bx]) == (e8 < e16)
+            assert np.array_equal(ma["recon"][sl], m8["recon"][sl] if e8 < e16 else m16["recon"][sl])
+
+
+# ----------------------------------------------------------------------------
 # SSIM (Sec. 3.1, Fig. 2(b); Wang et al. 2004 window and constants)
 # ----------------------------------------------------------------------------
 def check_ssim_window(o):
