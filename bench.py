@@ -408,6 +408,27 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                             "GB_s": round(gbs_a, 1), "frac": round(gbs_a / peak, 4), "ms": round(ms_a, 4),
                             "launches_per_step": 3}
 
+    # -- mixed 8/16 tiling (the video experiment's second scenario): every
+    #    region coded with T and as four 8x8 blocks with T8, the better kept
+    mqp = (tx16.tx16_mixed_qparams * FRAMES)(*[tx16.tx16_mixed_qparams(args.q, args.r, max(1, args.r // 4), 0)] * FRAMES)
+    split = torch.zeros(blocks, dtype=torch.uint8, device="cuda")
+
+    def mixed():
+        st = lib.tx16_codec_mixed(ins, outs, FRAMES, ctypes.cast(mqp, ctypes.c_void_p),
+                                  ctypes.c_void_p(split.data_ptr()), ctypes.c_void_p(sse_ptr), sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_codec_mixed")
+    for _ in range(3):
+        mixed()
+    ms_m = _events_time(mixed, 10, stream)
+    sse_m = d_sse.cpu().tolist()
+    psnr_m = float(np.mean(tx16.tx16_psnr(sse_m, [ins[0]] * FRAMES)))
+    out["mixed_tiling"] = {"workload": f"{FRAMES} frames {W}x{H} uint8, q={args.q:g}, r16={args.r}, "
+                                       f"r8={max(1, args.r // 4)}, tiling chosen per 16x16 region by squared error",
+                           "Mregions_s": round(blocks / (ms_m * 1e-3) / 1e6, 1), "ms": round(ms_m, 4),
+                           "split_fraction": round(float(split.float().mean().item()), 4),
+                           "mean_psnr_db": round(psnr_m, 4)}
+
     # -- SSIM of every frame against its reconstruction (the paper's second
     #    measure): arithmetic-bound, 137.5 binary32 operations per window position
     ms_t = torch.zeros(FRAMES, dtype=torch.float64, device="cuda")

@@ -190,6 +190,38 @@ tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_image* out, int
                                 const tx16_qparams* qp, uint64_t* sse, void* stream);
 
 /*
+ * Mixed 8/16 tiling: the video experiment's second scenario (Sec. 3.2), where
+ * the 8-point approximation T8 (14 additions, Sec. 2.1; the even rows of T on
+ * the first 8 columns: the half of M2 M3 M4 that acts on the sums
+ * x_i + x_{15-i}) codes blocks beside T.  Every 16x16 region of an image is
+ * coded as one 16x16 block with T (quantiser q, zone Z_r16, as
+ * tx16_codec_batch) and as four 8x8 blocks with T8 (the same q on
+ * s8_u s8_v Y8[u][v], S8 = sqrt((T8 T8^t)^-1), zone = the first r8 cells of
+ * the 8x8 zig-zag scan; without a quantiser the exact inverse
+ * 64 X_tilde = T8^t (D8 Y8 D8) T8, D8 = 8 S8^2), and one of the two is kept:
+ *   mode 0  the tiling with the smaller squared error of the region (ties:
+ *           16x16) -- the paper leaves the choice to the encoder
+ *   mode 1  always 16x16;   mode 2  always 8x8.
+ *   in, out   as tx16_codec_batch (sides multiples of 16; out may be NULL)
+ *   qp        host array of n tx16_mixed_qparams: q (<= 0: no quantiser),
+ *             r16 in 1..256, r8 in 1..64, mode
+ *   split     device uint8, one flag per 16x16 region (1 = four 8x8 blocks),
+ *             regions in raster order, image after image; or NULL
+ *   sse       device uint64[n] or NULL: squared error of the kept tiling;
+ *             zeroed by the call
+ * Returns TX16_EINVAL (nothing launched) for a bad argument.
+ */
+typedef struct {
+  float q;
+  int32_t r16;
+  int32_t r8;
+  int32_t mode;
+} tx16_mixed_qparams;
+
+tx16_status tx16_codec_mixed(const tx16_image* in, const tx16_image* out, int32_t n,
+                             const tx16_mixed_qparams* qp, uint8_t* split, uint64_t* sse, void* stream);
+
+/*
  * SSIM, the paper's second quality measure (Sec. 3.1: Fig. 2(b) plots SSIM per
  * additive cost, Fig. 3 quotes it per image).  The paper cites Wang, Bovik,
  * Sheikh and Simoncelli (2004) without fixing window or constants; this

@@ -187,3 +187,59 @@ __host__ __device__ constexpr int scale_class(int u) {
 }
 
 }  // namespace tx16
+
+namespace tx16 {
+
+// The 8-point approximation T8 from which T is built (Sec. 2.1: 14 additions):
+// the halves of M2, M3 and M4 that act on the sums x_i + x_{15-i} (their
+// top-left 8x8 blocks), then the outputs in frequency order, taken from the
+// even rows of T:   y[k] = e[g8[k]], g8 = 0, 7, 3, 5, 1, 6, 2, 4.
+//   c[i] = x[i] + x[7-i], c[4+i] = x[3-i] - x[4+i]          (B8, 8 additions)
+//   d = (c0+c3, c1+c2, c1-c2, c0-c3, -c4, -c5, -c6, -c7)     (B4, -I4: 4)
+//   e = (d0+d1, d0-d1, -d2, d3, d4, d5, d6, -d7)             (2)
+template <typename V>
+__device__ __forceinline__ void fwd8(V (&x)[8]) {
+  V c[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    c[i] = x[i] + x[7 - i];
+    c[4 + i] = x[3 - i] - x[4 + i];
+  }
+  const V d0 = c[0] + c[3], d1 = c[1] + c[2], d2 = c[1] - c[2], d3 = c[0] - c[3];
+  // e0 = d0 + d1, e1 = d0 - d1, e2 = -d2, e3 = d3, e4..e6 = -c4..-c6, e7 = c7
+  x[0] = d0 + d1;   // e0
+  x[1] = c[7];      // e7 = -d7 = c7
+  x[2] = d3;        // e3
+  x[3] = -c[5];     // e5
+  x[4] = d0 - d1;   // e1
+  x[5] = -c[6];     // e6
+  x[6] = -d2;       // e2
+  x[7] = -c[4];     // e4
+}
+
+// x <- T8^t x: the same symmetric stages in reverse order, the outputs of the
+// forward network scattered back (e[g8[k]] = x[k]).
+template <typename V>
+__device__ __forceinline__ void inv8(V (&x)[8]) {
+  const V e0 = x[0], e7 = x[1], e3 = x[2], e5 = x[3], e1 = x[4], e6 = x[5], e2 = x[6], e4 = x[7];
+  // M4 block: d = (e0+e1, e0-e1, -e2, e3, e4, e5, e6, -e7)
+  const V d0 = e0 + e1, d1 = e0 - e1, d2 = -e2, d3 = e3;
+  // B4 and -I4: c = (d0+d3, d1+d2, d1-d2, d0-d3, -e4, -e5, -e6, e7)
+  V c[8];
+  c[0] = d0 + d3;
+  c[1] = d1 + d2;
+  c[2] = d1 - d2;
+  c[3] = d0 - d3;
+  c[4] = -e4;
+  c[5] = -e5;
+  c[6] = -e6;
+  c[7] = e7;
+  // B8
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    x[i] = c[i] + c[7 - i];
+    x[4 + i] = c[3 - i] - c[4 + i];
+  }
+}
+
+}  // namespace tx16

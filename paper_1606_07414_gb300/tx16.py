@@ -75,6 +75,8 @@ _SIGNATURES = {
                                            ctypes.POINTER(tx16_qparams), ctypes.c_void_p, ctypes.c_void_p]),
     "tx16_ssim": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image), ctypes.c_int32,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tx16_codec_mixed": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image), ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tx16_codec_batch_static": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.POINTER(tx16_image),
                                                ctypes.c_int32, ctypes.POINTER(tx16_qparams), ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
@@ -231,6 +233,28 @@ def tx16_ssim(a: Sequence, b: Sequence, mssim, map=None, stream=None, bits: int 
     lib = load()
     _check(lib.tx16_ssim(_images(a, bits), _images(b, bits), len(a), _ptr(mssim), _ptr(map), _stream(stream)),
            "tx16_ssim")
+
+
+class tx16_mixed_qparams(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_float), ("r16", ctypes.c_int32), ("r8", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+MIXED_MODES = {"auto": 0, "16": 1, "8": 2}
+
+
+def tx16_codec_mixed(inp: Sequence, out: Sequence | None, qp: Sequence[tuple], split=None, sse=None,
+                     stream=None, bits: int | None = None) -> None:
+    """Mixed 8/16 tiling.  qp: (q, r16, r8, mode) per image, mode 'auto',
+    '16' or '8' (or 0, 1, 2); split: uint8 CUDA tensor, one flag per 16x16
+    region, or None."""
+    lib = load()
+    arr = (tx16_mixed_qparams * max(1, len(qp)))()
+    for i, (q, r16, r8, mode) in enumerate(qp):
+        arr[i] = tx16_mixed_qparams(float(q) if q is not None else 0.0, int(r16), int(r8),
+                                    MIXED_MODES.get(mode, mode) if isinstance(mode, str) else int(mode))
+    out_arr = _images(out, bits) if out is not None else None
+    _check(lib.tx16_codec_mixed(_images(inp, bits), out_arr, len(inp), ctypes.cast(arr, ctypes.c_void_p),
+                                _ptr(split), _ptr(sse), _stream(stream)), "tx16_codec_mixed")
 
 
 def tx16_sse(a: Sequence, b: Sequence, sse, stream=None, bits: int | None = None) -> None:

@@ -496,3 +496,22 @@ def test_quantiser_constants_are_far_from_binary32_midpoints():
             ulp32 = np.spacing(f)
             frac = abs(float(x) - float(f)) / float(ulp32)
             assert abs(frac - 0.5) > 1e-6, (q, x)
+
+
+def test_t8_quantiser_constants_agree_with_the_library_formula():
+    """The library forms the 8 x 8 constants from s8_u s8_v = 2^(-3 + k/2)
+    (k = c(u) + c(v)) in double; the oracle from products of S8 entries.  The
+    binary32 values agree for every step size the tests use (no double value
+    within a few ulps of a binary32 midpoint)."""
+    s8 = O.s8_diag()
+    for q in (1.0, 2.0, 4.0, 5.3, 8.0, 12.0, 16.0, 32.0, 64.0):
+        for u in range(8):
+            for v in range(8):
+                c = [0, 2, 1, 2, 0, 2, 1, 2]
+                k = c[u] + c[v]
+                lib = math.ldexp(1.0, -3 + k // 2) * (math.sqrt(2.0) if k & 1 else 1.0)
+                x = s8[u] * s8[v]
+                assert np.float32(x / q) == np.float32(lib / q), (q, u, v)
+                assert np.float32(q * x) == np.float32(q * lib), (q, u, v)
+                f = np.float32(x / q)
+                assert abs(abs(float(x / q) - float(f)) / float(np.spacing(f)) - 0.5) > 1e-6
