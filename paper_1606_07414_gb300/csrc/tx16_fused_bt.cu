@@ -13,9 +13,9 @@
 //   row pass     re-paired into (row 2p, row 2p+1) again: inverse row
 //                network, rounding, 16-byte stores, squared error
 // No shared-memory exchange and no barrier.  Shared memory holds each
-// thread's 16 input rows, double-buffered: while a tile is coded, cp.async
-// brings the warp's next tile, and the squared error reads the rows there
-// again.  A small per-warp table holds the quantiser constants of the image
+// thread's 16 input rows, double-buffered for most classes: while a tile is
+// coded, cp.async brings the warp's next tile; the squared error reads the
+// rows there again.  A small per-warp table holds the quantiser constants of the image
 // being coded (each lane of a column pair has its own column's scale and
 // sign).
 //
@@ -40,9 +40,11 @@ constexpr int kWarpTile = 32;  // blocks per warp tile
 // Warps per CTA, resident CTAs per SM the registers are budgeted for, and
 // column pairs parked in shared memory, per zonal class (compile-time
 // tunable; the register limit per thread is 65536 / (32 * warps * CTAs)).
-// Measured on 1920x1088 frames: class A (4 kept columns) 3 CTAs of 4 warps;
-// classes B and C (6 and 8) 2 CTAs of 4 warps with one column pair parked,
-// which removes their register spills.
+// Measured on 1920x1088 frames: class A (4 kept columns) 3 CTAs of 4 warps,
+// two input stages; class B (6) 3 CTAs with one column pair parked and one
+// input stage (the next tile is fetched after the current one's rows are
+// used; other warps cover the latency), which fits 168 registers; class C (8)
+// 2 CTAs, one pair parked, two stages.
 #ifndef TX16_BT_WARPS_A
 #define TX16_BT_WARPS_A 4
 #endif
@@ -53,7 +55,7 @@ constexpr int kWarpTile = 32;  // blocks per warp tile
 #define TX16_BT_WARPS_B 4
 #endif
 #ifndef TX16_BT_MINCTAS_B
-#define TX16_BT_MINCTAS_B 2
+#define TX16_BT_MINCTAS_B 3
 #endif
 #ifndef TX16_BT_WARPS_C
 #define TX16_BT_WARPS_C 4
@@ -67,21 +69,33 @@ constexpr int kWarpTile = 32;  // blocks per warp tile
 #ifndef TX16_BT_CZ_SMEM_C
 #define TX16_BT_CZ_SMEM_C 1
 #endif
+#ifndef TX16_BT_STAGES_A
+#define TX16_BT_STAGES_A 2
+#endif
+#ifndef TX16_BT_STAGES_B
+#define TX16_BT_STAGES_B 1
+#endif
+#ifndef TX16_BT_STAGES_C
+#define TX16_BT_STAGES_C 2
+#endif
 // kCzSmem: the inverse column results of the first kCzSmem column pairs wait
 // in shared memory (16 float2 per thread and pair) instead of registers.
 template <class Z>
 struct BtLimits;
 template <>
 struct BtLimits<ZoneA> {
-  static constexpr int kWarps = TX16_BT_WARPS_A, kMinCtas = TX16_BT_MINCTAS_A, kCzSmem = 0;
+  static constexpr int kWarps = TX16_BT_WARPS_A, kMinCtas = TX16_BT_MINCTAS_A, kCzSmem = 0,
+                       kStages = TX16_BT_STAGES_A;
 };
 template <>
 struct BtLimits<ZoneB> {
-  static constexpr int kWarps = TX16_BT_WARPS_B, kMinCtas = TX16_BT_MINCTAS_B, kCzSmem = TX16_BT_CZ_SMEM_B;
+  static constexpr int kWarps = TX16_BT_WARPS_B, kMinCtas = TX16_BT_MINCTAS_B, kCzSmem = TX16_BT_CZ_SMEM_B,
+                       kStages = TX16_BT_STAGES_B;
 };
 template <>
 struct BtLimits<ZoneC> {
-  static constexpr int kWarps = TX16_BT_WARPS_C, kMinCtas = TX16_BT_MINCTAS_C, kCzSmem = TX16_BT_CZ_SMEM_C;
+  static constexpr int kWarps = TX16_BT_WARPS_C, kMinCtas = TX16_BT_MINCTAS_C, kCzSmem = TX16_BT_CZ_SMEM_C,
+                       kStages = TX16_BT_STAGES_C;
 };
 
 // Quantiser constants of one image for column pairs c < NP and scale classes
@@ -144,6 +158,8 @@ template <class Z>
 constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16; }
 // bytes of the parked column results: 16 float2 per thread, [row][thread]
 template <class Z>
+constexpr int stages() { return BtLimits<Z>::kStages; }
+template <class Z>
 constexpr int cz_bytes() { return BtLimits<Z>::kCzSmem * 16 * 32 * BtLimits<Z>::kWarps * 8; }
 
 template <int MAXI, class Z, bool DST>
@@ -165,7 +181,9 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
   const int nw = gridDim.x * kBtWarps;
   int t = blockIdx.x * kBtWarps + wib;
   if (t >= P.ntiles) return;
-  uint8_t* const cz_park = rows_smem + 2 * kStageBytes + threadIdx.x * 8;
+  constexpr int kStages = BtLimits<Z>::kStages;  // 2: the next tile is fetched during this one
+  static_assert(kStages == 1 || kStages == 2, "one or two input stages");
+  uint8_t* const cz_park = rows_smem + kStages * kStageBytes + threadIdx.x * 8;
 
   // prefetch the 16 rows of this thread's block of tile tt (image kk) into
   // stage st; image fields are read from the parameter bank where used
@@ -201,10 +219,10 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
   unsigned long long acc = 0;
   int stage = 0;
 
-  for (; t < P.ntiles; t += nw, stage ^= 1) {
-    // fetch the next tile of this warp while this one is coded
+  for (; t < P.ntiles; t += nw, stage ^= (kStages - 1)) {
     const int tn = t + nw;
-    if (tn < P.ntiles) {
+    if (kStages == 2 && tn < P.ntiles) {
+      // fetch the next tile of this warp while this one is coded
       if (tn >= end_kn) {
         while (kn + 1 < P.nimg && P.img[kn + 1].tile0 <= tn) ++kn;
         end_kn = tile_end_of(kn);
@@ -356,6 +374,14 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
       }
     }
     acc += (unsigned long long)(s1 - 2u * s2);
+    if (kStages == 1 && tn < P.ntiles) {
+      // one stage: the next tile's rows replace this one's once they are used
+      if (tn >= end_kn) {
+        while (kn + 1 < P.nimg && P.img[kn + 1].tile0 <= tn) ++kn;
+        end_kn = tile_end_of(kn);
+      }
+      prefetch(kn, tn, 0);
+    }
   }
   if (P.sse) flush_sse(P.sse, P.img[k].out_index, acc);
 }
@@ -376,7 +402,7 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
   P.ntiles = tiles;
   constexpr int kBtWarps = BtLimits<Z>::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
-  constexpr size_t smem = 2 * size_t(stage_bytes<Z>()) + size_t(cz_bytes<Z>());
+  constexpr size_t smem = size_t(stages<Z>()) * size_t(stage_bytes<Z>()) + size_t(cz_bytes<Z>());
   static int occ = 0;
   if (occ == 0) {
     int o = 0;
