@@ -278,14 +278,17 @@ tx16_status tx16_plan_run(tx16_plan* plan, uint64_t* sse, int32_t* levels, void*
 tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels, void* stream);
 
 /* Time the schedule candidates (resident CTAs per SM, tiles per claim) of
- * each group on the plan's own data and keep the fastest.  cache_path: a
+ * each group on the plan's own data and keep the fastest.  The schedule tuned
+ * is that of the kernel a run without levels uses (groups with at most 8 kept
+ * columns: one 16x16 block per thread, warps claiming 32-block tiles).  cache_path: a
  * text file of tuned schedules keyed by device, group and size class (read
  * and extended), or NULL.  Synchronous on `stream`; writes the outputs. */
 tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* stream);
 
 /* Introspection: number of groups and, for the first max_runs of them, the
  * zone class (0..4, -1 = general kernel), tiles, CTAs per SM (0 = all that
- * fit) and tiles per claim.  Host arrays; any of them may be NULL. */
+ * fit) and tiles per claim of the kernel a run without levels uses.  Host
+ * arrays; any of them may be NULL. */
 tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, int32_t* tiles,
                            int32_t* ctas_per_sm, int32_t* chunk, int32_t max_runs);
 

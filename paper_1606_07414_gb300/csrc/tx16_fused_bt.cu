@@ -162,9 +162,47 @@ constexpr int stages() { return BtLimits<Z>::kStages; }
 template <class Z>
 constexpr int cz_bytes() { return BtLimits<Z>::kCzSmem * 16 * 32 * BtLimits<Z>::kWarps * 8; }
 
-template <int MAXI, class Z, bool DST>
-__global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCtas)
-    fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
+// Tile schedules of one warp (every call is warp-uniform).  StaticWarps: warp
+// w takes tiles w, w + W, w + 2W, ... (W warps in the grid).  DynamicWarps:
+// the warp claims chunks of tiles from a counter of the work list, the next
+// chunk one chunk ahead, so that the next tile is known while this one runs.
+struct StaticWarps {
+  int t0, step, ntiles;
+  __device__ __forceinline__ int first() const { return t0 < ntiles ? t0 : -1; }
+  __device__ __forceinline__ int next(int t) const { return t + step < ntiles ? t + step : -1; }
+};
+
+struct DynamicWarps {
+  unsigned* counter;
+  int ntiles, chunk, cur_end, next_start;
+  __device__ __forceinline__ int claim() const {
+    unsigned v = 0;
+    if ((threadIdx.x & 31) == 0) v = atomicAdd(counter, unsigned(chunk));
+    return int(__shfl_sync(0xffffffffu, v, 0));
+  }
+  __device__ __forceinline__ int first() {
+    const int s = claim();
+    if (s >= ntiles) return -1;
+    cur_end = min(s + chunk, ntiles);
+    next_start = claim();
+    return s;
+  }
+  __device__ __forceinline__ int next(int t) {
+    if (t + 1 < cur_end) return t + 1;
+    const int s = next_start;
+    if (s >= ntiles) return -1;
+    cur_end = min(s + chunk, ntiles);
+    next_start = claim();
+    return s;
+  }
+};
+
+// The codec over the tiles a schedule hands this warp.  imgs: the launch's
+// descriptors (tile0 in warp tiles, ascending), in kernel parameters or in a
+// device work list.
+template <class Z, bool DST, class Sched>
+__device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int nimg, int ntiles,
+                                         unsigned long long* sse, Sched& sched) {
   constexpr int kBtWarps = BtLimits<Z>::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
   constexpr int kStageBytes = stage_bytes<Z>();
@@ -178,9 +216,8 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   PairConsts<NP>& Q = consts[wib];
-  const int nw = gridDim.x * kBtWarps;
-  int t = blockIdx.x * kBtWarps + wib;
-  if (t >= P.ntiles) return;
+  int t = sched.first();
+  if (t < 0) return;
   constexpr int kStages = BtLimits<Z>::kStages;  // 2: the next tile is fetched during this one
   static_assert(kStages == 1 || kStages == 2, "one or two input stages");
   uint8_t* const cz_park = rows_smem + kStages * kStageBytes + threadIdx.x * 8;
@@ -188,7 +225,7 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
   // prefetch the 16 rows of this thread's block of tile tt (image kk) into
   // stage st; image fields are read from the parameter bank where used
   auto prefetch = [&](int kk, int tt, int st) {
-    const ImgParam& I = P.img[kk];
+    const ImgParam& I = imgs[kk];
     const int blk = (tt - I.tile0) * kWarpTile + lane;
     const bool ok = blk < I.nblk;
     const int2 c = ok ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
@@ -200,31 +237,31 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
       cp_async16(s + i * (kBtThreads * 16), ok ? g + int64_t(i) * I.src_pitch : src, ok ? 16 : 0);
     cp_async_commit();
   };
-  auto tile_end_of = [&](int kk) { return kk + 1 < P.nimg ? P.img[kk + 1].tile0 : P.ntiles; };
+  auto tile_end_of = [&](int kk) { return kk + 1 < nimg ? imgs[kk + 1].tile0 : ntiles; };
   // column heights of image kk, 5 bits each (V <= 8: 40 bits)
   auto heights = [&](int kk) {
     unsigned long long hp = 0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) hp |= (unsigned long long)(P.img[kk].colh[v]) << (5 * v);
+    for (int v = 0; v < V; ++v) hp |= (unsigned long long)(imgs[kk].colh[v]) << (5 * v);
     return hp;
   };
 
   // the image of the tile being coded (k) and of the tile being fetched (kn)
-  int k = image_of_tile(P.img, P.nimg, t);
+  int k = image_of_tile(imgs, nimg, t);
   int kn = k;
   int end_k = tile_end_of(k), end_kn = end_k;
   prefetch(k, t, 0);
   unsigned long long hp = heights(k);
-  fill_consts<NP>(P.img[k], Q, lane);
+  fill_consts<NP>(imgs[k], Q, lane);
   unsigned long long acc = 0;
   int stage = 0;
 
-  for (; t < P.ntiles; t += nw, stage ^= (kStages - 1)) {
-    const int tn = t + nw;
-    if (kStages == 2 && tn < P.ntiles) {
+  while (t >= 0) {
+    const int tn = sched.next(t);
+    if (kStages == 2 && tn >= 0) {
       // fetch the next tile of this warp while this one is coded
       if (tn >= end_kn) {
-        while (kn + 1 < P.nimg && P.img[kn + 1].tile0 <= tn) ++kn;
+        kn = image_of_tile(imgs, nimg, tn);
         end_kn = tile_end_of(kn);
       }
       prefetch(kn, tn, stage ^ 1);
@@ -233,15 +270,15 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
       cp_async_wait<0>();
     }
     if (t >= end_k) {  // warp-uniform: a later image
-      if (P.sse) flush_sse(P.sse, P.img[k].out_index, acc);
+      if (sse) flush_sse(sse, imgs[k].out_index, acc);
       acc = 0;
-      while (k + 1 < P.nimg && P.img[k + 1].tile0 <= t) ++k;
+      k = image_of_tile(imgs, nimg, t);
       end_k = tile_end_of(k);
       hp = heights(k);
       __syncwarp();
-      fill_consts<NP>(P.img[k], Q, lane);
+      fill_consts<NP>(imgs[k], Q, lane);
     }
-    const ImgParam& I = P.img[k];
+    const ImgParam& I = imgs[k];
     const bool quant = (I.flags & kQuantFlag) != 0;
     const int blk = (t - I.tile0) * kWarpTile + lane;
     const bool valid = blk < I.nblk;
@@ -353,8 +390,8 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
         xb[q] = __byte_perm(t01, t23, 0x7632u);
       }
       if (DST && valid) {
-        const int64_t dp = P.img[k].dst_pitch;
-        uint8_t* drow = static_cast<uint8_t*>(P.img[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 16;
+        const int64_t dp = imgs[k].dst_pitch;
+        uint8_t* drow = static_cast<uint8_t*>(imgs[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 16;
         __stcs(reinterpret_cast<uint4*>(drow), make_uint4(xa[0], xa[1], xa[2], xa[3]));
         __stcs(reinterpret_cast<uint4*>(drow + dp), make_uint4(xb[0], xb[1], xb[2], xb[3]));
       }
@@ -374,16 +411,34 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
       }
     }
     acc += (unsigned long long)(s1 - 2u * s2);
-    if (kStages == 1 && tn < P.ntiles) {
+    if (kStages == 1 && tn >= 0) {
       // one stage: the next tile's rows replace this one's once they are used
       if (tn >= end_kn) {
-        while (kn + 1 < P.nimg && P.img[kn + 1].tile0 <= tn) ++kn;
+        kn = image_of_tile(imgs, nimg, tn);
         end_kn = tile_end_of(kn);
       }
       prefetch(kn, tn, 0);
     }
+    t = tn;
+    stage ^= (kStages - 1);
   }
-  if (P.sse) flush_sse(P.sse, P.img[k].out_index, acc);
+  if (sse) flush_sse(sse, imgs[k].out_index, acc);
+}
+
+template <int MAXI, class Z, bool DST>
+__global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCtas)
+    fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
+  StaticWarps sched{int(blockIdx.x) * BtLimits<Z>::kWarps + int(threadIdx.x >> 5),
+                    int(gridDim.x) * BtLimits<Z>::kWarps, P.ntiles};
+  bt_tiles<Z, DST>(P.img, P.nimg, P.ntiles, P.sse, sched);
+}
+
+template <class Z, bool DST>
+__global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCtas)
+    fused_bt_list_kernel(const ImgParam* __restrict__ imgs, int nimg, int ntiles, unsigned* counter, int chunk,
+                         unsigned long long* sse) {
+  DynamicWarps sched{counter, ntiles, chunk, 0, 0};
+  bt_tiles<Z, DST>(imgs, nimg, ntiles, sse, sched);
 }
 
 template <int MAXI, class Z, bool DST>
@@ -435,6 +490,40 @@ tx16_status launch_bt_zone(int zone, bool dst, const ImgParam* imgs, int n, unsi
   }
 }
 
+template <class Z, bool DST>
+tx16_status launch_bt_list(const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter, int chunk,
+                           int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
+  constexpr int kThreadsZ = 32 * BtLimits<Z>::kWarps;
+  constexpr size_t smem = size_t(stages<Z>()) * size_t(stage_bytes<Z>()) + size_t(cz_bytes<Z>());
+  static int occ = 0;
+  if (occ == 0) {
+    int o = 0;
+    if (cudaFuncSetAttribute(fused_bt_list_kernel<Z, DST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem)) != cudaSuccess)
+      return TX16_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_list_kernel<Z, DST>, kThreadsZ, smem) !=
+            cudaSuccess || o < 1)
+      o = 1;
+    occ = o;
+  }
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  const int grid = std::max(1, std::min((ntiles + BtLimits<Z>::kWarps - 1) / BtLimits<Z>::kWarps,
+                                        per_sm * device_sm_count()));
+  fused_bt_list_kernel<Z, DST><<<grid, kThreadsZ, smem, stream>>>(d_imgs, nimg, ntiles, counter, chunk, sse);
+  return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
+}
+
+template <class Z>
+int bt_list_max_ctas(bool dst) {
+  constexpr size_t smem = size_t(stages<Z>()) * size_t(stage_bytes<Z>()) + size_t(cz_bytes<Z>());
+  int o = 0;
+  auto k = dst ? fused_bt_list_kernel<Z, true> : fused_bt_list_kernel<Z, false>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 32 * BtLimits<Z>::kWarps, smem) != cudaSuccess || o < 1)
+    o = 1;
+  return o;
+}
+
 }  // namespace
 
 // Zonal classes routed to this kernel (bit z for class z; compile-time
@@ -445,6 +534,34 @@ tx16_status launch_bt_zone(int zone, bool dst, const ImgParam* imgs, int n, unsi
 
 bool fused_bt_supports(int zone, bool levels) {
   return !levels && zone >= 0 && zone <= 2 && ((TX16_BT_ZONE_MASK >> zone) & 1);
+}
+
+int bt_warp_tiles(int nblk) { return (nblk + kWarpTile - 1) / kWarpTile; }
+
+tx16_status launch_fused_bt_list(int zone, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter,
+                                 int chunk, int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
+  switch (zone) {
+    case 0:
+      return dst ? launch_bt_list<ZoneA, true>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream)
+                 : launch_bt_list<ZoneA, false>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 1:
+      return dst ? launch_bt_list<ZoneB, true>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream)
+                 : launch_bt_list<ZoneB, false>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 2:
+      return dst ? launch_bt_list<ZoneC, true>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream)
+                 : launch_bt_list<ZoneC, false>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    default:
+      return TX16_EINVAL;
+  }
+}
+
+int fused_bt_list_max_ctas(int zone, bool dst) {
+  switch (zone) {
+    case 0: return bt_list_max_ctas<ZoneA>(dst);
+    case 1: return bt_list_max_ctas<ZoneB>(dst);
+    case 2: return bt_list_max_ctas<ZoneC>(dst);
+    default: return 0;
+  }
 }
 
 tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,

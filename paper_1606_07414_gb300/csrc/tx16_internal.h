@@ -72,6 +72,13 @@ int fused_list_max_ctas(int zone, bool lev, bool dst);  // resident CTAs per SM
 bool fused_bt_supports(int zone, bool levels);
 tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
                             cudaStream_t stream);
+// Its work-list form: descriptors in device memory with tile0 in warp tiles
+// of 32 blocks (bt_warp_tiles), relative to the list and ascending; warps
+// claim `chunk` tiles at a time from *counter (zeroed before the launch).
+int bt_warp_tiles(int nblk);
+tx16_status launch_fused_bt_list(int zone, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter,
+                                 int chunk, int ctas_per_sm, unsigned long long* sse, cudaStream_t stream);
+int fused_bt_list_max_ctas(int zone, bool dst);  // resident CTAs per SM
 
 // Launchers (tx16_codec.cu).  `imgs` points at `n` ImgParam already filled in
 // (except tile0, set here), all with the same sample size.

@@ -3,7 +3,9 @@
 //
 // The work list is the table of per-image descriptors (ImgParam) in device
 // memory, grouped by zonal class, plus one tile counter per class.  CTAs of
-// the work-list kernel claim chunks of tiles from their class's counter, so
+// the work-list kernel claim chunks of tiles from their class's counter (for
+// classes up to 8 kept columns without levels, warps of the one-block-per-
+// thread kernel claim warp tiles of 32 blocks), so
 // images with more kept coefficients (dearer columns) and uneven sizes balance
 // across the SMs without any host-side partitioning.  A run is
 //   memset(sse), memset(counters), one launch per class (+ the general kernel
@@ -36,9 +38,13 @@ struct ClassRun {
   int zone;        // 0..4 fused zone class, -1: general kernel (by value, host table)
   int first;       // first descriptor of the run in the table
   int count;       // descriptors in the run
-  int ntiles;      // tiles of the run
+  int ntiles;      // tiles of the run (16 blocks, pair kernel)
   int ctas_per_sm; // 0: as many as fit
   int chunk;       // tiles per claim
+  // classes the one-block-per-thread kernel takes when no levels are asked:
+  // its own table (tile0 in warp tiles of 32 blocks) and schedule
+  bool bt;
+  int bt_ntiles, bt_ctas_per_sm, bt_chunk;
 };
 
 }  // namespace
@@ -48,8 +54,10 @@ struct tx16_plan {
   int n = 0;
   bool has_dst = false;
   std::vector<ImgParam> table;  // grouped by run; tile0 relative to the run
+  std::vector<ImgParam> bt_table;  // the same descriptors, tile0 in warp tiles
   std::vector<ClassRun> runs;
   ImgParam* d_table = nullptr;
+  ImgParam* d_bt_table = nullptr;
   unsigned* d_counters = nullptr;
   // graph of one run, keyed by the output pointers it was captured with
   cudaGraphExec_t graph = nullptr;
@@ -72,7 +80,10 @@ tx16_status run_plan(tx16_plan* p, uint64_t* sse, int32_t* levels, cudaStream_t 
   for (size_t i = 0; i < p->runs.size(); ++i) {
     const ClassRun& r = p->runs[i];
     tx16_status s;
-    if (r.zone >= 0) {
+    if (r.zone >= 0 && r.bt && levels == nullptr) {
+      s = launch_fused_bt_list(r.zone, p->has_dst, p->d_bt_table + r.first, r.count, r.bt_ntiles, p->d_counters + i,
+                               r.bt_chunk, r.bt_ctas_per_sm, s64, st);
+    } else if (r.zone >= 0) {
       s = launch_fused_list(r.zone, levels != nullptr, p->has_dst, p->d_table + r.first, r.count, r.ntiles,
                             p->d_counters + i, r.chunk, r.ctas_per_sm, s64, levels, st);
     } else {
@@ -118,30 +129,41 @@ tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_
   p->n = n;
   p->has_dst = out != nullptr;
   for (int c = -1; c <= 4; ++c) {
-    ClassRun r{c, int(p->table.size()), 0, 0, 0, 1};
+    ClassRun r{c, int(p->table.size()), 0, 0, 0, 1, c >= 0 && fused_bt_supports(c, false), 0, 0, 1};
     for (int i = 0; i < n; ++i) {
       if (cls[i] != c) continue;
       ImgParam q = params[i];
       q.tile0 = r.ntiles;
       r.ntiles += fused_tiles(q.nblk);
       p->table.push_back(q);
+      q.tile0 = r.bt_ntiles;
+      r.bt_ntiles += bt_warp_tiles(q.nblk);
+      p->bt_table.push_back(q);
       ++r.count;
     }
     if (r.count == 0) continue;
-    // default schedule: all resident CTAs, claims sized for ~8 claims per CTA
+    // default schedules: all resident CTAs, claims sized for ~8 claims per
+    // CTA (pair kernel) or per warp of 4-warp CTAs (one block per thread)
     if (c >= 0) {
       const int ctas = fused_list_max_ctas(c, false, p->has_dst) * device_sm_count();
       r.chunk = std::max(1, std::min(16, r.ntiles / std::max(1, ctas * 8)));
     }
+    if (r.bt) {
+      const int warps = fused_bt_list_max_ctas(c, p->has_dst) * device_sm_count() * 4;
+      r.bt_chunk = std::max(1, std::min(16, r.bt_ntiles / std::max(1, warps * 8)));
+    }
     p->runs.push_back(r);
   }
   if (cudaMalloc(&p->d_table, sizeof(ImgParam) * p->table.size()) != cudaSuccess ||
+      cudaMalloc(&p->d_bt_table, sizeof(ImgParam) * p->bt_table.size()) != cudaSuccess ||
       cudaMalloc(&p->d_counters, sizeof(unsigned) * std::max<size_t>(1, p->runs.size())) != cudaSuccess) {
     tx16_plan_destroy(p);
     return TX16_ENOMEM;
   }
   if (cudaMemcpy(p->d_table, p->table.data(), sizeof(ImgParam) * p->table.size(), cudaMemcpyHostToDevice) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaMemcpy(p->d_bt_table, p->bt_table.data(), sizeof(ImgParam) * p->bt_table.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
     tx16_plan_destroy(p);
     return TX16_ECUDA;
   }
@@ -162,8 +184,10 @@ tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels,
     return TX16_EINVAL;
   if (plan->graph == nullptr || plan->graph_sse != sse || plan->graph_levels != levels) {
     // occupancy queries happen on first use of a kernel: do them before capture
-    for (const ClassRun& r : plan->runs)
+    for (const ClassRun& r : plan->runs) {
       if (r.zone >= 0) fused_list_max_ctas(r.zone, levels != nullptr, plan->has_dst);
+      if (r.bt) fused_bt_list_max_ctas(r.zone, plan->has_dst);
+    }
     if (plan->graph != nullptr) {
       cudaGraphExecDestroy(plan->graph);
       plan->graph = nullptr;
@@ -216,32 +240,42 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
     std::string dev(prop.name);
     std::replace(dev.begin(), dev.end(), ' ', '_');  // keys are single words in the cache file
     char key[320];
-    std::snprintf(key, sizeof key, "%s|%d|%d|%d", dev.c_str(), r.zone, int(plan->has_dst), bucket);
+    // the schedule tuned is that of the kernel a run without levels uses
+    std::snprintf(key, sizeof key, "%s|%d|%d|%d%s", dev.c_str(), r.zone, int(plan->has_dst), bucket,
+                  r.bt ? "|bt" : "");
+    int& run_ctas = r.bt ? r.bt_ctas_per_sm : r.ctas_per_sm;
+    int& run_chunk = r.bt ? r.bt_chunk : r.chunk;
+    const int run_tiles = r.bt ? r.bt_ntiles : r.ntiles;
     bool hit = false;
     for (const std::string& c : cache) {
       int ctas = 0, chunk = 0;
       char k2[320];
       if (std::sscanf(c.c_str(), "%319s %d %d", k2, &ctas, &chunk) == 3 && std::string(k2) == key) {
-        r.ctas_per_sm = ctas;
-        r.chunk = chunk;
+        run_ctas = ctas;
+        run_chunk = chunk;
         hit = true;
       }
     }
     if (hit) continue;
-    const int maxc = fused_list_max_ctas(r.zone, false, plan->has_dst);
+    const int maxc = r.bt ? fused_bt_list_max_ctas(r.zone, plan->has_dst)
+                          : fused_list_max_ctas(r.zone, false, plan->has_dst);
+    const int claimers_per_cta = r.bt ? 4 : 1;  // warps of a one-block-per-thread CTA claim separately
     float best = 1e30f;
-    int best_ctas = r.ctas_per_sm, best_chunk = r.chunk;
+    int best_ctas = run_ctas, best_chunk = run_chunk;
     const int chunks[] = {1, 2, 4, 8, 16};
     for (int ctas = maxc; ctas >= 1 && ctas >= maxc - 4; --ctas) {
       for (int chunk : chunks) {
-        if (chunk > std::max(1, r.ntiles / (ctas * device_sm_count()))) continue;
+        if (chunk > std::max(1, run_tiles / (ctas * claimers_per_cta * device_sm_count()))) continue;
         float ms = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
           if (cudaMemsetAsync(plan->d_counters + i, 0, sizeof(unsigned), st) != cudaSuccess) return TX16_ECUDA;
           cudaEventRecord(e0, st);
-          if (launch_fused_list(r.zone, false, plan->has_dst, plan->d_table + r.first, r.count, r.ntiles,
-                                plan->d_counters + i, chunk, ctas, nullptr, nullptr, st) != TX16_OK)
-            return TX16_ECUDA;
+          const tx16_status ls =
+              r.bt ? launch_fused_bt_list(r.zone, plan->has_dst, plan->d_bt_table + r.first, r.count, r.bt_ntiles,
+                                          plan->d_counters + i, chunk, ctas, nullptr, st)
+                   : launch_fused_list(r.zone, false, plan->has_dst, plan->d_table + r.first, r.count, r.ntiles,
+                                       plan->d_counters + i, chunk, ctas, nullptr, nullptr, st);
+          if (ls != TX16_OK) return TX16_ECUDA;
           cudaEventRecord(e1, st);
           if (cudaEventSynchronize(e1) != cudaSuccess) return TX16_ECUDA;
           float t = 0.f;
@@ -255,8 +289,8 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
         }
       }
     }
-    r.ctas_per_sm = best_ctas;
-    r.chunk = best_chunk;
+    run_ctas = best_ctas;
+    run_chunk = best_chunk;
     char line[400];
     std::snprintf(line, sizeof line, "%s %d %d\n", key, best_ctas, best_chunk);
     cache.emplace_back(line);
@@ -282,10 +316,12 @@ tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, 
   if (plan == nullptr || runs == nullptr) return TX16_EINVAL;
   *runs = int32_t(plan->runs.size());
   for (int i = 0; i < *runs && i < max_runs; ++i) {
-    if (zone) zone[i] = plan->runs[i].zone;
-    if (tiles) tiles[i] = plan->runs[i].ntiles;
-    if (ctas_per_sm) ctas_per_sm[i] = plan->runs[i].ctas_per_sm;
-    if (chunk) chunk[i] = plan->runs[i].chunk;
+    // the schedule of the kernel a run without levels uses
+    const ClassRun& r = plan->runs[i];
+    if (zone) zone[i] = r.zone;
+    if (tiles) tiles[i] = r.bt ? r.bt_ntiles : r.ntiles;
+    if (ctas_per_sm) ctas_per_sm[i] = r.bt ? r.bt_ctas_per_sm : r.ctas_per_sm;
+    if (chunk) chunk[i] = r.bt ? r.bt_chunk : r.chunk;
   }
   return TX16_OK;
 }
@@ -295,6 +331,7 @@ void tx16_plan_destroy(tx16_plan* plan) {
   if (plan->graph) cudaGraphExecDestroy(plan->graph);
   if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
   if (plan->d_table) cudaFree(plan->d_table);
+  if (plan->d_bt_table) cudaFree(plan->d_bt_table);
   if (plan->d_counters) cudaFree(plan->d_counters);
   delete plan;
 }
