@@ -17,11 +17,13 @@
 // one image and walks down it in chunks of 64 rows.  Per chunk: stage the new
 // input rows (as centred floats; the words were fetched into registers during
 // the previous chunk's column pass), the row pass for 64 (first chunk 74) rows
-// of the five moment planes, then the column pass, one column and 8 rows per
-// thread.  The last 10 rows of the moment planes move to the top for the next
-// chunk.  The kernel is arithmetic-bound: 137.5 binary32 operations per output
-// (row pass 65.5: 10.5 products and 11 per moment with the window's symmetry;
-// column pass 55; the index 17) against 2 sample reads.
+// of the five moment planes, then the column pass, 4 rows of a pair of
+// columns per thread.  The last 10 rows of the moment planes move to the top
+// for the next chunk.  The kernel is arithmetic-bound: 137.5 binary32
+// operations per output (row pass 65.5: 10.5 products and 11 per moment with
+// the window's symmetry; column pass 55; the index 17) against 2 sample
+// reads; the column pass and the index run on packed pairs of columns
+// (__ffma2_rn and friends: two operations per instruction).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -214,41 +216,54 @@ __global__ void __launch_bounds__(kSsimThreads, sizeof(Smp) == 1 ? 3 : 2) ssim_k
     __syncthreads();
     // the next chunk's samples are fetched now and land behind the column pass
     if (r0 + kChunk < r_end) fetch(r0 + kChunk + kHalo, kChunk);
-    // column pass: column cc, output rows r0 + 8 rg .. r0 + 8 rg + 7
+    // column pass: columns 2 cp and 2 cp + 1 as one packed pair (each lane
+    // the same binary32 operations as a scalar pass), output rows
+    // r0 + 4 rg .. r0 + 4 rg + 3
     {
-      const int cc = tid & (kStripCols - 1);
-      const int rg = tid >> 5;
-      float e[5][8];
+      const int cp = tid & 15;
+      const int rg = tid >> 4;
+      float2 e[5][4];
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
-        float v[8 + kHalo];
+        float2 v[4 + kHalo];
 #pragma unroll
-        for (int m = 0; m < 8 + kHalo; ++m) v[m] = hm[(q * kHRows + 8 * rg + m) * kStripCols + cc];
+        for (int m = 0; m < 4 + kHalo; ++m)
+          v[m] = *reinterpret_cast<const float2*>(hm + (q * kHRows + 4 * rg + m) * kStripCols + 2 * cp);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float acc = 0.f;
+        for (int i = 0; i < 4; ++i) {
+          float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int k = 0; k < kWin; ++k) acc = fmaf(P.g[k], v[i + k], acc);
+          for (int k = 0; k < kWin; ++k) acc = __ffma2_rn(make_float2(P.g[k], P.g[k]), v[i + k], acc);
           e[q][i] = acc;
         }
       }
-      const int x = c0 + cc;
+      const int x = c0 + 2 * cp;
+      const float2 centre = make_float2(I.centre, I.centre);
+      const float2 c1 = make_float2(I.c1, I.c1), c2 = make_float2(I.c2, I.c2);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int y = r0 + 8 * rg + i;
-        const float mxp = e[0][i], myp = e[1][i];
-        const float sxx = fmaf(-mxp, mxp, e[2][i]);
-        const float syy = fmaf(-myp, myp, e[3][i]);
-        const float sxy = fmaf(-mxp, myp, e[4][i]);
-        const float mx = mxp + I.centre, my = myp + I.centre;
-        const float n1 = fmaf(2.f * mx, my, I.c1);
-        const float d1 = fmaf(mx, mx, fmaf(my, my, I.c1));
-        const float n2 = fmaf(2.f, sxy, I.c2);
-        const float d2 = (sxx + syy) + I.c2;
-        const float s = __fdividef(n1 * n2, d1 * d2);
-        if (y < r_end && x < I.mw) {
-          sum += s;
-          if (MAP) P.map[I.map_off + int64_t(y) * I.mw + x] = s;
+      for (int i = 0; i < 4; ++i) {
+        const int y = r0 + 4 * rg + i;
+        const float2 mxp = e[0][i], myp = e[1][i];
+        const float2 nmx = make_float2(-mxp.x, -mxp.y), nmy = make_float2(-myp.x, -myp.y);
+        const float2 sxx = __ffma2_rn(nmx, mxp, e[2][i]);
+        const float2 syy = __ffma2_rn(nmy, myp, e[3][i]);
+        const float2 sxy = __ffma2_rn(nmx, myp, e[4][i]);
+        const float2 mx = __fadd2_rn(mxp, centre), my = __fadd2_rn(myp, centre);
+        const float2 n1 = __ffma2_rn(__fadd2_rn(mx, mx), my, c1);  // mx + mx = 2 mx exactly
+        const float2 d1 = __ffma2_rn(mx, mx, __ffma2_rn(my, my, c1));
+        const float2 n2 = __ffma2_rn(make_float2(2.f, 2.f), sxy, c2);
+        const float2 d2 = __fadd2_rn(__fadd2_rn(sxx, syy), c2);
+        const float2 num = __fmul2_rn(n1, n2), den = __fmul2_rn(d1, d2);
+        const float sa = __fdividef(num.x, den.x), sb = __fdividef(num.y, den.y);
+        if (y < r_end) {
+          if (x < I.mw) {
+            sum += sa;
+            if (MAP) P.map[I.map_off + int64_t(y) * I.mw + x] = sa;
+          }
+          if (x + 1 < I.mw) {
+            sum += sb;
+            if (MAP) P.map[I.map_off + int64_t(y) * I.mw + x + 1] = sb;
+          }
         }
       }
     }

@@ -16,8 +16,8 @@ g_n = n u / (1 - n u)).  With samples centred on c = 2^(bits-1)
   * |d index| <= |index| (dD1/D1 + dD2/D2 + 7u) + (dN1 |N2| + |N1| dN2) / (D1 D2),
     with the denominators reduced by their own error bounds; the test allows
     twice that per position;
-  * the mean: the mean of the per-position bounds plus 40 u (binary32 partial
-    sums of at most 32 indices per thread before the binary64 reduction).
+  * the mean: the mean of the per-position bounds plus 72 u (binary32 partial
+    sums of at most 64 indices per thread before the binary64 reduction).
 """
 import numpy as np
 import pytest
@@ -139,7 +139,7 @@ def _check(pair, bits, mssim, smap):
     assert smap.shape == want.shape
     err = np.abs(smap - want)
     assert np.all(err <= b), f"max excess {np.max(err - b)} at {np.unravel_index(np.argmax(err - b), b.shape)}"
-    assert abs(mssim - want.mean()) <= b.mean() + 40 * U
+    assert abs(mssim - want.mean()) <= b.mean() + 72 * U
 
 
 SIZES = [((11, 11), 8), ((64, 64), 8), ((75, 140), 8), ((300, 47), 8), ((270, 300), 8),
