@@ -114,3 +114,46 @@ def test_serve_create_rejects_malformed_config_before_any_device_call(lib):
     h = ctypes.c_void_p()
     for bad in (b"{", b"[1]", b'{"streams": }', b'{"streams" 3}', b'{streams: 3}'):
         assert lib.tx16_serve_create(bad, ctypes.byref(h)) == 1  # TX16_EINVAL
+
+
+def test_new_entry_points_reject_bad_arguments_before_any_device_call(lib):
+    """tx16_codec_any_size, tx16_ssim, tx16_codec_mixed and tx16_zonal_sweep
+    check their arguments on the host and launch nothing on error."""
+    from paper_1606_07414_gb300 import tx16
+
+    E = tx16.TX16_EINVAL
+    dev = ctypes.c_void_p(0x20000)
+    qp = (tx16.tx16_qparams * 1)(tx16.tx16_qparams(8.0, 16))
+    # any size: sides need not be multiples of 16, but pitch rules hold
+    assert lib.tx16_codec_any_size((tx16.tx16_image * 1)(_img(37, 50, pitch=40)), None, 1, qp, None, None) == E
+    assert lib.tx16_codec_any_size((tx16.tx16_image * 1)(_img(37, 50, pitch=32)), None, 1, qp, None, None) == E
+    assert lib.tx16_codec_any_size((tx16.tx16_image * 1)(_img(0, 50, pitch=48)), None, 1, qp, None, None) == E
+    assert lib.tx16_codec_any_size((tx16.tx16_image * 1)(_img(37, 50, pitch=48)),
+                                   (tx16.tx16_image * 1)(_img(36, 50, pitch=48)), 1, qp, None, None) == E
+    assert lib.tx16_codec_any_size((tx16.tx16_image * 1)(_img(37, 50, pitch=48)), None, 1, qp,
+                                   ctypes.c_void_p(0x20004), None) == E
+    # SSIM: both sides at least 11, equal shapes and depths
+    a = (tx16.tx16_image * 1)(_img(10, 32, pitch=16))
+    b = (tx16.tx16_image * 1)(_img(32, 32))
+    c = (tx16.tx16_image * 1)(_img(32, 32, bits=10, pitch=64))
+    assert lib.tx16_ssim(a, a, 1, dev, None, None) == E
+    assert lib.tx16_ssim(b, c, 1, dev, None, None) == E
+    assert lib.tx16_ssim(b, b, 1, None, None, None) == E
+    assert lib.tx16_ssim(b, b, 1, ctypes.c_void_p(0x20004), None, None) == E
+    # mixed tiling: r16 in 1..256, r8 in 1..64, mode 0..2, finite q
+    good = (tx16.tx16_image * 1)(_img(32, 32))
+    for q, r16, r8, mode in [(8.0, 0, 4, 0), (8.0, 16, 0, 0), (8.0, 16, 65, 0), (8.0, 16, 4, 3),
+                             (float("inf"), 16, 4, 0)]:
+        m = (tx16.tx16_mixed_qparams * 1)(tx16.tx16_mixed_qparams(q, r16, r8, mode))
+        assert lib.tx16_codec_mixed(good, None, 1, ctypes.cast(m, ctypes.c_void_p), None, None, None) == E
+    m = (tx16.tx16_mixed_qparams * 1)(tx16.tx16_mixed_qparams(8.0, 16, 4, 0))
+    assert lib.tx16_codec_mixed((tx16.tx16_image * 1)(_img(30, 32)), None, 1,
+                                ctypes.cast(m, ctypes.c_void_p), None, None, None) == E
+    # zonal sweep: 1 <= nr <= 16, r in 1..256
+    rl = (ctypes.c_int32 * 17)(*([16] * 17))
+    assert lib.tx16_zonal_sweep(good, 1, rl, 17, dev, None) == E
+    assert lib.tx16_zonal_sweep(good, 1, (ctypes.c_int32 * 1)(0), 1, dev, None) == E
+    assert lib.tx16_zonal_sweep(good, 1, (ctypes.c_int32 * 1)(257), 1, dev, None) == E
+    # empty batches are valid no-ops
+    assert lib.tx16_codec_any_size(good, None, 0, qp, None, None) == tx16.TX16_OK
+    assert lib.tx16_codec_mixed(good, None, 0, ctypes.cast(m, ctypes.c_void_p), None, None, None) == tx16.TX16_OK
