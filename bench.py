@@ -706,11 +706,10 @@ def _measured_peak():
 
 def _codec_kernel_name(r):
     """The fused kernel the library picks for an 8-bit batch with zone Z_r
-    and no level output (one block per thread up to 6 kept columns)."""
-    if r <= 8:
-        return "tx16::fused_bt_kernel<256, Zone<3,4>, DST=true> (one block per thread)"
-    if r <= 16:
-        return "tx16::fused_bt_kernel<256, Zone<5,6>, DST=true> (one block per thread)"
+    and no level output (one block per thread up to 8 kept columns)."""
+    for rmax, zone in ((8, "Zone<3,4>"), (16, "Zone<5,6>"), (32, "Zone<7,8>")):
+        if r <= rmax:
+            return f"tx16::fused_bt_kernel<256, {zone}, DST=true> (one block per thread)"
     return "tx16::fused_u8_kernel<256, Zone, LEV=false, DST=true> (two blocks per thread pair)"
 
 
