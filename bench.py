@@ -408,6 +408,34 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                             "GB_s": round(gbs_a, 1), "frac": round(gbs_a / peak, 4), "ms": round(ms_a, 4),
                             "launches_per_step": 3}
 
+    # -- 10-bit 3840 x 2160 frames (uint16 samples, 1 KB per block in and
+    #    out): the fused 16-bit path against the general kernel
+    n10, H10, W10 = 64, 2160, 3840
+    f10 = torch.from_numpy(synth_frames_10bit(n10, H10, W10).view(np.int16)).cuda()
+    o10 = torch.empty_like(f10)
+    in10 = (tx16.tx16_image * n10)(*[tx16.image(f10[i], 10) for i in range(n10)])
+    out10 = (tx16.tx16_image * n10)(*[tx16.image(o10[i], 10) for i in range(n10)])
+    sse10 = torch.zeros(n10, dtype=torch.int64, device="cuda")
+    blocks10 = n10 * (H10 // 16) * (W10 // 16)
+    res10 = {}
+    for label, qv in (("fused", 64.0), ("general", 0.01)):
+        qp10 = (tx16.tx16_qparams * n10)(*[tx16.tx16_qparams(qv, args.r)] * n10)
+
+        def c10():
+            st = lib.tx16_codec_batch(in10, out10, n10, qp10, ctypes.c_void_p(sse10.data_ptr()), None, sptr)
+            if st != 0:
+                raise tx16.Tx16Error(st, "tx16_codec_batch")
+        for _ in range(3):
+            c10()
+        ms10 = _events_time(c10, 10, stream)
+        gbs10 = blocks10 * 1024 / (ms10 * 1e-3) / 1e9
+        res10[label] = {"q": qv, "Mblocks_s": round(blocks10 / (ms10 * 1e-3) / 1e6, 1), "GB_s": round(gbs10, 1),
+                        "frac": round(gbs10 / peak, 4), "ms": round(ms10, 4)}
+    out["frames_10bit"] = {"workload": f"{n10} frames {W10}x{H10} 10-bit in uint16, r={args.r}; q = 64 on the "
+                                       "fused 16-bit path, q = 0.01 (below its range) on the general kernel",
+                           **res10}
+    del f10, o10
+
     # -- mixed 8/16 tiling (the video experiment's second scenario): every
     #    region coded with T and as four 8x8 blocks with T8, the better kept
     mqp = (tx16.tx16_mixed_qparams * FRAMES)(*[tx16.tx16_mixed_qparams(args.q, args.r, max(1, args.r // 4), 0)] * FRAMES)
@@ -468,6 +496,13 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
         frames_np = h_in[: args.cpu_frames].numpy()
         out["cpu_baseline"] = cpu_oracle_rate(frames_np, args.q, args.r)
     return out
+
+
+def synth_frames_10bit(n, h, w):
+    """n 10-bit frames (uint16), the same AR(1) video model at 10 bits."""
+    from paper_1606_07414_gb300 import synth
+
+    return synth.video_frames(SEED + 10, n, h, w, rho=0.95, bits=10)
 
 
 def _gen_field(job):

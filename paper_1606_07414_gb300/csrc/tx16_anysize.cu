@@ -5,12 +5,13 @@
 // written and counted in the squared error.
 //
 // Each image is split on the host into its interior of whole blocks, which
-// the ordinary codec kernels handle (the fused pair kernel for 8-bit
-// samples), and at most two edge strips -- the last, partial block column
-// (full height) and the last, partial block row (interior width) -- which the
-// kernel below codes with the replication done in its loads: a row below the
-// image reads the last row instead, and samples right of the image take the
-// value of the last column.  Both launches add into the image's SSE slot.
+// the ordinary codec kernels handle (a fused kernel where the samples and the
+// step suit it, the general kernel otherwise), and at most two edge strips --
+// the last, partial block column (full height) and the last, partial block
+// row (interior width) -- which the kernel below codes with the replication
+// done in its loads: a row below the image reads the last row instead, and
+// samples right of the image take the value of the last column.  Both
+// launches add into the image's SSE slot.
 //
 // The strip kernel has the general kernel's mapping (16 threads per block,
 // int32 forward, binary32 or exact inverse).  Colour images are coded plane
@@ -260,21 +261,16 @@ extern "C" tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_imag
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (sse != nullptr && cudaMemsetAsync(sse, 0, sizeof(uint64_t) * size_t(n), st) != cudaSuccess) return TX16_ECUDA;
   unsigned long long* s64 = reinterpret_cast<unsigned long long*>(sse);
-  // interiors: runs of consecutive images with an interior and one kernel
+  // interiors: runs of consecutive images that have one, by kernel
   int s = 0;
   while (s < n) {
     if (inner[s].nblk == 0) {
       ++s;
       continue;
     }
-    const bool fast = in[s].bits == 8 && fused_eligible(inner[s]);
     int e = s + 1;
-    while (e < n && inner[e].nblk > 0 && (in[e].bits == 8 && fused_eligible(inner[e])) == fast &&
-           sample_bytes(in[e].bits) == sample_bytes(in[s].bits))
-      ++e;
-    const tx16_status r = fast ? launch_fused_u8(inner.data() + s, e - s, s64 ? s64 + s : nullptr, nullptr, st)
-                               : launch_blocks(kOpCodec, sample_bytes(in[s].bits), inner.data() + s, e - s,
-                                               s64 ? s64 + s : nullptr, nullptr, st);
+    while (e < n && inner[e].nblk > 0) ++e;
+    const tx16_status r = launch_codec_runs(inner.data() + s, e - s, s64 ? s64 + s : nullptr, nullptr, st);
     if (r != TX16_OK) return r;
     s = e;
   }

@@ -124,6 +124,36 @@ static tx16_status launch_runs(Op op, const tx16_image* imgs, std::vector<ImgPar
 
 using namespace tx16;
 
+namespace tx16 {
+
+// Runs of consecutive images by kernel: the fused 8-bit kernels (steps of
+// q >= kFusedMinQ or no quantiser), the fused 16-bit path (9..12-bit samples
+// with a quantiser of q >= 2^(bits-8) kFusedMinQ), the general block kernel
+// for the rest.  sse[i] belongs to P[i]; levels (or null) are block-major in
+// the order of P.
+tx16_status launch_codec_runs(ImgParam* P, int n, unsigned long long* sse, int32_t* levels, cudaStream_t st) {
+  auto kind = [&](const ImgParam& p) {
+    if ((p.flags & 0xff) == 8) return fused_eligible(p) ? 1 : 0;
+    return fused_bt16_eligible(p) ? 2 : 0;
+  };
+  int s = 0;
+  while (s < n) {
+    const int ks = kind(P[s]);
+    const int sb = sample_bytes(P[s].flags & 0xff);
+    int e = s + 1;
+    while (e < n && kind(P[e]) == ks && sample_bytes(P[e].flags & 0xff) == sb) ++e;
+    unsigned long long* ss = sse ? sse + s : nullptr;
+    const tx16_status r = ks == 1   ? launch_fused_u8(P + s, e - s, ss, levels, st)
+                          : ks == 2 ? launch_fused_u16(P + s, e - s, ss, levels, st)
+                                    : launch_blocks(kOpCodec, sb, P + s, e - s, ss, levels, st);
+    if (r != TX16_OK) return r;
+    s = e;
+  }
+  return TX16_OK;
+}
+
+}  // namespace tx16
+
 extern "C" {
 
 const char* tx16_status_str(tx16_status s) {
@@ -216,23 +246,8 @@ tx16_status tx16_codec_batch(const tx16_image* in, const tx16_image* out, int32_
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (sse != nullptr && cudaMemsetAsync(sse, 0, sizeof(uint64_t) * size_t(n), st) != cudaSuccess)
     return TX16_ECUDA;
-  // 8-bit runs whose steps suit the fused pair kernel go there; the rest
-  // (16-bit samples, q below kFusedMinQ) take the general block kernel
   unsigned long long* s64 = reinterpret_cast<unsigned long long*>(sse);
-  int s = 0;
-  while (s < n) {
-    const bool fast = in[s].bits == 8 && (qp[s].q <= 0.f || qp[s].q >= kFusedMinQ);
-    int e = s + 1;
-    while (e < n && (in[e].bits == 8 && (qp[e].q <= 0.f || qp[e].q >= kFusedMinQ)) == fast &&
-           sample_bytes(in[e].bits) == sample_bytes(in[s].bits))
-      ++e;
-    const tx16_status r = fast ? launch_fused_u8(P.data() + s, e - s, s64 ? s64 + s : nullptr, levels, st)
-                               : launch_blocks(kOpCodec, sample_bytes(in[s].bits), P.data() + s, e - s,
-                                               s64 ? s64 + s : nullptr, levels, st);
-    if (r != TX16_OK) return r;
-    s = e;
-  }
-  return TX16_OK;
+  return launch_codec_runs(P.data(), n, s64, levels, st);
 }
 
 tx16_status tx16_sse(const tx16_image* a, const tx16_image* b, int32_t n, uint64_t* sse, void* stream) {

@@ -154,13 +154,35 @@ __device__ __forceinline__ float2 ld_shared_f2(const void* p) {
 // Input rows: per thread 16 rows of 16 bytes per stage, laid out
 // [stage][row][thread] so that a warp's 16-byte accesses to one row are
 // contiguous.
-template <class Z>
-constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16; }
+template <class Z, int SB = 1>
+constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16 * SB; }
 // bytes of the parked column results: 16 float2 per thread, [row][thread]
-template <class Z>
-constexpr int stages() { return BtLimits<Z>::kStages; }
+// input stages: the class's setting for 8-bit samples; one stage for 16-bit
+// samples (two stages of 32-byte rows would leave one CTA per SM)
+template <class Z, int SB = 1>
+constexpr int stages() { return SB == 1 ? BtLimits<Z>::kStages : 1; }
 template <class Z>
 constexpr int cz_bytes() { return BtLimits<Z>::kCzSmem * 16 * 32 * BtLimits<Z>::kWarps * 8; }
+
+// The 4 * SB words of staged row `row` of this thread (slots row * SB + h).
+template <int SB>
+__device__ __forceinline__ void load_row_words(const uint8_t* rows, int row, int slot_bytes, unsigned (&w)[4 * SB]) {
+#pragma unroll
+  for (int h = 0; h < SB; ++h) {
+    const uint4 v = *reinterpret_cast<const uint4*>(rows + (row * SB + h) * slot_bytes);
+    w[4 * h] = v.x;
+    w[4 * h + 1] = v.y;
+    w[4 * h + 2] = v.z;
+    w[4 * h + 3] = v.w;
+  }
+}
+
+// 2^23 + sample j of a staged row, as a float (exact for samples < 2^16)
+template <int SB>
+__device__ __forceinline__ float biased_sample(const unsigned (&w)[4 * SB], int j) {
+  if (SB == 1) return biased(w[j >> 2], j & 3);
+  return __uint_as_float(__byte_perm(w[j >> 1], 0x4B000000u, (j & 1) ? 0x7532u : 0x7510u));
+}
 
 // Tile schedules of one warp (every call is warp-uniform).  StaticWarps: warp
 // w takes tiles w, w + W, w + 2W, ... (W warps in the grid).  DynamicWarps:
@@ -200,12 +222,16 @@ struct DynamicWarps {
 // The codec over the tiles a schedule hands this warp.  imgs: the launch's
 // descriptors (tile0 in warp tiles, ascending), in kernel parameters or in a
 // device work list.
-template <class Z, bool DST, class Sched>
+// SB: bytes per sample (1: 8-bit planes; 2: 9..12-bit planes in uint16).
+// Staged rows: slot (row * SB + half) holds 16 bytes of each thread's row.
+template <class Z, bool DST, int SB, class Sched>
 __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int nimg, int ntiles,
                                          unsigned long long* sse, Sched& sched) {
+  static_assert(SB == 1 || SB == 2, "8- or 16-bit samples");
   constexpr int kBtWarps = BtLimits<Z>::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
-  constexpr int kStageBytes = stage_bytes<Z>();
+  constexpr int kStageBytes = stage_bytes<Z, SB>();
+  constexpr int kSlot = kBtThreads * 16;  // bytes of one staged slot
   constexpr int kCzSmem = BtLimits<Z>::kCzSmem;  // parked column pairs
   static_assert(kCzSmem < Z::V / 2, "at least one column pair stays in registers");
   constexpr int V = Z::V;
@@ -218,7 +244,7 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
   PairConsts<NP>& Q = consts[wib];
   int t = sched.first();
   if (t < 0) return;
-  constexpr int kStages = BtLimits<Z>::kStages;  // 2: the next tile is fetched during this one
+  constexpr int kStages = stages<Z, SB>();  // 2: the next tile is fetched during this one
   static_assert(kStages == 1 || kStages == 2, "one or two input stages");
   uint8_t* const cz_park = rows_smem + kStages * kStageBytes + threadIdx.x * 8;
 
@@ -230,11 +256,13 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
     const bool ok = blk < I.nblk;
     const int2 c = ok ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
     const uint8_t* src = static_cast<const uint8_t*>(I.src);
-    const uint8_t* g = src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16;
+    const uint8_t* g = src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16 * SB;
     uint8_t* s = rows_smem + st * kStageBytes + threadIdx.x * 16;
 #pragma unroll
     for (int i = 0; i < 16; ++i)
-      cp_async16(s + i * (kBtThreads * 16), ok ? g + int64_t(i) * I.src_pitch : src, ok ? 16 : 0);
+#pragma unroll
+      for (int h = 0; h < SB; ++h)
+        cp_async16(s + (i * SB + h) * kSlot, ok ? g + int64_t(i) * I.src_pitch + 16 * h : src, ok ? 16 : 0);
     cp_async_commit();
   };
   auto tile_end_of = [&](int kk) { return kk + 1 < nimg ? imgs[kk + 1].tile0 : ntiles; };
@@ -283,19 +311,18 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
     const int blk = (t - I.tile0) * kWarpTile + lane;
     const bool valid = blk < I.nblk;
     const int2 c = valid ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
-    const uint8_t* rows = rows_smem + stage * kStageBytes + threadIdx.x * 16;
+    const uint8_t* rows = rows_smem + stage * kStageBytes + threadIdx.x * 16;  // slot 0 of this thread
 
     // ---- forward row pass: R[p][v] = (row 2p, row 2p + 1) at column v ----
     float2 R[8][V];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
-      const uint4 a = *reinterpret_cast<const uint4*>(rows + (2 * p) * (kBtThreads * 16));
-      const uint4 b = *reinterpret_cast<const uint4*>(rows + (2 * p + 1) * (kBtThreads * 16));
-      const unsigned wa[4] = {a.x, a.y, a.z, a.w};
-      const unsigned wb[4] = {b.x, b.y, b.z, b.w};
+      unsigned wa[4 * SB], wb[4 * SB];
+      load_row_words<SB>(rows, 2 * p, kSlot, wa);
+      load_row_words<SB>(rows, 2 * p + 1, kSlot, wb);
       float2 X[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) X[j] = make_float2(biased(wa[j >> 2], j & 3), biased(wb[j >> 2], j & 3));
+      for (int j = 0; j < 16; ++j) X[j] = make_float2(biased_sample<SB>(wa, j), biased_sample<SB>(wb, j));
       float2 y[16];
       Z::FwdRow::run(X, y);
 #pragma unroll
@@ -369,48 +396,90 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
       }
       float2 z[16];
       Z::InvRow::run(wv, z);  // z[j] = sign[j] * X_tilde[row][j]
-      // sample = clip(floor(X + 1/2), 0, 255): the low byte of the binary16
-      // value RZ(RD(X + 1024.5)) clamped to [1024, 1279]
-      unsigned hh[16];
+      if (SB == 1) {
+        // sample = clip(floor(X + 1/2), 0, 255): the low byte of the binary16
+        // value RZ(RD(X + 1024.5)) clamped to [1024, 1279]
+        unsigned hh[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(1024.5f))
-                                                 : sub2_rd(f2(1024.5f), z[j]);
-        const unsigned raw = cvt_rz_h2(r);
-        __half2 hv = *reinterpret_cast<const __half2*>(&raw);
-        hv = __hmin2(__hmax2(hv, lo), hi);
-        hh[j] = *reinterpret_cast<const unsigned*>(&hv);
-      }
-      unsigned xa[4], xb[4];
+        for (int j = 0; j < 16; ++j) {
+          const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(1024.5f))
+                                                   : sub2_rd(f2(1024.5f), z[j]);
+          const unsigned raw = cvt_rz_h2(r);
+          __half2 hv = *reinterpret_cast<const __half2*>(&raw);
+          hv = __hmin2(__hmax2(hv, lo), hi);
+          hh[j] = *reinterpret_cast<const unsigned*>(&hv);
+        }
+        unsigned xa[4], xb[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const unsigned t01 = __byte_perm(hh[4 * q], hh[4 * q + 1], 0x6240u);
-        const unsigned t23 = __byte_perm(hh[4 * q + 2], hh[4 * q + 3], 0x6240u);
-        xa[q] = __byte_perm(t01, t23, 0x5410u);
-        xb[q] = __byte_perm(t01, t23, 0x7632u);
-      }
-      if (DST && valid) {
-        const int64_t dp = imgs[k].dst_pitch;
-        uint8_t* drow = static_cast<uint8_t*>(imgs[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 16;
-        __stcs(reinterpret_cast<uint4*>(drow), make_uint4(xa[0], xa[1], xa[2], xa[3]));
-        __stcs(reinterpret_cast<uint4*>(drow + dp), make_uint4(xb[0], xb[1], xb[2], xb[3]));
-      }
-      // SSE = sum x^2 + sum y^2 - 2 sum x y; a block past the image's end
-      // was staged as zeros and reconstructs to zeros
-      const uint4 a = *reinterpret_cast<const uint4*>(rows + (2 * p) * (kBtThreads * 16));
-      const uint4 b = *reinterpret_cast<const uint4*>(rows + (2 * p + 1) * (kBtThreads * 16));
-      const unsigned ia[4] = {a.x, a.y, a.z, a.w}, ib[4] = {b.x, b.y, b.z, b.w};
+        for (int q = 0; q < 4; ++q) {
+          const unsigned t01 = __byte_perm(hh[4 * q], hh[4 * q + 1], 0x6240u);
+          const unsigned t23 = __byte_perm(hh[4 * q + 2], hh[4 * q + 3], 0x6240u);
+          xa[q] = __byte_perm(t01, t23, 0x5410u);
+          xb[q] = __byte_perm(t01, t23, 0x7632u);
+        }
+        if (DST && valid) {
+          const int64_t dp = imgs[k].dst_pitch;
+          uint8_t* drow = static_cast<uint8_t*>(imgs[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 16;
+          __stcs(reinterpret_cast<uint4*>(drow), make_uint4(xa[0], xa[1], xa[2], xa[3]));
+          __stcs(reinterpret_cast<uint4*>(drow + dp), make_uint4(xb[0], xb[1], xb[2], xb[3]));
+        }
+        // SSE = sum x^2 + sum y^2 - 2 sum x y; a block past the image's end
+        // was staged as zeros and reconstructs to zeros
+        const uint4 a = *reinterpret_cast<const uint4*>(rows + (2 * p) * kSlot);
+        const uint4 b = *reinterpret_cast<const uint4*>(rows + (2 * p + 1) * kSlot);
+        const unsigned ia[4] = {a.x, a.y, a.z, a.w}, ib[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        s1 = __dp4a(ia[q], ia[q], s1);
-        s1 = __dp4a(xa[q], xa[q], s1);
-        s1 = __dp4a(ib[q], ib[q], s1);
-        s1 = __dp4a(xb[q], xb[q], s1);
-        s2 = __dp4a(ia[q], xa[q], s2);
-        s2 = __dp4a(ib[q], xb[q], s2);
+        for (int q = 0; q < 4; ++q) {
+          s1 = __dp4a(ia[q], ia[q], s1);
+          s1 = __dp4a(xa[q], xa[q], s1);
+          s1 = __dp4a(ib[q], ib[q], s1);
+          s1 = __dp4a(xb[q], xb[q], s1);
+          s2 = __dp4a(ia[q], xa[q], s2);
+          s2 = __dp4a(ib[q], xb[q], s2);
+        }
+      } else {
+        // sample = clip(floor(X + 1/2), 0, peak): R = RD(X + 1024.5), then
+        // RD(R + 2^23) = 2^23 + floor(R) exactly (floor(RD(v)) = floor(v));
+        // its bits, clamped as integers to [2^23 + 1024, 2^23 + 1024 + peak]
+        // (bits of positive floats are ordered), less 2^23 + 1024
+        const int peak = (1 << (imgs[k].flags & 0xff)) - 1;
+        const int bmin = 0x4B000400, bmax = 0x4B000400 + peak;
+        unsigned ya[8], yb[8];  // reconstructed rows 2p and 2p + 1, two samples per word
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          int va[2], vb[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float2 r = Z::InvRow::sign(j + e) >= 0 ? __fadd2_rd(z[j + e], f2(1024.5f))
+                                                         : sub2_rd(f2(1024.5f), z[j + e]);
+            const float2 m = __fadd2_rd(r, f2(8388608.f));
+            va[e] = min(max(__float_as_int(m.x), bmin), bmax) - bmin;
+            vb[e] = min(max(__float_as_int(m.y), bmin), bmax) - bmin;
+          }
+          ya[j >> 1] = unsigned(va[0]) | (unsigned(va[1]) << 16);
+          yb[j >> 1] = unsigned(vb[0]) | (unsigned(vb[1]) << 16);
+        }
+        if (DST && valid) {
+          const int64_t dp = imgs[k].dst_pitch;
+          uint8_t* drow = static_cast<uint8_t*>(imgs[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 32;
+          __stcs(reinterpret_cast<uint4*>(drow), make_uint4(ya[0], ya[1], ya[2], ya[3]));
+          __stcs(reinterpret_cast<uint4*>(drow) + 1, make_uint4(ya[4], ya[5], ya[6], ya[7]));
+          __stcs(reinterpret_cast<uint4*>(drow + dp), make_uint4(yb[0], yb[1], yb[2], yb[3]));
+          __stcs(reinterpret_cast<uint4*>(drow + dp) + 1, make_uint4(yb[4], yb[5], yb[6], yb[7]));
+        }
+        // SSE: integer differences of the staged samples and the reconstruction
+        unsigned wa[8], wb[8];
+        load_row_words<2>(rows, 2 * p, kSlot, wa);
+        load_row_words<2>(rows, 2 * p + 1, kSlot, wb);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int d0 = int(wa[q] & 0xffffu) - int(ya[q] & 0xffffu), d1 = int(wa[q] >> 16) - int(ya[q] >> 16);
+          const int d2 = int(wb[q] & 0xffffu) - int(yb[q] & 0xffffu), d3 = int(wb[q] >> 16) - int(yb[q] >> 16);
+          s1 += unsigned(d0 * d0) + unsigned(d1 * d1) + unsigned(d2 * d2) + unsigned(d3 * d3);
+        }
       }
     }
-    acc += (unsigned long long)(s1 - 2u * s2);
+    acc += SB == 1 ? (unsigned long long)(s1 - 2u * s2) : (unsigned long long)s1;
     if (kStages == 1 && tn >= 0) {
       // one stage: the next tile's rows replace this one's once they are used
       if (tn >= end_kn) {
@@ -425,12 +494,18 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
   if (sse) flush_sse(sse, imgs[k].out_index, acc);
 }
 
-template <int MAXI, class Z, bool DST>
-__global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCtas)
+// resident CTAs per SM the registers are budgeted for: the class's setting
+// for 8-bit samples, at most 2 for 16-bit samples (wider staging, more live
+// values in the rounding)
+template <class Z, int SB>
+constexpr int min_ctas() { return SB == 1 ? BtLimits<Z>::kMinCtas : (BtLimits<Z>::kMinCtas < 2 ? BtLimits<Z>::kMinCtas : 2); }
+
+template <int MAXI, class Z, bool DST, int SB>
+__global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, min_ctas<Z, SB>())
     fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
   StaticWarps sched{int(blockIdx.x) * BtLimits<Z>::kWarps + int(threadIdx.x >> 5),
                     int(gridDim.x) * BtLimits<Z>::kWarps, P.ntiles};
-  bt_tiles<Z, DST>(P.img, P.nimg, P.ntiles, P.sse, sched);
+  bt_tiles<Z, DST, SB>(P.img, P.nimg, P.ntiles, P.sse, sched);
 }
 
 template <class Z, bool DST>
@@ -438,10 +513,10 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
     fused_bt_list_kernel(const ImgParam* __restrict__ imgs, int nimg, int ntiles, unsigned* counter, int chunk,
                          unsigned long long* sse) {
   DynamicWarps sched{counter, ntiles, chunk, 0, 0};
-  bt_tiles<Z, DST>(imgs, nimg, ntiles, sse, sched);
+  bt_tiles<Z, DST, 1>(imgs, nimg, ntiles, sse, sched);
 }
 
-template <int MAXI, class Z, bool DST>
+template <int MAXI, class Z, bool DST, int SB>
 tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
   BatchParams<MAXI> P;
   P.nimg = n;
@@ -457,35 +532,36 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
   P.ntiles = tiles;
   constexpr int kBtWarps = BtLimits<Z>::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
-  constexpr size_t smem = size_t(stages<Z>()) * size_t(stage_bytes<Z>()) + size_t(cz_bytes<Z>());
+  constexpr size_t smem =
+      size_t(stages<Z, SB>()) * size_t(stage_bytes<Z, SB>()) + size_t(cz_bytes<Z>());
   static int occ = 0;
   if (occ == 0) {
     int o = 0;
-    if (cudaFuncSetAttribute(fused_bt_kernel<MAXI, Z, DST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(fused_bt_kernel<MAXI, Z, DST, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(smem)) != cudaSuccess)
       return TX16_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_kernel<MAXI, Z, DST>, kBtThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_kernel<MAXI, Z, DST, SB>, kBtThreads, smem) !=
             cudaSuccess || o < 1)
       o = 1;
     occ = o;
   }
   const int grid = std::max(1, std::min((tiles + kBtWarps - 1) / kBtWarps, occ * device_sm_count()));
-  fused_bt_kernel<MAXI, Z, DST><<<grid, kBtThreads, smem, stream>>>(P);
+  fused_bt_kernel<MAXI, Z, DST, SB><<<grid, kBtThreads, smem, stream>>>(P);
   return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
 }
 
-template <int MAXI, class Z>
+template <int MAXI, class Z, int SB>
 tx16_status launch_bt_dst(bool dst, const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
-  return dst ? launch_bt<MAXI, Z, true>(imgs, n, sse, stream) : launch_bt<MAXI, Z, false>(imgs, n, sse, stream);
+  return dst ? launch_bt<MAXI, Z, true, SB>(imgs, n, sse, stream) : launch_bt<MAXI, Z, false, SB>(imgs, n, sse, stream);
 }
 
-template <int MAXI>
+template <int MAXI, int SB>
 tx16_status launch_bt_zone(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
                            cudaStream_t stream) {
   switch (zone) {
-    case 0: return launch_bt_dst<MAXI, ZoneA>(dst, imgs, n, sse, stream);
-    case 1: return launch_bt_dst<MAXI, ZoneB>(dst, imgs, n, sse, stream);
-    case 2: return launch_bt_dst<MAXI, ZoneC>(dst, imgs, n, sse, stream);
+    case 0: return launch_bt_dst<MAXI, ZoneA, SB>(dst, imgs, n, sse, stream);
+    case 1: return launch_bt_dst<MAXI, ZoneB, SB>(dst, imgs, n, sse, stream);
+    case 2: return launch_bt_dst<MAXI, ZoneC, SB>(dst, imgs, n, sse, stream);
     default: return TX16_EINVAL;
   }
 }
@@ -566,8 +642,33 @@ int fused_bt_list_max_ctas(int zone, bool dst) {
 
 tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
                             cudaStream_t stream) {
-  if (n <= 8) return launch_bt_zone<8>(zone, dst, imgs, n, sse, stream);
-  return launch_bt_zone<kMaxImg>(zone, dst, imgs, n, sse, stream);
+  if (n <= 8) return launch_bt_zone<8, 1>(zone, dst, imgs, n, sse, stream);
+  return launch_bt_zone<kMaxImg, 1>(zone, dst, imgs, n, sse, stream);
+}
+
+bool fused_bt16_eligible(const ImgParam& p) {
+  const int bits = p.flags & 0xff;
+  // a quantiser (the exact no-quantiser inverse needs the integer kernel
+  // beyond 8 bits) with |Y f| + 1/2 < 2^23 for the rounding trick:
+  // q >= 2^(bits - 8) / 256
+  return bits > 8 && bits <= 12 && (p.flags & kQuantFlag) && p.g[0] * 16.0f >= kFusedMinQ * float(1 << (bits - 8));
+}
+
+tx16_status launch_fused_u16(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
+                             cudaStream_t stream) {
+  for (int s = 0; s < n; s += kMaxImg) {
+    const int m = std::min(kMaxImg, n - s);
+    const int zone = fused_zone_class(imgs + s, m);
+    const bool dst = imgs[s].dst != nullptr;
+    ImgParam* mut = const_cast<ImgParam*>(imgs + s);
+    const tx16_status st =
+        fused_bt_supports(zone, levels != nullptr)
+            ? (m <= 8 ? launch_bt_zone<8, 2>(zone, dst, imgs + s, m, sse ? sse + s : nullptr, stream)
+                      : launch_bt_zone<kMaxImg, 2>(zone, dst, imgs + s, m, sse ? sse + s : nullptr, stream))
+            : launch_blocks(kOpCodec, 2, mut, m, sse ? sse + s : nullptr, levels, stream);
+    if (st != TX16_OK) return st;
+  }
+  return TX16_OK;
 }
 
 }  // namespace tx16

@@ -79,6 +79,12 @@ int bt_warp_tiles(int nblk);
 tx16_status launch_fused_bt_list(int zone, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter,
                                  int chunk, int ctas_per_sm, unsigned long long* sse, cudaStream_t stream);
 int fused_bt_list_max_ctas(int zone, bool dst);  // resident CTAs per SM
+// 9..12-bit planes (uint16 samples) with a quantiser of q >= 2^(bits-8)/256:
+// the one-block-per-thread kernel for zonal classes up to 8 kept columns and
+// no levels, the general kernel otherwise.
+bool fused_bt16_eligible(const ImgParam& p);
+tx16_status launch_fused_u16(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
+                             cudaStream_t stream);
 
 // Launchers (tx16_codec.cu).  `imgs` points at `n` ImgParam already filled in
 // (except tile0, set here), all with the same sample size.
@@ -88,5 +94,9 @@ tx16_status launch_quantise(const int32_t* coeffs, int64_t nblk, const ImgParam&
                             int32_t* levels, cudaStream_t stream);
 
 int device_sm_count();
+
+// The codec over n images by runs of the kernel that suits them (fused 8-bit,
+// fused 16-bit, general); tx16_capi.cu.
+tx16_status launch_codec_runs(ImgParam* P, int n, unsigned long long* sse, int32_t* levels, cudaStream_t st);
 
 }  // namespace tx16

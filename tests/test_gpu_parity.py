@@ -321,3 +321,52 @@ def test_codec_without_levels_many_tiles(tx, q, r, frames):
         got = np.stack([rec[i][(b // nbx) * 16:(b // nbx) * 16 + 16, (b % nbx) * 16:(b % nbx) * 16 + 16] for b in pick])
         ref = oracle_blocks(X.astype(np.int64), q, r, 8)
         assert np.array_equal(got, ref["recon"]), i
+
+
+# --------------------------------------------------------------------------
+# 9..12-bit planes through the fused path (one block per thread, 16-bit
+# samples; a quantiser of q >= 2^(bits-8)/256, up to 8 kept columns, no
+# levels) and the general kernel beside it
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("bits,q,r", [(10, 16.0, 16), (10, 4.0, 8), (10, 64.0, 32), (12, 64.0, 16),
+                                      (12, 16.0, 4), (9, 8.0, 16), (10, 2.0 ** -5, 16)])
+def test_codec_16bit_without_levels(tx, bits, q, r):
+    import torch
+
+    shapes = [(80, 272), (16, 16), (64, 528), (48, 48)]
+    imgs = [synth.ar1_image(900 + i + bits + r, h, w, 0.93, bits) for i, (h, w) in enumerate(shapes)]
+    keep = [to_dev(im) for im in imgs]
+    outs = [empty_like_img(h, w, bits, pad=8) for h, w in shapes]
+    sse = torch.full((len(imgs),), -1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_batch([tx.image(d, bits) for d in keep], [tx.image(o, bits) for o in outs],
+                        [(q, r)] * len(imgs), sse=sse)
+    torch.cuda.synchronize()
+    for i, im in enumerate(imgs):
+        ref = oracle_blocks(O.image_to_blocks(im.astype(np.int64)), q, r, bits)
+        rec = from_dev(outs[i], bits)
+        assert np.array_equal(O.image_to_blocks(rec.astype(np.int64)), ref["recon"]), i
+        assert int(sse[i].item()) == O.sse(im, rec), i
+
+
+def test_codec_16bit_2160p_frame(tx):
+    """One 3840 x 2160 10-bit frame (the serving mix's large request) through
+    the fused 16-bit path: sampled blocks against the oracle, SSE against the
+    GPU's own reconstruction."""
+    import torch
+
+    H, W, bits = 2160, 3840, 10
+    img = synth.ar1_image(2160, H, W, 0.95, bits)
+    d = to_dev(img)
+    out = empty_like_img(H, W, bits)
+    sse = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_batch([tx.image(d, bits)], [tx.image(out, bits)], [(16.0, 16)], sse=sse)
+    torch.cuda.synchronize()
+    rec = from_dev(out, bits)
+    assert int(sse.item()) == O.sse(img, rec)
+    nbx, nb = W // 16, (H // 16) * (W // 16)
+    rng = np.random.default_rng(10)
+    pick = np.unique(np.concatenate([rng.integers(0, nb, 600), np.arange(0, nb, 32), [nb - 1]]))
+    X = np.stack([img[(b // nbx) * 16:(b // nbx) * 16 + 16, (b % nbx) * 16:(b % nbx) * 16 + 16] for b in pick])
+    got = np.stack([rec[(b // nbx) * 16:(b // nbx) * 16 + 16, (b % nbx) * 16:(b % nbx) * 16 + 16] for b in pick])
+    ref = oracle_blocks(X.astype(np.int64), 16.0, 16, bits)
+    assert np.array_equal(got, ref["recon"])
