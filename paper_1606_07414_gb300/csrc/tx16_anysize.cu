@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -172,7 +173,7 @@ tx16_status launch_any(const AnyParam* imgs, int n, unsigned long long* sse, cud
     tiles += (imgs[i].p.nblk + kTileBlocks - 1) / kTileBlocks;
   }
   P.ntiles = tiles;
-  static int occ = 0;
+  static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, any_size_kernel<Smp, kAnyMaxImg>, kThreads, 0) !=

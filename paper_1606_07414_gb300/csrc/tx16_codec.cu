@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "tx16_block.cuh"
@@ -217,7 +218,7 @@ static tx16_status launch_one(const ImgParam* imgs, int n, unsigned long long* s
     tiles += (imgs[i].nblk + kTileBlocks - 1) / kTileBlocks;
   }
   P.ntiles = tiles;
-  static int occ = 0;  // resident CTAs per SM for this instance (same on every GB300)
+  static std::atomic<int> occ{0};  // resident CTAs per SM for this instance (same on every GB300)
   if (occ == 0) {
     int o = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, block_kernel<Smp, MAXI, OP>, kThreads, 0) !=

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "tx16_internal.h"
 #include "tx16_net.cuh"
@@ -388,7 +389,7 @@ tx16_status launch_fused(const ImgParam* imgs, int n, unsigned long long* sse, i
     tiles += (imgs[i].nblk + kTileBlocks - 1) / kTileBlocks;
   }
   P.ntiles = tiles;
-  static int occ = 0;
+  static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     // prefer shared memory over L1 so the register limit, not the carveout,
@@ -432,7 +433,7 @@ tx16_status launch_fused_modes(int zone, const ImgParam* imgs, int n, unsigned l
 
 template <class Z, bool LEV, bool DST>
 int list_max_ctas() {
-  static int occ = 0;
+  static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     cudaFuncSetAttribute(fused_u8_list_kernel<Z, LEV, DST>, cudaFuncAttributePreferredSharedMemoryCarveout,

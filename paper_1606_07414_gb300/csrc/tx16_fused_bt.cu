@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "tx16_fused_common.cuh"
 #include "tx16_internal.h"
@@ -161,8 +162,17 @@ constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16 * SB; }
 // samples (two stages of 32-byte rows would leave one CTA per SM)
 template <class Z, int SB = 1>
 constexpr int stages() { return SB == 1 ? BtLimits<Z>::kStages : 1; }
-template <class Z>
-constexpr int cz_bytes() { return BtLimits<Z>::kCzSmem * 16 * 32 * BtLimits<Z>::kWarps * 8; }
+// column pairs parked in shared memory: the class's setting for 8-bit
+// samples; TX16_BT16_CZ (at most the class's setting) for 16-bit samples
+#ifndef TX16_BT16_CZ
+#define TX16_BT16_CZ 1
+#endif
+template <class Z, int SB = 1>
+constexpr int cz_pairs() {
+  return SB == 1 ? BtLimits<Z>::kCzSmem : (BtLimits<Z>::kCzSmem < TX16_BT16_CZ ? BtLimits<Z>::kCzSmem : TX16_BT16_CZ);
+}
+template <class Z, int SB = 1>
+constexpr int cz_bytes() { return cz_pairs<Z, SB>() * 16 * 32 * BtLimits<Z>::kWarps * 8; }
 
 // The 4 * SB words of staged row `row` of this thread (slots row * SB + h).
 template <int SB>
@@ -232,7 +242,7 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
   constexpr int kBtThreads = 32 * kBtWarps;
   constexpr int kStageBytes = stage_bytes<Z, SB>();
   constexpr int kSlot = kBtThreads * 16;  // bytes of one staged slot
-  constexpr int kCzSmem = BtLimits<Z>::kCzSmem;  // parked column pairs
+  constexpr int kCzSmem = cz_pairs<Z, SB>();  // parked column pairs
   static_assert(kCzSmem < Z::V / 2, "at least one column pair stays in registers");
   constexpr int V = Z::V;
   constexpr int NP = V / 2;
@@ -497,8 +507,14 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
 // resident CTAs per SM the registers are budgeted for: the class's setting
 // for 8-bit samples, at most 2 for 16-bit samples (wider staging, more live
 // values in the rounding)
+#ifndef TX16_BT16_MINCTAS
+#define TX16_BT16_MINCTAS 2
+#endif
 template <class Z, int SB>
-constexpr int min_ctas() { return SB == 1 ? BtLimits<Z>::kMinCtas : (BtLimits<Z>::kMinCtas < 2 ? BtLimits<Z>::kMinCtas : 2); }
+constexpr int min_ctas() {
+  return SB == 1 ? BtLimits<Z>::kMinCtas
+                 : (BtLimits<Z>::kMinCtas < TX16_BT16_MINCTAS ? BtLimits<Z>::kMinCtas : TX16_BT16_MINCTAS);
+}
 
 template <int MAXI, class Z, bool DST, int SB>
 __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, min_ctas<Z, SB>())
@@ -533,8 +549,8 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
   constexpr int kBtWarps = BtLimits<Z>::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
   constexpr size_t smem =
-      size_t(stages<Z, SB>()) * size_t(stage_bytes<Z, SB>()) + size_t(cz_bytes<Z>());
-  static int occ = 0;
+      size_t(stages<Z, SB>()) * size_t(stage_bytes<Z, SB>()) + size_t(cz_bytes<Z, SB>());
+  static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     if (cudaFuncSetAttribute(fused_bt_kernel<MAXI, Z, DST, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -571,7 +587,7 @@ tx16_status launch_bt_list(const ImgParam* d_imgs, int nimg, int ntiles, unsigne
                            int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
   constexpr int kThreadsZ = 32 * BtLimits<Z>::kWarps;
   constexpr size_t smem = size_t(stages<Z>()) * size_t(stage_bytes<Z>()) + size_t(cz_bytes<Z>());
-  static int occ = 0;
+  static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     if (cudaFuncSetAttribute(fused_bt_list_kernel<Z, DST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -582,7 +598,7 @@ tx16_status launch_bt_list(const ImgParam* d_imgs, int nimg, int ntiles, unsigne
       o = 1;
     occ = o;
   }
-  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ.load()) : occ.load();
   const int grid = std::max(1, std::min((ntiles + BtLimits<Z>::kWarps - 1) / BtLimits<Z>::kWarps,
                                         per_sm * device_sm_count()));
   fused_bt_list_kernel<Z, DST><<<grid, kThreadsZ, smem, stream>>>(d_imgs, nimg, ntiles, counter, chunk, sse);

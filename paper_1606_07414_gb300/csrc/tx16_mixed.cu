@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -266,7 +267,7 @@ tx16_status launch_mixed(const MixedParam* imgs, int n, unsigned long long* sse,
     tiles += (imgs[i].p.nblk + kTileBlocks - 1) / kTileBlocks;
   }
   P.ntiles = tiles;
-  static int occ = 0;
+  static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, mixed_kernel<Smp, kMixMaxImg>, kThreads, 0) !=

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -298,7 +299,7 @@ tx16_status launch_ssim(const SsimImg* imgs, int n, const float* g, double* mssi
     units += imgs[i].nstrips * ((imgs[i].mh + kSegRows - 1) / kSegRows);
   }
   P.nunits = units;
-  static bool attr = false;
+  static std::atomic<bool> attr{false};
   if (!attr) {
     if (cudaFuncSetAttribute(ssim_kernel<Smp, MAP, kSsimMaxImg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(kSsimSmem)) != cudaSuccess)

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "tx16_internal.h"
@@ -180,7 +181,7 @@ tx16_status launch_sweep(const SweepImg* imgs, int n, const uint8_t (*colh)[16],
     tiles += (imgs[i].nblk + 15) / 16;
   }
   P.ntiles = tiles;
-  static int occ = 0;
+  static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, sweep_kernel<Smp, MAXI>, 256, 0) != cudaSuccess || o < 1)
