@@ -591,6 +591,22 @@ def _serving(tx16, torch, np, args):
         pools.append((H, W, bits, ins, outs))
     srv = tx16.Server({"device_pool_mb": 16384, "streams": 3, "max_batch": 256})
     rates = [int(x) for x in args.serve_rates.split(",")]
+    # untimed warm-up: every request kind, q and r through both forms once
+    # (first launches of each kernel variant load their modules)
+    dev_in = {k: torch.empty((H, W), dtype=torch.uint8 if b == 8 else torch.int16, device="cuda")
+              for k, (H, W, b) in enumerate(kinds)}
+    dev_out = {k: torch.empty_like(v) for k, v in dev_in.items()}
+    sse = torch.zeros(1, dtype=torch.int64, device="cuda")
+    warm = []
+    for k, (H, W, bits, ins, outs) in enumerate(pools):
+        for q in (8.0, 16.0, 32.0):
+            for r in (4, 16, 64, 256):
+                warm.append(srv.submit_ptr(ins[0].data_ptr(), W, H, bits, q, r, outs[0].data_ptr()))
+                tx16.tx16_codec_batch([tx16.image(dev_in[k], bits)], [tx16.image(dev_out[k], bits)], [(q, r)],
+                                      sse=sse)
+    for t in warm:
+        srv.wait(t)
+    torch.cuda.synchronize()
     out = {"workload": "Poisson arrivals; 60% 256x256 u8, 30% 1920x1088 u8, 10% 3840x2160 10-bit; "
                        "q in {8,16,32}, r in {4,16,64,256}; pinned host buffers", "rates": []}
     for rate in rates:
@@ -626,10 +642,6 @@ def _serving(tx16, torch, np, args):
                             "req_per_s": round(achieved, 1)}}
         # the plain form: each request coded alone (copy in, one launch, copy out) as it arrives
         m = min(n, max(200, int(rate * 0.5)))
-        dev_in = {k: torch.empty((H, W), dtype=torch.uint8 if b == 8 else torch.int16, device="cuda")
-                  for k, (H, W, b) in enumerate(kinds)}
-        dev_out = {k: torch.empty_like(v) for k, v in dev_in.items()}
-        sse = torch.zeros(1, dtype=torch.int64, device="cuda")
         lat = []
         t0 = time.perf_counter()
         due = t0

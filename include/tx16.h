@@ -317,6 +317,11 @@ typedef struct tx16_server tx16_server;
  *   "streams"         groups in flight (default 3, 1..16)
  *   "max_batch"       requests per group (default 256)
  *   "max_queue"       queued requests before submit returns TX16_EBUSY
+ *   "spin_us"         polling window, 0..1e6 (default 300): after its last
+ *                     progress the worker polls for submissions and finished
+ *                     groups this long before it blocks, and tx16_serve_wait
+ *                     polls this long before it blocks; 0 blocks at once
+ *                     (no host core kept busy, longer hand-offs at low load)
  * The server uses the device current at creation. */
 tx16_status tx16_serve_create(const char* json_cfg, tx16_server** server);
 

@@ -12,10 +12,15 @@
 //               then an event;
 //             - retires slots whose event has fired: PSNR, latency, frees the
 //               requests' arena space, wakes their waiters.
+//           With nothing to do it polls (submissions, slot events) for up to
+//           spin_us after its last progress, then blocks until a submit or a
+//           slot's host callback wakes it: at low load the hand-offs between
+//           threads, not the GPU, set the latency.
 //           Groups on different slots overlap on the GPU (copies of one with
 //           the kernel of another), and requests that arrive while others are
 //           in flight join the next group: the batch is never closed.
-//  wait     blocks (bounded) until a request is done.
+//  wait     polls for up to spin_us, then blocks (bounded) until the request
+//           is done.
 //
 // All device memory (the arena, per-slot SSE arrays) is allocated once at
 // creation; requests never allocate.  Host buffers are the caller's: the input
@@ -109,7 +114,7 @@ struct Request {
   Clock::time_point t_submit;
   char* d_in = nullptr;
   char* d_out = nullptr;
-  bool done = false;
+  std::atomic<bool> done{false};
   tx16_status status = TX16_OK;
   double psnr = 0.0;
   double latency_us = 0.0;
@@ -121,9 +126,7 @@ struct Slot {
   uint64_t* d_sse = nullptr;
   uint64_t* h_sse = nullptr;  // pinned
   std::vector<Request*> reqs;
-  bool busy = false;
-  bool finished = false;  // set by the stream's host callback
-  Clock::time_point t_finished;
+  bool busy = false;  // written by the worker thread only
   struct tx16_server* server = nullptr;
 };
 
@@ -143,6 +146,8 @@ struct tx16_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   bool paused = false;  // admission held (tx16_serve_pause)
+  std::atomic<uint64_t> pokes{0};  // bumped by submit, pause, stop and slot callbacks
+  double spin_us = 300;            // polling window of the worker and of waiters
   std::thread worker;
   // statistics
   std::vector<double> lat;  // reservoir of latencies (us)
@@ -213,15 +218,17 @@ void record_latency(tx16_server* s, double us) {
 }
 
 // Runs on the CUDA runtime's callback thread when a slot's stream has passed
-// its last copy: stamps the completion time and wakes the worker (no CUDA
-// calls are allowed here).
+// its last copy: wakes the worker (no CUDA calls are allowed here).  The
+// worker learns that a group is done from the slot's event, so a callback of
+// a group that the worker already retired is only a spurious wake-up.  Taking
+// the lock orders the wake-up after any event query the worker made before it
+// blocked.
 void CUDART_CB slot_done(void* arg) {
   Slot* slot = static_cast<Slot*>(arg);
   tx16_server* s = slot->server;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    slot->finished = true;
-    slot->t_finished = Clock::now();
+    s->pokes.fetch_add(1, std::memory_order_release);
   }
   s->cv_work.notify_one();
 }
@@ -257,7 +264,7 @@ tx16_status launch_group(tx16_server* s, Slot& slot) {
 }
 
 void retire(tx16_server* s, Slot& slot, tx16_status st) {
-  const Clock::time_point t = slot.finished ? slot.t_finished : Clock::now();
+  const Clock::time_point t = Clock::now();
   for (size_t i = 0; i < slot.reqs.size(); ++i) {
     Request* r = slot.reqs[i];
     r->status = st;
@@ -271,24 +278,38 @@ void retire(tx16_server* s, Slot& slot, tx16_status st) {
     s->arena.free(r->d_in);
     s->arena.free(r->d_out);
     r->d_in = r->d_out = nullptr;
-    r->done = true;
+    r->done.store(true, std::memory_order_release);
   }
   s->t_last = t;
   slot.reqs.clear();
   slot.busy = false;
-  slot.finished = false;
+}
+
+// Poll, without the lock, until a submission or callback arrives, a slot in
+// flight finishes, or the window ends.  Returns at once when the window is 0.
+void poll_for_work(tx16_server* s, uint64_t seen, Clock::time_point until) {
+  while (Clock::now() < until) {
+    if (s->pokes.load(std::memory_order_acquire) != seen) return;
+    for (Slot& slot : s->slots)
+      if (slot.busy && cudaEventQuery(slot.event) != cudaErrorNotReady) return;
+  }
 }
 
 void worker_main(tx16_server* s) {
   cudaSetDevice(s->device);
+  const auto spin = std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double, std::micro>(s->spin_us));
+  Clock::time_point last_progress = Clock::now();
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    // retire groups whose host callback has fired
+    const uint64_t seen = s->pokes.load(std::memory_order_acquire);
+    // retire groups whose event has completed (an error of the group's work
+    // is reported by the query)
     bool progressed = false;
     for (Slot& slot : s->slots) {
-      if (!slot.busy || !slot.finished) continue;
-      const cudaError_t q = cudaEventQuery(slot.event);  // reports an error of the group's work
-      retire(s, slot, (q == cudaSuccess || q == cudaErrorNotReady) ? TX16_OK : TX16_ECUDA);
+      if (!slot.busy) continue;
+      const cudaError_t q = cudaEventQuery(slot.event);
+      if (q == cudaErrorNotReady) continue;
+      retire(s, slot, q == cudaSuccess ? TX16_OK : TX16_ECUDA);
       progressed = true;
     }
     if (progressed) s->cv_done.notify_all();
@@ -309,7 +330,6 @@ void worker_main(tx16_server* s) {
       }
       if (slot.reqs.empty()) break;
       slot.busy = true;
-      slot.finished = false;
       // issue copies and the launch without holding the lock (submit stays cheap)
       lk.unlock();
       const tx16_status st = launch_group(s, slot);
@@ -323,7 +343,14 @@ void worker_main(tx16_server* s) {
     }
     const bool inflight = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot& x) { return x.busy; });
     if (s->stop && s->queue.empty() && !inflight) break;
-    if (!progressed) {
+    const Clock::time_point now = Clock::now();
+    if (progressed) {
+      last_progress = now;
+    } else if (now < last_progress + spin) {
+      lk.unlock();
+      poll_for_work(s, seen, last_progress + spin);
+      lk.lock();
+    } else if (s->pokes.load(std::memory_order_acquire) == seen) {
       // sleep until a callback, a submit, a resume or stop (bounded: re-check)
       s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
     }
@@ -351,8 +378,10 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
   const int nslots = cfg.count("streams") ? int(cfg["streams"]) : 3;
   s->max_batch = cfg.count("max_batch") ? int(cfg["max_batch"]) : 256;
   s->max_queue = cfg.count("max_queue") ? size_t(cfg["max_queue"]) : size_t(1) << 20;
+  s->spin_us = cfg.count("spin_us") ? cfg["spin_us"] : 300.0;
   const size_t pool = size_t(pool_mb * (1 << 20));
-  if (pool < 4096 || nslots < 1 || nslots > 16 || s->max_batch < 1 || s->max_batch > 4096 || s->max_queue < 1) {
+  if (pool < 4096 || nslots < 1 || nslots > 16 || s->max_batch < 1 || s->max_batch > 4096 || s->max_queue < 1 ||
+      !(s->spin_us >= 0 && s->spin_us <= 1e6)) {
     delete s;
     return TX16_EINVAL;
   }
@@ -412,6 +441,7 @@ tx16_status tx16_serve_submit(tx16_server* s, const void* host_pixels, int32_t w
     s->queue.push_back(r);
     s->live[r->ticket] = r;
     *ticket = r->ticket;
+    s->pokes.fetch_add(1, std::memory_order_release);
   }
   s->cv_work.notify_one();
   return TX16_OK;
@@ -422,10 +452,20 @@ tx16_status tx16_serve_wait(tx16_server* s, uint64_t ticket, int32_t timeout_ms,
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->live.find(ticket);
   if (it == s->live.end()) return TX16_EINVAL;
-  Request* r = it->second;
-  const auto deadline = Clock::now() + std::chrono::milliseconds(std::max(0, timeout_ms));
-  while (!r->done) {
-    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !r->done) return TX16_ETIMEOUT;
+  Request* r = it->second;  // only its waiter frees it, so it outlives the unlocked poll
+  const Clock::time_point t0 = Clock::now();
+  const auto deadline = t0 + std::chrono::milliseconds(std::max(0, timeout_ms));
+  if (!r->done.load(std::memory_order_acquire) && s->spin_us > 0) {
+    const auto until = std::min(deadline, t0 + std::chrono::duration_cast<Clock::duration>(
+                                                   std::chrono::duration<double, std::micro>(s->spin_us)));
+    lk.unlock();
+    while (!r->done.load(std::memory_order_acquire) && Clock::now() < until) {
+    }
+    lk.lock();
+  }
+  while (!r->done.load(std::memory_order_acquire)) {
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !r->done.load(std::memory_order_acquire))
+      return TX16_ETIMEOUT;
   }
   if (psnr) *psnr = r->psnr;
   if (latency_us) *latency_us = r->latency_us;
@@ -464,6 +504,7 @@ tx16_status tx16_serve_pause(tx16_server* s, int32_t paused) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->paused = paused != 0;
+    s->pokes.fetch_add(1, std::memory_order_release);
   }
   s->cv_work.notify_all();
   return TX16_OK;
@@ -484,12 +525,10 @@ void tx16_serve_destroy(tx16_server* s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
+    s->paused = false;  // let queued work drain
+    s->pokes.fetch_add(1, std::memory_order_release);
   }
   s->cv_work.notify_all();
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->paused = false;  // let queued work drain
-  }
   if (s->worker.joinable()) s->worker.join();
   for (Slot& slot : s->slots) {
     if (slot.stream) cudaStreamSynchronize(slot.stream);

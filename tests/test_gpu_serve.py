@@ -114,3 +114,28 @@ def test_admission_and_errors_made_on_the_host(tx):
     srv.pause(True)
     srv.submit(small, 16.0, 16)
     srv.close()
+
+
+@pytest.mark.parametrize("spin_us", [0, 20000])
+def test_polling_window_does_not_change_results(tx, spin_us):
+    """spin_us = 0 blocks at once (completion learnt from the slot callbacks);
+    a long window keeps the worker polling slot events throughout."""
+    srv = tx.Server({"device_pool_mb": 64, "streams": 2, "max_batch": 8, "spin_us": spin_us})
+    reqs = _mix(23, 40)
+    outs, tickets = [], []
+    for img, bits, q, r in reqs:
+        o = np.zeros_like(img)
+        outs.append(o)
+        tickets.append(srv.submit(img, q, r, out=o, bits=bits))
+    for (img, bits, q, r), o, t in zip(reqs, outs, tickets):
+        p, lat = srv.wait(t)
+        ref = O.codec_image(img, q, r, bits, "fp32" if q else "fp64")
+        assert np.array_equal(o, ref["recon"]) and lat > 0
+    srv.close()
+
+
+def test_bad_polling_window_is_rejected(tx):
+    for bad in (-1, 2e6, float("nan")):
+        with pytest.raises(tx.Tx16Error) as e:
+            tx.Server({"spin_us": bad})
+        assert e.value.status == tx.TX16_EINVAL
