@@ -815,6 +815,40 @@ def run_ssim_only(args):
                       "mean_ssim": round(float(ms_t.mean().item()), 6)}), flush=True)
 
 
+def run_frames10_only(args):
+    """The fused 16-bit codec on --frames 3840 x 2160 10-bit frames, --steps
+    timed launches after --warmup; prints one short JSON line (not the bench
+    line)."""
+    import numpy as np
+    import torch
+
+    from paper_1606_07414_gb300 import tx16
+
+    lib = tx16.load()
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    n, H10, W10 = FRAMES, 2160, 3840
+    f10 = torch.from_numpy(synth_frames_10bit(n, H10, W10).view(np.int16)).cuda()
+    o10 = torch.empty_like(f10)
+    ins = (tx16.tx16_image * n)(*[tx16.image(f10[i], 10) for i in range(n)])
+    outs = (tx16.tx16_image * n)(*[tx16.image(o10[i], 10) for i in range(n)])
+    qp = (tx16.tx16_qparams * n)(*[tx16.tx16_qparams(64.0, args.r)] * n)
+    sse = torch.zeros(n, dtype=torch.int64, device="cuda")
+
+    def c10():
+        st = lib.tx16_codec_batch(ins, outs, n, qp, ctypes.c_void_p(sse.data_ptr()), None, sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_codec_batch")
+    for _ in range(args.warmup):
+        c10()
+    ms = _events_time(c10, args.steps, stream)
+    blocks = n * (H10 // 16) * (W10 // 16)
+    gbs = blocks * 1024 / (ms * 1e-3) / 1e9
+    print(json.dumps({"frames10_ms": round(ms, 4), "frames": n, "r": args.r,
+                      "Mblocks_s": round(blocks / (ms * 1e-3) / 1e6, 1), "GB_s": round(gbs, 1),
+                      "frac": round(gbs / _measured_peak()["value"], 4)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -833,6 +867,8 @@ def main():
     ap.add_argument("--frames", type=int, default=FRAMES, help="smaller cases for profiling")
     ap.add_argument("--ssim-only", action="store_true",
                     help="time tx16_ssim alone on --frames frames and their reconstruction (profiling)")
+    ap.add_argument("--frames10-only", action="store_true",
+                    help="time the fused 16-bit codec alone on --frames 10-bit 3840x2160 frames (profiling)")
     args = ap.parse_args()
     globals()["FRAMES"] = args.frames
     if args.warmup < 3 and args.impl == "tx16":
@@ -841,6 +877,8 @@ def main():
         run_reference(args)
     elif args.ssim_only:
         run_ssim_only(args)
+    elif args.frames10_only:
+        run_frames10_only(args)
     else:
         run_gpu(args)
 

@@ -138,6 +138,19 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// wait_group with a count known after unrolling (0..7)
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+  switch (n) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    default: cp_async_wait<7>(); break;
+  }
+}
 
 // Shared-memory float2 through volatile accesses, so that a value parked in
 // shared memory is not forwarded back into registers by the compiler.
@@ -162,6 +175,14 @@ constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16 * SB; }
 // samples (two stages of 32-byte rows would leave one CTA per SM)
 template <class Z, int SB = 1>
 constexpr int stages() { return SB == 1 ? BtLimits<Z>::kStages : 1; }
+// Single-stage refill: bit 0 for 8-bit samples, bit 1 for 16-bit samples.
+// Set: the next tile's rows are fetched pair by pair during the inverse pass
+// ("rolling"); clear: all 16 after the tile.
+#ifndef TX16_BT_ROLLING
+#define TX16_BT_ROLLING 2
+#endif
+template <class Z, int SB = 1>
+constexpr bool rolling_refill() { return stages<Z, SB>() == 1 && ((TX16_BT_ROLLING >> (SB - 1)) & 1) != 0; }
 // column pairs parked in shared memory: the class's setting for 8-bit
 // samples; TX16_BT16_CZ (at most the class's setting) for 16-bit samples
 #ifndef TX16_BT16_CZ
@@ -256,25 +277,36 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
   if (t < 0) return;
   constexpr int kStages = stages<Z, SB>();  // 2: the next tile is fetched during this one
   static_assert(kStages == 1 || kStages == 2, "one or two input stages");
+  constexpr bool kRolling = rolling_refill<Z, SB>();
   uint8_t* const cz_park = rows_smem + kStages * kStageBytes + threadIdx.x * 8;
 
-  // prefetch the 16 rows of this thread's block of tile tt (image kk) into
-  // stage st; image fields are read from the parameter bank where used
-  auto prefetch = [&](int kk, int tt, int st) {
+  // Where this thread's block of tile tt (image kk) is read from: its first
+  // row and the row pitch, or, past the image's end, the image base with
+  // pitch 0 and no bytes (the copies then fill zeros).
+  struct RowSrc {
+    const uint8_t* g;
+    int64_t pitch;
+    int bytes;
+  };
+  auto row_src = [&](int kk, int tt) {
     const ImgParam& I = imgs[kk];
     const int blk = (tt - I.tile0) * kWarpTile + lane;
-    const bool ok = blk < I.nblk;
-    const int2 c = ok ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
     const uint8_t* src = static_cast<const uint8_t*>(I.src);
-    const uint8_t* g = src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16 * SB;
+    if (blk >= I.nblk) return RowSrc{src, 0, 0};
+    const int2 c = block_coords(I.div_magic, I.nbx, blk);
+    return RowSrc{src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16 * SB, I.src_pitch, 16};
+  };
+  // rows [i0, i1) of a block into stage st, as one commit group
+  auto fetch_rows = [&](const RowSrc& r, int st, int i0, int i1) {
     uint8_t* s = rows_smem + st * kStageBytes + threadIdx.x * 16;
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
+    for (int i = i0; i < i1; ++i)
 #pragma unroll
-      for (int h = 0; h < SB; ++h)
-        cp_async16(s + (i * SB + h) * kSlot, ok ? g + int64_t(i) * I.src_pitch + 16 * h : src, ok ? 16 : 0);
+      for (int h = 0; h < SB; ++h) cp_async16(s + (i * SB + h) * kSlot, r.g + int64_t(i) * r.pitch + 16 * h, r.bytes);
     cp_async_commit();
   };
+  // the 16 rows of this thread's block of tile tt (image kk) into stage st
+  auto prefetch = [&](int kk, int tt, int st) { fetch_rows(row_src(kk, tt), st, 0, 16); };
   auto tile_end_of = [&](int kk) { return kk + 1 < nimg ? imgs[kk + 1].tile0 : ntiles; };
   // column heights of image kk, 5 bits each (V <= 8: 40 bits)
   auto heights = [&](int kk) {
@@ -293,20 +325,28 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
   fill_consts<NP>(imgs[k], Q, lane);
   unsigned long long acc = 0;
   int stage = 0;
+  // One stage, rolling refill: the rows of the next tile are fetched row pair
+  // by row pair as the inverse pass of this tile finishes with them (one
+  // commit group per pair, in order), and the forward pass of the next tile
+  // waits for each pair only when it needs it.  "rolling" says that the
+  // current tile's rows arrived that way.  Otherwise one stage is refilled
+  // with all 16 rows after the tile.
+  bool rolling = false;
 
   while (t >= 0) {
     const int tn = sched.next(t);
+    if (tn >= 0 && tn >= end_kn) {
+      kn = image_of_tile(imgs, nimg, tn);
+      end_kn = tile_end_of(kn);
+    }
     if (kStages == 2 && tn >= 0) {
       // fetch the next tile of this warp while this one is coded
-      if (tn >= end_kn) {
-        kn = image_of_tile(imgs, nimg, tn);
-        end_kn = tile_end_of(kn);
-      }
       prefetch(kn, tn, stage ^ 1);
       cp_async_wait<1>();
-    } else {
+    } else if (kStages == 2 || !rolling) {
       cp_async_wait<0>();
     }
+    const RowSrc next = (kRolling && tn >= 0) ? row_src(kn, tn) : RowSrc{nullptr, 0, 0};
     if (t >= end_k) {  // warp-uniform: a later image
       if (sse) flush_sse(sse, imgs[k].out_index, acc);
       acc = 0;
@@ -327,6 +367,7 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
     float2 R[8][V];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
+      if (kRolling && rolling) cp_async_wait_n(7 - p);  // row pair p of this tile has arrived
       unsigned wa[4 * SB], wb[4 * SB];
       load_row_words<SB>(rows, 2 * p, kSlot, wa);
       load_row_words<SB>(rows, 2 * p + 1, kSlot, wb);
@@ -488,16 +529,12 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
           s1 += unsigned(d0 * d0) + unsigned(d1 * d1) + unsigned(d2 * d2) + unsigned(d3 * d3);
         }
       }
+      // rows 2p and 2p + 1 of the stage are used: refill them for the next tile
+      if (kRolling && tn >= 0) fetch_rows(next, 0, 2 * p, 2 * p + 2);
     }
     acc += SB == 1 ? (unsigned long long)(s1 - 2u * s2) : (unsigned long long)s1;
-    if (kStages == 1 && tn >= 0) {
-      // one stage: the next tile's rows replace this one's once they are used
-      if (tn >= end_kn) {
-        kn = image_of_tile(imgs, nimg, tn);
-        end_kn = tile_end_of(kn);
-      }
-      prefetch(kn, tn, 0);
-    }
+    if (kStages == 1 && !kRolling && tn >= 0) prefetch(kn, tn, 0);  // the used rows replaced at once
+    rolling = kRolling && tn >= 0;
     t = tn;
     stage ^= (kStages - 1);
   }
