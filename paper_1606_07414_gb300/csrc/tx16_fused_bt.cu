@@ -165,11 +165,18 @@ __device__ __forceinline__ float2 ld_shared_f2(const void* p) {
   return v;
 }
 
+// Warps per CTA: the class's setting for 8-bit samples, TX16_BT16_WARPS for
+// 16-bit samples (smaller CTAs fit more warps beside the wider staging).
+#ifndef TX16_BT16_WARPS
+#define TX16_BT16_WARPS 4
+#endif
+template <class Z, int SB = 1>
+constexpr int bt_warps() { return SB == 1 ? BtLimits<Z>::kWarps : TX16_BT16_WARPS; }
 // Input rows: per thread 16 rows of 16 bytes per stage, laid out
 // [stage][row][thread] so that a warp's 16-byte accesses to one row are
 // contiguous.
 template <class Z, int SB = 1>
-constexpr int stage_bytes() { return 16 * 32 * BtLimits<Z>::kWarps * 16 * SB; }
+constexpr int stage_bytes() { return 16 * 32 * bt_warps<Z, SB>() * 16 * SB; }
 // bytes of the parked column results: 16 float2 per thread, [row][thread]
 // input stages: the class's setting for 8-bit samples; one stage for 16-bit
 // samples (two stages of 32-byte rows would leave one CTA per SM)
@@ -193,7 +200,7 @@ constexpr int cz_pairs() {
   return SB == 1 ? BtLimits<Z>::kCzSmem : (BtLimits<Z>::kCzSmem < TX16_BT16_CZ ? BtLimits<Z>::kCzSmem : TX16_BT16_CZ);
 }
 template <class Z, int SB = 1>
-constexpr int cz_bytes() { return cz_pairs<Z, SB>() * 16 * 32 * BtLimits<Z>::kWarps * 8; }
+constexpr int cz_bytes() { return cz_pairs<Z, SB>() * 16 * 32 * bt_warps<Z, SB>() * 8; }
 
 // The 4 * SB words of staged row `row` of this thread (slots row * SB + h).
 template <int SB>
@@ -259,7 +266,7 @@ template <class Z, bool DST, int SB, class Sched>
 __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int nimg, int ntiles,
                                          unsigned long long* sse, Sched& sched) {
   static_assert(SB == 1 || SB == 2, "8- or 16-bit samples");
-  constexpr int kBtWarps = BtLimits<Z>::kWarps;
+  constexpr int kBtWarps = bt_warps<Z, SB>();
   constexpr int kBtThreads = 32 * kBtWarps;
   constexpr int kStageBytes = stage_bytes<Z, SB>();
   constexpr int kSlot = kBtThreads * 16;  // bytes of one staged slot
@@ -490,11 +497,13 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
         }
       } else {
         // sample = clip(floor(X + 1/2), 0, peak): R = RD(X + 1024.5), then
-        // RD(R + 2^23) = 2^23 + floor(R) exactly (floor(RD(v)) = floor(v));
-        // its bits, clamped as integers to [2^23 + 1024, 2^23 + 1024 + peak]
-        // (bits of positive floats are ordered), less 2^23 + 1024
+        // RD(R + 2^23 + 64512) = 2^23 + 65536 + floor(R) - 1024 exactly
+        // (floor(RD(v)) = floor(v); the sum lies in [2^23, 2^24) where the
+        // spacing is 1); its bits, clamped as integers to
+        // [2^23 + 65536, 2^23 + 65536 + peak] (bits of floats are ordered),
+        // hold the sample in their low 16 bits
         const int peak = (1 << (imgs[k].flags & 0xff)) - 1;
-        const int bmin = 0x4B000400, bmax = 0x4B000400 + peak;
+        const int bmin = 0x4B010000, bmax = 0x4B010000 + peak;
         unsigned ya[8], yb[8];  // reconstructed rows 2p and 2p + 1, two samples per word
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
@@ -503,12 +512,12 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
           for (int e = 0; e < 2; ++e) {
             const float2 r = Z::InvRow::sign(j + e) >= 0 ? __fadd2_rd(z[j + e], f2(1024.5f))
                                                          : sub2_rd(f2(1024.5f), z[j + e]);
-            const float2 m = __fadd2_rd(r, f2(8388608.f));
-            va[e] = min(max(__float_as_int(m.x), bmin), bmax) - bmin;
-            vb[e] = min(max(__float_as_int(m.y), bmin), bmax) - bmin;
+            const float2 m = __fadd2_rd(r, f2(8388608.f + 64512.f));
+            va[e] = min(max(__float_as_int(m.x), bmin), bmax);
+            vb[e] = min(max(__float_as_int(m.y), bmin), bmax);
           }
-          ya[j >> 1] = unsigned(va[0]) | (unsigned(va[1]) << 16);
-          yb[j >> 1] = unsigned(vb[0]) | (unsigned(vb[1]) << 16);
+          ya[j >> 1] = __byte_perm(unsigned(va[0]), unsigned(va[1]), 0x5410u);
+          yb[j >> 1] = __byte_perm(unsigned(vb[0]), unsigned(vb[1]), 0x5410u);
         }
         if (DST && valid) {
           const int64_t dp = imgs[k].dst_pitch;
@@ -542,22 +551,19 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
 }
 
 // resident CTAs per SM the registers are budgeted for: the class's setting
-// for 8-bit samples, at most 2 for 16-bit samples (wider staging, more live
-// values in the rounding)
+// for 8-bit samples, TX16_BT16_MINCTAS for 16-bit samples (wider staging,
+// more live values in the rounding)
 #ifndef TX16_BT16_MINCTAS
 #define TX16_BT16_MINCTAS 2
 #endif
 template <class Z, int SB>
-constexpr int min_ctas() {
-  return SB == 1 ? BtLimits<Z>::kMinCtas
-                 : (BtLimits<Z>::kMinCtas < TX16_BT16_MINCTAS ? BtLimits<Z>::kMinCtas : TX16_BT16_MINCTAS);
-}
+constexpr int min_ctas() { return SB == 1 ? BtLimits<Z>::kMinCtas : TX16_BT16_MINCTAS; }
 
 template <int MAXI, class Z, bool DST, int SB>
-__global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, min_ctas<Z, SB>())
+__global__ void __launch_bounds__(32 * bt_warps<Z, SB>(), min_ctas<Z, SB>())
     fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
-  StaticWarps sched{int(blockIdx.x) * BtLimits<Z>::kWarps + int(threadIdx.x >> 5),
-                    int(gridDim.x) * BtLimits<Z>::kWarps, P.ntiles};
+  StaticWarps sched{int(blockIdx.x) * bt_warps<Z, SB>() + int(threadIdx.x >> 5),
+                    int(gridDim.x) * bt_warps<Z, SB>(), P.ntiles};
   bt_tiles<Z, DST, SB>(P.img, P.nimg, P.ntiles, P.sse, sched);
 }
 
@@ -583,7 +589,7 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
     tiles += (imgs[i].nblk + kWarpTile - 1) / kWarpTile;
   }
   P.ntiles = tiles;
-  constexpr int kBtWarps = BtLimits<Z>::kWarps;
+  constexpr int kBtWarps = bt_warps<Z, SB>();
   constexpr int kBtThreads = 32 * kBtWarps;
   constexpr size_t smem =
       size_t(stages<Z, SB>()) * size_t(stage_bytes<Z, SB>()) + size_t(cz_bytes<Z, SB>());
