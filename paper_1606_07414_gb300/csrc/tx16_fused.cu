@@ -22,7 +22,6 @@
 // |k| < 2^24).  The networks come from tx16_pairnet.cuh (generated), where
 // negations are folded into the additions at compile time and the zonal
 // extents prune the work.
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -305,26 +304,21 @@ __device__ __forceinline__ void codec_tiles(const ImgParam* imgs, int nimg, int 
                         : make_float2(0.f, 0.f);
       float2 z[16];
       Z::InvRow::run(w, z);  // z[j] = sign[j] * X_tilde[l][j]
-      // sample = clip(floor(X + 1/2), 0, 255): the low byte of the binary16
-      // value RZ(RD(X + 1024.5)) clamped to [1024, 1279]
-      unsigned h[16];
-      const __half2 lo = __float2half2_rn(1024.f), hi = __float2half2_rn(1279.f);
+      // sample = clip(floor(X + 1/2), 0, 255): the bits of
+      // RD(RD(X + 1/2) 2^-149), clamped and packed four to a word
+      int na[16], nb[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(1024.5f))
-                                                 : sub2_rd(f2(1024.5f), z[j]);
-        const unsigned raw = cvt_rz_h2(r);
-        __half2 hv = *reinterpret_cast<const __half2*>(&raw);
-        hv = __hmin2(__hmax2(hv, lo), hi);
-        h[j] = *reinterpret_cast<const unsigned*>(&hv);
+        const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(0.5f)) : sub2_rd(f2(0.5f), z[j]);
+        const float2 n = floor_bits2(r);
+        na[j] = __float_as_int(n.x);
+        nb[j] = __float_as_int(n.y);
       }
       unsigned xa[4], xb[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const unsigned t01 = __byte_perm(h[4 * q], h[4 * q + 1], 0x6240u);
-        const unsigned t23 = __byte_perm(h[4 * q + 2], h[4 * q + 3], 0x6240u);
-        xa[q] = __byte_perm(t01, t23, 0x5410u);
-        xb[q] = __byte_perm(t01, t23, 0x7632u);
+        xa[q] = pack4_sat_u8(na[4 * q], na[4 * q + 1], na[4 * q + 2], na[4 * q + 3]);
+        xb[q] = pack4_sat_u8(nb[4 * q], nb[4 * q + 1], nb[4 * q + 2], nb[4 * q + 3]);
       }
       if (DST) {
         if (pa.x >= 0)

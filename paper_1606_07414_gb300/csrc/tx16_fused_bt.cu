@@ -22,7 +22,6 @@
 // The arithmetic is that of the two-blocks-per-pair kernel (tx16_fused.cu) on
 // differently paired lanes: the same generated networks, the same binary32
 // quantiser steps and the same exact rounding, so results are identical.
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -99,31 +98,38 @@ struct BtLimits<ZoneC> {
                        kStages = TX16_BT_STAGES_C;
 };
 
-// Quantiser constants of one image for column pairs c < NP and scale classes
-// e(u) = 0, 1, 2; lane .x is column 2c, lane .y column 2c + 1.
-template <int NP>
+// Quantiser constants of one image for column pairs c < NP; lane .x is
+// column 2c, lane .y column 2c + 1.  The scale is zero outside the zone, so a
+// dropped coefficient quantises to level 0 and dequantises to (signed) zero
+// with no test of the zone in the kernel body; g depends only on the scale
+// classes e(u) = 0, 1, 2.
+template <int U, int NP>
 struct PairConsts {
-  float2 fs[3][NP];  // quantiser: sign_v f ; no quantiser: sign_v D'_u D'_v / 256
+  float2 fs[U][NP];  // quantiser: sign_v f ; no quantiser: sign_v D'_u D'_v / 256 ; 0 outside the zone
   float2 gg[3][NP];  // g
   float2 gc[3][NP];  // -2^23 g
 };
 
-template <int NP>
-__device__ __forceinline__ void fill_consts(const ImgParam& I, PairConsts<NP>& Q, int lane) {
-  constexpr int kPer = 6 * NP;  // floats per table
+template <int U, int NP>
+__device__ __forceinline__ void fill_consts(const ImgParam& I, PairConsts<U, NP>& Q, int lane) {
   const bool quant = (I.flags & kQuantFlag) != 0;
   float* q = reinterpret_cast<float*>(&Q);
-  for (int idx = lane; idx < 3 * kPer; idx += 32) {
+  for (int idx = lane; idx < U * 2 * NP; idx += 32) {
+    const int u = idx / (2 * NP);
+    const int v = idx - u * 2 * NP;  // = 2 c + half
+    const int k = scale_class(u) + scale_class(v);
+    const float sv = ((kFwdNegMask >> v) & 1u) ? -1.f : 1.f;
+    const float val = quant ? sv * I.f[k] : sv * float(1 << k) * (1.f / 256.f);
+    q[idx] = u < int(I.colh[v]) ? val : 0.f;
+  }
+  constexpr int kPer = 6 * NP;  // floats per g table
+  for (int idx = lane; idx < 2 * kPer; idx += 32) {
     const int tab = idx / kPer;
     const int rem = idx - tab * kPer;
     const int e = rem / (2 * NP);
-    const int v = rem - e * 2 * NP;  // = 2 c + half
+    const int v = rem - e * 2 * NP;
     const int k = e + scale_class(v);
-    const float sv = ((kFwdNegMask >> v) & 1u) ? -1.f : 1.f;
-    float val;
-    if (quant) val = tab == 0 ? sv * I.f[k] : tab == 1 ? I.g[k] : -8388608.f * I.g[k];
-    else val = tab == 0 ? sv * float(1 << k) * (1.f / 256.f) : 0.f;
-    q[idx] = val;
+    q[U * 2 * NP + idx] = quant ? (tab == 0 ? I.g[k] : -8388608.f * I.g[k]) : 0.f;
   }
   __syncwarp();
 }
@@ -276,10 +282,10 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
   constexpr int NP = V / 2;
   static_assert(V % 2 == 0, "column pairs");
   extern __shared__ __align__(16) uint8_t rows_smem[];  // 2 stages
-  __shared__ PairConsts<NP> consts[kBtWarps];
+  __shared__ PairConsts<Z::U, NP> consts[kBtWarps];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  PairConsts<NP>& Q = consts[wib];
+  PairConsts<Z::U, NP>& Q = consts[wib];
   int t = sched.first();
   if (t < 0) return;
   constexpr int kStages = stages<Z, SB>();  // 2: the next tile is fetched during this one
@@ -315,21 +321,13 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
   // the 16 rows of this thread's block of tile tt (image kk) into stage st
   auto prefetch = [&](int kk, int tt, int st) { fetch_rows(row_src(kk, tt), st, 0, 16); };
   auto tile_end_of = [&](int kk) { return kk + 1 < nimg ? imgs[kk + 1].tile0 : ntiles; };
-  // column heights of image kk, 5 bits each (V <= 8: 40 bits)
-  auto heights = [&](int kk) {
-    unsigned long long hp = 0;
-#pragma unroll
-    for (int v = 0; v < V; ++v) hp |= (unsigned long long)(imgs[kk].colh[v]) << (5 * v);
-    return hp;
-  };
 
   // the image of the tile being coded (k) and of the tile being fetched (kn)
   int k = image_of_tile(imgs, nimg, t);
   int kn = k;
   int end_k = tile_end_of(k), end_kn = end_k;
   prefetch(k, t, 0);
-  unsigned long long hp = heights(k);
-  fill_consts<NP>(imgs[k], Q, lane);
+  fill_consts<Z::U, NP>(imgs[k], Q, lane);
   unsigned long long acc = 0;
   int stage = 0;
   // One stage, rolling refill: the rows of the next tile are fetched row pair
@@ -359,9 +357,8 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
       acc = 0;
       k = image_of_tile(imgs, nimg, t);
       end_k = tile_end_of(k);
-      hp = heights(k);
       __syncwarp();
-      fill_consts<NP>(imgs[k], Q, lane);
+      fill_consts<Z::U, NP>(imgs[k], Q, lane);
     }
     const ImgParam& I = imgs[k];
     const bool quant = (I.flags & kQuantFlag) != 0;
@@ -402,26 +399,21 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
       float2 w[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) w[u] = make_float2(0.f, 0.f);
-      const int h0 = int((hp >> (10 * cp)) & 31u), h1 = int((hp >> (10 * cp + 5)) & 31u);
-      static_assert(5 * V <= 64, "column heights packed in 64 bits");
       if (quant) {
 #pragma unroll
         for (int u = 0; u < Z::U; ++u) {
           const int e = scale_class(u);
-          const float2 tq = __fmul2_rn(n[u], Q.fs[e][cp]);
+          const float2 tq = __fmul2_rn(n[u], Q.fs[u][cp]);
           const float2 a = make_float2(fabsf(tq.x), fabsf(tq.y));
           const float2 m = __fadd2_rd(__fadd2_rd(a, f2(0.5f)), f2(8388608.f));  // 2^23 + floor(|t| + 1/2)
           float2 q = __ffma2_rn(m, Q.gg[e][cp], Q.gc[e][cp]);                 // fl32(level * g)
           q.x = __uint_as_float(__float_as_uint(q.x) | (__float_as_uint(tq.x) & 0x80000000u));
           q.y = __uint_as_float(__float_as_uint(q.y) | (__float_as_uint(tq.y) & 0x80000000u));
-          w[u] = make_float2(u < h0 ? q.x : 0.f, u < h1 ? q.y : 0.f);
+          w[u] = q;
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < Z::U; ++u) {
-          const float2 q = __fmul2_rn(n[u], Q.fs[scale_class(u)][cp]);
-          w[u] = make_float2(u < h0 ? q.x : 0.f, u < h1 ? q.y : 0.f);
-        }
+        for (int u = 0; u < Z::U; ++u) w[u] = __fmul2_rn(n[u], Q.fs[u][cp]);
       }
       float2 z[16];
       Z::InvCol::run(w, z);  // z[i] = (T^t W)[i][2 cp .. 2 cp + 1] (with the network's signs)
@@ -436,7 +428,6 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
 
     // ---- inverse row pass, rounding, store, SSE: rows 2p and 2p + 1 ----
     unsigned s1 = 0, s2 = 0;
-    const __half2 lo = __float2half2_rn(1024.f), hi = __float2half2_rn(1279.f);
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
       float2 wv[16];
@@ -455,25 +446,21 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
       float2 z[16];
       Z::InvRow::run(wv, z);  // z[j] = sign[j] * X_tilde[row][j]
       if (SB == 1) {
-        // sample = clip(floor(X + 1/2), 0, 255): the low byte of the binary16
-        // value RZ(RD(X + 1024.5)) clamped to [1024, 1279]
-        unsigned hh[16];
+        // sample = clip(floor(X + 1/2), 0, 255): the bits of
+        // RD(RD(X + 1/2) 2^-149), clamped and packed four to a word
+        int na[16], nb[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(1024.5f))
-                                                   : sub2_rd(f2(1024.5f), z[j]);
-          const unsigned raw = cvt_rz_h2(r);
-          __half2 hv = *reinterpret_cast<const __half2*>(&raw);
-          hv = __hmin2(__hmax2(hv, lo), hi);
-          hh[j] = *reinterpret_cast<const unsigned*>(&hv);
+          const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(0.5f)) : sub2_rd(f2(0.5f), z[j]);
+          const float2 n = floor_bits2(r);
+          na[j] = __float_as_int(n.x);
+          nb[j] = __float_as_int(n.y);
         }
         unsigned xa[4], xb[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const unsigned t01 = __byte_perm(hh[4 * q], hh[4 * q + 1], 0x6240u);
-          const unsigned t23 = __byte_perm(hh[4 * q + 2], hh[4 * q + 3], 0x6240u);
-          xa[q] = __byte_perm(t01, t23, 0x5410u);
-          xb[q] = __byte_perm(t01, t23, 0x7632u);
+          xa[q] = pack4_sat_u8(na[4 * q], na[4 * q + 1], na[4 * q + 2], na[4 * q + 3]);
+          xb[q] = pack4_sat_u8(nb[4 * q], nb[4 * q + 1], nb[4 * q + 2], nb[4 * q + 3]);
         }
         if (DST && valid) {
           const int64_t dp = imgs[k].dst_pitch;
@@ -496,28 +483,23 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
           s2 = __dp4a(ib[q], xb[q], s2);
         }
       } else {
-        // sample = clip(floor(X + 1/2), 0, peak): R = RD(X + 1024.5), then
-        // RD(R + 2^23 + 64512) = 2^23 + 65536 + floor(R) - 1024 exactly
-        // (floor(RD(v)) = floor(v); the sum lies in [2^23, 2^24) where the
-        // spacing is 1); its bits, clamped as integers to
-        // [2^23 + 65536, 2^23 + 65536 + peak] (bits of floats are ordered),
-        // hold the sample in their low 16 bits
-        const int peak = (1 << (imgs[k].flags & 0xff)) - 1;
-        const int bmin = 0x4B010000, bmax = 0x4B010000 + peak;
+        // sample = clip(floor(X + 1/2), 0, peak): the bits of
+        // RD(RD(X + 1/2) 2^-149), clamped and packed two to a word
+        const unsigned peak2 = ((1u << (imgs[k].flags & 0xff)) - 1u) * 0x10001u;
         unsigned ya[8], yb[8];  // reconstructed rows 2p and 2p + 1, two samples per word
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
           int va[2], vb[2];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            const float2 r = Z::InvRow::sign(j + e) >= 0 ? __fadd2_rd(z[j + e], f2(1024.5f))
-                                                         : sub2_rd(f2(1024.5f), z[j + e]);
-            const float2 m = __fadd2_rd(r, f2(8388608.f + 64512.f));
-            va[e] = min(max(__float_as_int(m.x), bmin), bmax);
-            vb[e] = min(max(__float_as_int(m.y), bmin), bmax);
+            const float2 r = Z::InvRow::sign(j + e) >= 0 ? __fadd2_rd(z[j + e], f2(0.5f))
+                                                         : sub2_rd(f2(0.5f), z[j + e]);
+            const float2 n = floor_bits2(r);
+            va[e] = __float_as_int(n.x);
+            vb[e] = __float_as_int(n.y);
           }
-          ya[j >> 1] = __byte_perm(unsigned(va[0]), unsigned(va[1]), 0x5410u);
-          yb[j >> 1] = __byte_perm(unsigned(vb[0]), unsigned(vb[1]), 0x5410u);
+          ya[j >> 1] = pack2_sat_u16(va[0], va[1], peak2);
+          yb[j >> 1] = pack2_sat_u16(vb[0], vb[1], peak2);
         }
         if (DST && valid) {
           const int64_t dp = imgs[k].dst_pitch;

@@ -1,7 +1,7 @@
 // Pieces shared by the two fused 8-bit codec kernels (tx16_fused.cu: two
 // blocks per thread pair through shared memory; tx16_fused_bt.cu: one block
 // per thread in registers): the zonal classes with their pruned networks, the
-// exact byte-to-float and float-to-binary16 conversions, block coordinates
+// exact byte-to-float conversion and sample rounding, block coordinates
 // and the per-image SSE flush.
 #pragma once
 
@@ -38,10 +38,37 @@ __device__ __forceinline__ float biased(unsigned w, int k) {
   return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | unsigned(k)));
 }
 
-// fl32 pair -> f16 pair with round toward zero; .x goes to the low half
-__device__ __forceinline__ unsigned cvt_rz_h2(float2 v) {
-  unsigned d;
-  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.y), "f"(v.x));
+// Exact rounding of reconstructed samples, clip(floor(X + 1/2), 0, peak), in
+// two packed operations and a saturating pack:
+//   v = RD(X + 1/2)     floor(v) = floor(X + 1/2): that integer is a binary32
+//                       value not above X + 1/2, so RD cannot fall below it;
+//   RD(v * 2^-149)      the multiple of the smallest subnormal not above
+//                       v * 2^-149: for 0 <= v < 2^23 the subnormal whose bits
+//                       are the integer floor(v); for v < 0 a negative value
+//                       (or -0), whose bits read as int32 are negative; for
+//                       larger v a value whose bits exceed any peak (the bits
+//                       of non-negative floats are ordered like their values).
+// The bits, read as int32, are then clamped to [0, peak] as integers.
+// (The flush of subnormals is off in this build: no -ftz, no fast math.)
+__device__ __forceinline__ float2 floor_bits2(float2 v) { return __fmul2_rd(v, f2(__int_as_float(1))); }
+
+// four int32 values clamped to [0, 255], as the bytes s0 (lowest) .. s3 of one word
+__device__ __forceinline__ unsigned pack4_sat_u8(int s0, int s1, int s2, int s3) {
+  unsigned t, d;
+  // cvt.pack.sat.u8.s32.b32 d, a, b, c: d = c << 16 | sat(a) << 8 | sat(b)
+  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(t) : "r"(s3), "r"(s2), "r"(0));
+  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(s1), "r"(s0), "r"(t));
+  return d;
+}
+
+// two int32 values clamped to [0, peak] (peak < 2^16), as the low (s0) and
+// high (s1) halves of one word: saturating pack to [0, 65535], then a packed
+// 16-bit minimum with the peak
+__device__ __forceinline__ unsigned pack2_sat_u16(int s0, int s1, unsigned peak2) {
+  unsigned t, d;
+  // cvt.pack.sat.u16.s32 d, a, b: d = sat(a) << 16 | sat(b)
+  asm("cvt.pack.sat.u16.s32 %0, %1, %2;" : "=r"(t) : "r"(s1), "r"(s0));
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(t), "r"(peak2));
   return d;
 }
 
