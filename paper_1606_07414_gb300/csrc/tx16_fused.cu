@@ -326,21 +326,18 @@ __device__ __forceinline__ void codec_tiles(const ImgParam* imgs, int nimg, int 
         if (pb.x >= 0)
           __stcs(reinterpret_cast<uint4*>(S.dst + int64_t(pb.x) * S.dp + pb.y), make_uint4(xb[0], xb[1], xb[2], xb[3]));
       }
-      // SSE = sum x^2 + sum y^2 - 2 sum x y over the row's bytes (dp4a).  A
+      // SSE = sum |x - y|^2 over the row's bytes (vabsdiff4, then dp4a).  A
       // block past the end of the image was loaded as zeros and reconstructs
       // to zeros, so it adds nothing.
       const unsigned ia[4] = {ca.x, ca.y, ca.z, ca.w}, ib[4] = {cb.x, cb.y, cb.z, cb.w};
-      unsigned s1 = 0, s2 = 0;
+      unsigned s1 = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        s1 = __dp4a(ia[q], ia[q], s1);
-        s1 = __dp4a(xa[q], xa[q], s1);
-        s1 = __dp4a(ib[q], ib[q], s1);
-        s1 = __dp4a(xb[q], xb[q], s1);
-        s2 = __dp4a(ia[q], xa[q], s2);
-        s2 = __dp4a(ib[q], xb[q], s2);
+        const unsigned da = __vabsdiffu4(ia[q], xa[q]), db = __vabsdiffu4(ib[q], xb[q]);
+        s1 = __dp4a(da, da, s1);
+        s1 = __dp4a(db, db, s1);
       }
-      acc += (unsigned long long)(s1 - 2u * s2);
+      acc += s1;
     }
     t = tn;
   }

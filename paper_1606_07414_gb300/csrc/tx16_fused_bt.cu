@@ -366,6 +366,10 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
     const bool valid = blk < I.nblk;
     const int2 c = valid ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
     const uint8_t* rows = rows_smem + stage * kStageBytes + threadIdx.x * 16;  // slot 0 of this thread
+    // this thread's block in the output plane (the image's first block for a
+    // lane past its end, which stores nothing)
+    const int64_t dpitch = DST ? I.dst_pitch : 0;
+    uint8_t* const dblk = DST ? static_cast<uint8_t*>(I.dst) + int64_t(c.x) * 16 * dpitch + c.y * 16 * SB : nullptr;
 
     // ---- forward row pass: R[p][v] = (row 2p, row 2p + 1) at column v ----
     float2 R[8][V];
@@ -427,7 +431,7 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
     }
 
     // ---- inverse row pass, rounding, store, SSE: rows 2p and 2p + 1 ----
-    unsigned s1 = 0, s2 = 0;
+    unsigned s1 = 0;  // squared error of this tile's block
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
       float2 wv[16];
@@ -462,25 +466,21 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
           xa[q] = pack4_sat_u8(na[4 * q], na[4 * q + 1], na[4 * q + 2], na[4 * q + 3]);
           xb[q] = pack4_sat_u8(nb[4 * q], nb[4 * q + 1], nb[4 * q + 2], nb[4 * q + 3]);
         }
-        if (DST && valid) {
-          const int64_t dp = imgs[k].dst_pitch;
-          uint8_t* drow = static_cast<uint8_t*>(imgs[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 16;
-          __stcs(reinterpret_cast<uint4*>(drow), make_uint4(xa[0], xa[1], xa[2], xa[3]));
-          __stcs(reinterpret_cast<uint4*>(drow + dp), make_uint4(xb[0], xb[1], xb[2], xb[3]));
+        if (DST) {
+          uint8_t* drow = dblk + 2 * p * dpitch;
+          if (valid) __stcs(reinterpret_cast<uint4*>(drow), make_uint4(xa[0], xa[1], xa[2], xa[3]));
+          if (valid) __stcs(reinterpret_cast<uint4*>(drow + dpitch), make_uint4(xb[0], xb[1], xb[2], xb[3]));
         }
-        // SSE = sum x^2 + sum y^2 - 2 sum x y; a block past the image's end
-        // was staged as zeros and reconstructs to zeros
+        // SSE = sum |x - y|^2 by bytes (vabsdiff4, then dp4a); a block past
+        // the image's end was staged as zeros and reconstructs to zeros
         const uint4 a = *reinterpret_cast<const uint4*>(rows + (2 * p) * kSlot);
         const uint4 b = *reinterpret_cast<const uint4*>(rows + (2 * p + 1) * kSlot);
         const unsigned ia[4] = {a.x, a.y, a.z, a.w}, ib[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          s1 = __dp4a(ia[q], ia[q], s1);
-          s1 = __dp4a(xa[q], xa[q], s1);
-          s1 = __dp4a(ib[q], ib[q], s1);
-          s1 = __dp4a(xb[q], xb[q], s1);
-          s2 = __dp4a(ia[q], xa[q], s2);
-          s2 = __dp4a(ib[q], xb[q], s2);
+          const unsigned da = __vabsdiffu4(ia[q], xa[q]), db = __vabsdiffu4(ib[q], xb[q]);
+          s1 = __dp4a(da, da, s1);
+          s1 = __dp4a(db, db, s1);
         }
       } else {
         // sample = clip(floor(X + 1/2), 0, peak): the bits of
@@ -501,13 +501,12 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
           ya[j >> 1] = pack2_sat_u16(va[0], va[1], peak2);
           yb[j >> 1] = pack2_sat_u16(vb[0], vb[1], peak2);
         }
-        if (DST && valid) {
-          const int64_t dp = imgs[k].dst_pitch;
-          uint8_t* drow = static_cast<uint8_t*>(imgs[k].dst) + (int64_t(c.x) * 16 + 2 * p) * dp + c.y * 32;
-          __stcs(reinterpret_cast<uint4*>(drow), make_uint4(ya[0], ya[1], ya[2], ya[3]));
-          __stcs(reinterpret_cast<uint4*>(drow) + 1, make_uint4(ya[4], ya[5], ya[6], ya[7]));
-          __stcs(reinterpret_cast<uint4*>(drow + dp), make_uint4(yb[0], yb[1], yb[2], yb[3]));
-          __stcs(reinterpret_cast<uint4*>(drow + dp) + 1, make_uint4(yb[4], yb[5], yb[6], yb[7]));
+        if (DST) {
+          uint8_t* drow = dblk + 2 * p * dpitch;
+          if (valid) __stcs(reinterpret_cast<uint4*>(drow), make_uint4(ya[0], ya[1], ya[2], ya[3]));
+          if (valid) __stcs(reinterpret_cast<uint4*>(drow) + 1, make_uint4(ya[4], ya[5], ya[6], ya[7]));
+          if (valid) __stcs(reinterpret_cast<uint4*>(drow + dpitch), make_uint4(yb[0], yb[1], yb[2], yb[3]));
+          if (valid) __stcs(reinterpret_cast<uint4*>(drow + dpitch) + 1, make_uint4(yb[4], yb[5], yb[6], yb[7]));
         }
         // SSE: integer differences of the staged samples and the reconstruction
         unsigned wa[8], wb[8];
@@ -523,7 +522,7 @@ __device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int 
       // rows 2p and 2p + 1 of the stage are used: refill them for the next tile
       if (kRolling && tn >= 0) fetch_rows(next, 0, 2 * p, 2 * p + 2);
     }
-    acc += SB == 1 ? (unsigned long long)(s1 - 2u * s2) : (unsigned long long)s1;
+    acc += s1;
     if (kStages == 1 && !kRolling && tn >= 0) prefetch(kn, tn, 0);  // the used rows replaced at once
     rolling = kRolling && tn >= 0;
     t = tn;

@@ -370,3 +370,65 @@ def test_codec_16bit_2160p_frame(tx):
     got = np.stack([rec[(b // nbx) * 16:(b // nbx) * 16 + 16, (b % nbx) * 16:(b % nbx) * 16 + 16] for b in pick])
     ref = oracle_blocks(X.astype(np.int64), 16.0, 16, bits)
     assert np.array_equal(got, ref["recon"])
+
+
+# --------------------------------------------------------------------------
+# Clamping at both ends of the sample range: planes of extreme samples whose
+# zonal reconstructions overshoot far below 0 and above the peak (Gibbs-like
+# ringing), through the one-block-per-thread kernels (no levels, r <= 32),
+# the pair kernel (levels requested, or r > 32) and the 16-bit path
+# --------------------------------------------------------------------------
+def _extreme_planes(bits):
+    peak = (1 << bits) - 1
+    dt = np.uint8 if bits == 8 else np.uint16
+    ii, jj = np.indices((64, 96))
+    rng = np.random.default_rng(bits)
+    planes = [((ii + jj) % 2) * peak,                      # checkerboard
+              ((jj // 3) % 2) * peak,                      # vertical stripes, 3 wide
+              ((ii // 2) % 2) * peak,                      # horizontal stripes, 2 wide
+              (jj >= 45) * peak,                           # step edge inside a block
+              rng.integers(0, 2, (64, 96)) * peak,         # random two-level
+              np.full((64, 96), peak), np.zeros((64, 96))]
+    return [p.astype(dt) for p in planes]
+
+
+@pytest.mark.parametrize("q,r,levels", [(None, 32, False), (None, 16, False), (64.0, 4, False), (64.0, 16, False),
+                                        (16.0, 32, False), (8.0, 16, True), (64.0, 64, False), (32.0, 256, True),
+                                        (None, 150, True)])
+def test_codec_extreme_planes_clamp(tx, q, r, levels):
+    import torch
+
+    planes = _extreme_planes(8)
+    keep = [to_dev(p) for p in planes]
+    outs = [empty_like_img(64, 96, 8, pad=16) for _ in planes]
+    sse = torch.full((len(planes),), -1, dtype=torch.int64, device="cuda")
+    lev = _coeffs(len(planes) * 24) if levels else None
+    tx.tx16_codec_batch([tx.image(d) for d in keep], [tx.image(o) for o in outs], [(q, r)] * len(planes),
+                        sse=sse, levels=lev)
+    torch.cuda.synchronize()
+    overshoot = 0
+    for i, im in enumerate(planes):
+        ref = oracle_blocks(O.image_to_blocks(im.astype(np.int64)), q, r, 8)
+        rec = from_dev(outs[i], 8)
+        assert np.array_equal(O.image_to_blocks(rec.astype(np.int64)), ref["recon"]), i
+        assert int(sse[i].item()) == O.sse(im, rec), i
+        overshoot += int(np.sum((ref["X64"] < -0.5) | (ref["X64"] > 255.5)))
+    assert overshoot > 0  # the clamps were exercised
+
+
+@pytest.mark.parametrize("bits,q,r", [(10, 64.0, 4), (10, 16.0, 16), (12, 64.0, 32), (9, 8.0, 16)])
+def test_codec_16bit_extreme_planes_clamp(tx, bits, q, r):
+    import torch
+
+    planes = _extreme_planes(bits)
+    keep = [to_dev(p) for p in planes]
+    outs = [empty_like_img(64, 96, bits, pad=8) for _ in planes]
+    sse = torch.full((len(planes),), -1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_batch([tx.image(d, bits) for d in keep], [tx.image(o, bits) for o in outs],
+                        [(q, r)] * len(planes), sse=sse)
+    torch.cuda.synchronize()
+    for i, im in enumerate(planes):
+        ref = oracle_blocks(O.image_to_blocks(im.astype(np.int64)), q, r, bits)
+        rec = from_dev(outs[i], bits)
+        assert np.array_equal(O.image_to_blocks(rec.astype(np.int64)), ref["recon"]), i
+        assert int(sse[i].item()) == O.sse(im, rec), i
