@@ -13,11 +13,13 @@
 //   row pass     re-paired into (row 2p, row 2p+1) again: inverse row
 //                network, rounding, 16-byte stores, squared error
 // No shared-memory exchange and no barrier.  Shared memory holds each
-// thread's 16 input rows, double-buffered for most classes: while a tile is
-// coded, cp.async brings the warp's next tile; the squared error reads the
-// rows there again.  A small per-warp table holds the quantiser constants of the image
-// being coded (each lane of a column pair has its own column's scale and
-// sign).
+// thread's 16 input rows (one stage by default: cp.async refills it with the
+// warp's next tile once the current rows are used, and the other warps of the
+// SM cover that latency; two stages are a compile-time option), the inverse
+// column results of the parked column pairs, and a small per-warp table of
+// the quantiser constants of the image being coded (each lane of a column
+// pair has its own column's scale and sign).  The squared error reads the
+// staged rows again.
 //
 // The arithmetic is that of the two-blocks-per-pair kernel (tx16_fused.cu) on
 // differently paired lanes: the same generated networks, the same binary32
@@ -37,19 +39,19 @@ namespace {
 
 constexpr int kWarpTile = 32;  // blocks per warp tile
 
-// Warps per CTA, resident CTAs per SM the registers are budgeted for, and
-// column pairs parked in shared memory, per zonal class (compile-time
-// tunable; the register limit per thread is 65536 / (32 * warps * CTAs)).
-// Measured on 1920x1088 frames: class A (4 kept columns) 3 CTAs of 4 warps,
-// two input stages; class B (6) 3 CTAs with one column pair parked and one
-// input stage (the next tile is fetched after the current one's rows are
-// used; other warps cover the latency), which fits 168 registers; class C (8)
-// 2 CTAs, one pair parked, two stages.
+// Warps per CTA, resident CTAs per SM the registers are budgeted for, column
+// pairs parked in shared memory and input stages, per zonal class
+// (compile-time tunable; the register limit per thread is 65536 / (32 * warps
+// * CTAs)).  Measured on 1920x1088 frames, all with one input stage (the next
+// tile is fetched after the current one's rows are used; other warps cover
+// the latency) and 4-warp CTAs: class A (4 kept columns) one of its two
+// column pairs parked, 4 CTAs per SM (111 registers); class B (6) one pair
+// parked, 3 CTAs (147 registers); class C (8) two pairs parked, 3 CTAs.
 #ifndef TX16_BT_WARPS_A
 #define TX16_BT_WARPS_A 4
 #endif
 #ifndef TX16_BT_MINCTAS_A
-#define TX16_BT_MINCTAS_A 3
+#define TX16_BT_MINCTAS_A 4
 #endif
 #ifndef TX16_BT_WARPS_B
 #define TX16_BT_WARPS_B 4
@@ -61,22 +63,25 @@ constexpr int kWarpTile = 32;  // blocks per warp tile
 #define TX16_BT_WARPS_C 4
 #endif
 #ifndef TX16_BT_MINCTAS_C
-#define TX16_BT_MINCTAS_C 2
+#define TX16_BT_MINCTAS_C 3
+#endif
+#ifndef TX16_BT_CZ_SMEM_A
+#define TX16_BT_CZ_SMEM_A 1
 #endif
 #ifndef TX16_BT_CZ_SMEM_B
 #define TX16_BT_CZ_SMEM_B 1
 #endif
 #ifndef TX16_BT_CZ_SMEM_C
-#define TX16_BT_CZ_SMEM_C 1
+#define TX16_BT_CZ_SMEM_C 2
 #endif
 #ifndef TX16_BT_STAGES_A
-#define TX16_BT_STAGES_A 2
+#define TX16_BT_STAGES_A 1
 #endif
 #ifndef TX16_BT_STAGES_B
 #define TX16_BT_STAGES_B 1
 #endif
 #ifndef TX16_BT_STAGES_C
-#define TX16_BT_STAGES_C 2
+#define TX16_BT_STAGES_C 1
 #endif
 // kCzSmem: the inverse column results of the first kCzSmem column pairs wait
 // in shared memory (16 float2 per thread and pair) instead of registers.
@@ -84,7 +89,7 @@ template <class Z>
 struct BtLimits;
 template <>
 struct BtLimits<ZoneA> {
-  static constexpr int kWarps = TX16_BT_WARPS_A, kMinCtas = TX16_BT_MINCTAS_A, kCzSmem = 0,
+  static constexpr int kWarps = TX16_BT_WARPS_A, kMinCtas = TX16_BT_MINCTAS_A, kCzSmem = TX16_BT_CZ_SMEM_A,
                        kStages = TX16_BT_STAGES_A;
 };
 template <>
