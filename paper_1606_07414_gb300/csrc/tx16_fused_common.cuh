@@ -28,8 +28,17 @@ struct Zone {
 using ZoneA = Zone<3, 4, FwdRow4, FwdCol3, InvCol3, InvRow4, 8>;        // r <= 8
 using ZoneB = Zone<5, 6, FwdRow6, FwdCol5, InvCol5, InvRow6, 8>;        // r <= 16
 using ZoneC = Zone<7, 8, FwdRow8, FwdCol7, InvCol7, InvRow8, 6>;        // r <= 32
-using ZoneD = Zone<11, 10, FwdRow10, FwdCol11, InvCol11, InvRow10, 5>;  // r <= 64
-using ZoneE = Zone<16, 16, FwdRow16, FwdCol16, InvCol16, InvRow16, 4>;  // any r
+// resident CTAs per SM the pair kernel's registers are budgeted for, classes D and E
+// (compile-time tunable; measured on 1920x1088 frames: 7 and 6 beat 5 and 4
+// by 2.5 and 5 %; more spill)
+#ifndef TX16_PAIR_MINCTAS_D
+#define TX16_PAIR_MINCTAS_D 7
+#endif
+#ifndef TX16_PAIR_MINCTAS_E
+#define TX16_PAIR_MINCTAS_E 6
+#endif
+using ZoneD = Zone<11, 10, FwdRow10, FwdCol11, InvCol11, InvRow10, TX16_PAIR_MINCTAS_D>;  // r <= 64
+using ZoneE = Zone<16, 16, FwdRow16, FwdCol16, InvCol16, InvRow16, TX16_PAIR_MINCTAS_E>;  // any r
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
