@@ -682,6 +682,12 @@ def _oracle_frame(job):
     return frame.shape
 
 
+def _oracle_frame_timed(job):
+    t0 = time.perf_counter()
+    _oracle_frame(job)
+    return time.perf_counter() - t0
+
+
 def cpu_oracle_rate(frames_np, q, r, pool=None, cores=None):
     import multiprocessing as mp
 
@@ -695,13 +701,17 @@ def cpu_oracle_rate(frames_np, q, r, pool=None, cores=None):
     t0 = time.perf_counter()
     pool.map(_oracle_frame, [(f, q, r) for f in frames_np], chunksize=1)
     dt = time.perf_counter() - t0
+    t1 = pool.apply(_oracle_frame_timed, ((frames_np[0], q, r),))  # one frame, one core
     if own:
         pool.close()
         pool.join()
     nblk = len(frames_np) * (frames_np.shape[1] // 16) * (frames_np.shape[2] // 16)
+    nblk1 = (frames_np.shape[1] // 16) * (frames_np.shape[2] // 16)
     return {"value": round(nblk / dt / 1e6, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(frames_np)} of the {FRAMES} frames (float64 oracle codec_image, one frame per "
-                      f"task, {cores} single-threaded processes), {dt:.2f} s wall"}
+                      f"task, {cores} single-threaded processes), {dt:.2f} s wall",
+            "single_thread": {"value": round(nblk1 / t1 / 1e6, 5), "unit": UNIT, "cores": 1,
+                              "sample": f"one frame in one single-threaded process, {t1:.3f} s"}}
 
 
 def run_reference(args):
