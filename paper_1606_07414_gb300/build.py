@@ -32,6 +32,22 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: libtx16 needs the CUDA toolkit to build")
 
 
+# Flags that make binary32 arithmetic flush subnormal results to zero.  The
+# fused kernels round reconstructed samples through a subnormal whose bits are
+# the sample, so a build with any of these would be silently wrong.
+_FTZ_FLAGS = ("-ftz=true", "--ftz=true", "-use_fast_math", "--use_fast_math")
+
+
+def extra_flags() -> list[str]:
+    """Extra nvcc flags from TX16_NVCC_FLAGS, refusing those that flush
+    subnormals (ValueError)."""
+    extra = os.environ.get("TX16_NVCC_FLAGS", "").split()
+    bad = [f for f in extra if f.lower() in _FTZ_FLAGS]
+    if bad:
+        raise ValueError(f"TX16_NVCC_FLAGS {bad}: the fused kernels need subnormal results (no flush to zero)")
+    return extra
+
+
 def _sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
@@ -57,7 +73,7 @@ def build(verbose: bool = False, ptxas_info: bool = False, force: bool = False) 
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_time):
-            cmd = [nvcc, *ARCH, *FLAGS, *os.environ.get("TX16_NVCC_FLAGS", "").split(), "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *FLAGS, *extra_flags(), "-c", src, "-o", obj]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

@@ -157,3 +157,16 @@ def test_new_entry_points_reject_bad_arguments_before_any_device_call(lib):
     # empty batches are valid no-ops
     assert lib.tx16_codec_any_size(good, None, 0, qp, None, None) == tx16.TX16_OK
     assert lib.tx16_codec_mixed(good, None, 0, ctypes.cast(m, ctypes.c_void_p), None, None, None) == tx16.TX16_OK
+
+
+def test_build_refuses_flush_to_zero_flags(monkeypatch):
+    """The fused kernels' sample rounding goes through subnormal binary32
+    values, so extra nvcc flags that flush them are refused before compiling."""
+    from paper_1606_07414_gb300 import build
+
+    for bad in ("-ftz=true", "--use_fast_math", "-O3 -use_fast_math"):
+        monkeypatch.setenv("TX16_NVCC_FLAGS", bad)
+        with pytest.raises(ValueError):
+            build.extra_flags()
+    monkeypatch.setenv("TX16_NVCC_FLAGS", "-DTX16_BT_MINCTAS_B=3 -ftz=false")
+    assert build.extra_flags() == ["-DTX16_BT_MINCTAS_B=3", "-ftz=false"]
