@@ -8,9 +8,9 @@
 //
 // Mapping: 16 threads per block (thread l: row l, then column v = l), 16
 // blocks per CTA, int32 networks (tx16_net.cuh), row/column exchange through
-// a 16 x 17-word shared buffer per block; squared errors accumulate in
-// registers per r and are flushed with one atomic per warp and r when the
-// image changes.
+// a 16 x 17-word shared buffer per block; each r's squared error is summed
+// over the warp by shuffles into a per-warp shared-memory slot, flushed with
+// one atomic per warp and r when the image changes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,8 +62,12 @@ __device__ __forceinline__ void load_row(const void* p, int (&x)[16]) {
 template <typename Smp, int MAXI>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams<MAXI> P) {
   __shared__ int sm[16][16][17];
+  // per warp and r: squared error of the current image (lane 0 of the warp
+  // adds the warp's sum after each block pair; flushed on an image change)
+  __shared__ unsigned long long wacc[8][kSweepMaxR];
   const int l = threadIdx.x & 15;
   const int b = threadIdx.x >> 4;
+  const int wib = threadIdx.x >> 5;
   int(*Sx)[17] = sm[b];
   const int per = (P.ntiles + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * per;
@@ -71,22 +75,20 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   if (t0 >= t1) return;
   int k = 0;
   while (k + 1 < P.nimg && P.img[k + 1].tile0 <= t0) ++k;
-  unsigned long long acc[kSweepMaxR];
-#pragma unroll
-  for (int i = 0; i < kSweepMaxR; ++i) acc[i] = 0;
+  if ((threadIdx.x & 31) < kSweepMaxR) wacc[wib][threadIdx.x & 31] = 0;
+  __syncwarp();
   int acc_img = k;
   const int ev = scale_class(l);
 
-  auto flush = [&](int img) {
-#pragma unroll
-    for (int i = 0; i < kSweepMaxR; ++i) {
-      if (i >= P.nr) break;
-      unsigned long long v = acc[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0 && v) atomicAdd(P.sse + int64_t(img) * P.nr + i, v);
-      acc[i] = 0;
+  auto flush = [&](int img) {  // lane i < nr flushes r number i of its warp
+    __syncwarp();
+    const int i = threadIdx.x & 31;
+    if (i < P.nr) {
+      const unsigned long long v = wacc[wib][i];
+      if (v) atomicAdd(P.sse + int64_t(img) * P.nr + i, v);
+      wacc[wib][i] = 0;
     }
+    __syncwarp();
   };
 
   for (int t = t0; t < t1; ++t) {
@@ -150,16 +152,28 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       unsigned s = 0;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int n = z[j];
-        int pv = n >= 0 ? (n + 128) >> 8 : -((128 - n) >> 8);
-        pv = min(max(pv, 0), peak);
+        // round half away from zero of n / 256, clipped: a negative n
+        // clips to 0 whichever way it rounds, so floor((n + 128) / 256)
+        // (arithmetic shift) serves for every n
+        const int pv = min(max((z[j] + 128) >> 8, 0), peak);
         const int d = x0[j] - pv;
         s += unsigned(d * d);
       }
-      // accumulate into the register of this r (the unrolled index keeps it a register)
+      if (!valid) s = 0;
+      // the warp's sum for this r (two blocks, 32 rows), added by lane 0: in
+      // 32 bits for 8-bit samples (at most 32 * 16 * 255^2 < 2^32), in 64
+      // bits beyond
+      unsigned long long v;
+      if (sizeof(Smp) == 1) {
 #pragma unroll
-      for (int i = 0; i < kSweepMaxR; ++i)
-        if (i == ri && valid) acc[i] += s;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        v = s;
+      } else {
+        v = s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      }
+      if ((threadIdx.x & 31) == 0) wacc[wib][ri] += v;
     }
   }
   flush(acc_img);

@@ -52,3 +52,27 @@ def test_sweep_equals_one_codec_call_per_r(tx):
         s1 = torch.zeros(1, dtype=torch.int64, device="cuda")
         tx.tx16_codec_batch([img], None, [(None, r)], sse=s1)
         assert int(s1.item()) == int(sse[j].item())
+
+
+def test_sweep_extreme_planes_all_depths(tx):
+    """Planes of extreme samples (checkerboards, stripes and a step of 0 and
+    the peak) at 8, 10 and 12 bits: large per-row errors in the warp sums and
+    reconstructions clipped at both ends, exact against the oracle for every r."""
+    import torch
+
+    ii, jj = np.indices((48, 64))
+    imgs, bitss = [], []
+    for bits in (8, 10, 12):
+        peak = (1 << bits) - 1
+        dt = np.uint8 if bits == 8 else np.uint16
+        for pat in (((ii + jj) % 2) * peak, ((jj // 3) % 2) * peak, (jj >= 21) * peak):
+            imgs.append(pat.astype(dt))
+            bitss.append(bits)
+    keep = [to_dev(im) for im in imgs]
+    devs = [tx.image(t, b) for t, b in zip(keep, bitss)]
+    sse = torch.full((len(imgs) * len(R_LIST),), 7, dtype=torch.int64, device="cuda")
+    tx.tx16_zonal_sweep(devs, R_LIST, sse)
+    got = sse.cpu().numpy().reshape(len(imgs), len(R_LIST))
+    for i, (im, bits) in enumerate(zip(imgs, bitss)):
+        for j, r in enumerate(R_LIST):
+            assert got[i, j] == O.codec_image(im, None, r, bits)["sse"], (i, bits, r)
