@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(kThreads) any_size_kernel(const __grid_constan
     const ImgParam& I = A.p;
     const int blk = (t - I.tile0) * kTileBlocks + b;
     const bool valid = blk < I.nblk;
-    const int by = valid ? blk / I.nbx : 0;
-    const int bx = valid ? blk - by * I.nbx : 0;
+    int by = 0, bx = 0;
+    if (valid) block_row_col(I.div_magic, I.nbx, blk, by, bx);
     const int y = by * 16 + l;                 // image row of this thread's block row
     const int ysrc = min(y, A.h - 1);          // rows below the image repeat the last row
     const int x0 = bx * 16;

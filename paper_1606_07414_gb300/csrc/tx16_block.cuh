@@ -58,6 +58,20 @@ struct RowIO<uint16_t> {
   }
 };
 
+// (by, bx) of block blk of an image nbx blocks wide, without a division: the
+// high product of blk and magic = floor(2^32 / nbx) (2^32 - 1 for nbx = 1) is
+// the quotient or one short of it for blk < 2^31, and one compare corrects it
+__device__ __forceinline__ void block_row_col(uint32_t magic, int nbx, int blk, int& by, int& bx) {
+  int q = int(__umulhi(unsigned(blk), magic));
+  int r = blk - q * nbx;
+  if (r >= nbx) {
+    ++q;
+    r -= nbx;
+  }
+  by = q;
+  bx = r;
+}
+
 __device__ __forceinline__ int round_div256(int n) {
   // round_half_away(n / 256) in exact integers
   return n >= 0 ? (n + 128) >> 8 : -((128 - n) >> 8);

@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(kThreads) block_kernel(const __grid_constant__
     const ImgParam& I = P.img[k];
     const int blk = (t - I.tile0) * kTileBlocks + b;
     const bool valid = blk < I.nblk;
-    const int by = valid ? blk / I.nbx : 0;
-    const int bx = valid ? blk - by * I.nbx : 0;
+    int by = 0, bx = 0;
+    if (valid) block_row_col(I.div_magic, I.nbx, blk, by, bx);
     const int64_t row = int64_t(by) * 16 + l;
     const int64_t col_bytes = int64_t(bx) * 16 * int64_t(sizeof(Smp));
 

@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(kThreads) mixed_kernel(const __grid_constant__
     const ImgParam& I = M.p;
     const int blk = (t - I.tile0) * kTileBlocks + b;
     const bool valid = blk < I.nblk;
-    const int by = valid ? blk / I.nbx : 0;
-    const int bx = valid ? blk - by * I.nbx : 0;
+    int by = 0, bx = 0;
+    if (valid) block_row_col(I.div_magic, I.nbx, blk, by, bx);
     uint4 raw[IO::kVec];
     if (valid) {
       IO::load(static_cast<const char*>(I.src) + (int64_t(by) * 16 + l) * I.src_pitch +
