@@ -214,6 +214,12 @@ def run_gpu(args):
     }
     line.update(extra)
     line["clocks"] = clocks
+    prop = torch.cuda.get_device_properties(local_rank)
+    line["device"] = {"name": prop.name, "sm_count": prop.multi_processor_count,
+                      "compute_capability": f"{prop.major}.{prop.minor}",
+                      "hbm_gib": round(prop.total_memory / 2**30, 1)}
+    line["seeds"] = {"frames": SEED, "per_rank": "frames seed + rank", "10bit_frames": SEED + 10,
+                     "uneven_sizes": SEED + 9, "uneven_fields": f"{SEED + 700}..", "serving_arrivals": "seed + rate"}
     print(json.dumps(line), flush=True)
 
 

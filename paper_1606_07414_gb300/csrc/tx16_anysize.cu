@@ -209,6 +209,7 @@ using namespace tx16;
 
 extern "C" tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_image* out, int32_t n,
                                            const tx16_qparams* qp, uint64_t* sse, void* stream) {
+  TX16_TRACE("tx16_codec_any_size");
   if (n < 0 || (n > 0 && (in == nullptr || qp == nullptr))) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(sse) & 7u) != 0) return TX16_EINVAL;
   // interior of whole blocks (width and height rounded down to 16) per image,

@@ -174,6 +174,7 @@ int64_t tx16_image_blocks(const tx16_image* img) {
 }
 
 tx16_status tx16_forward(const tx16_image* imgs, int32_t n, int32_t* coeffs, void* stream) {
+  TX16_TRACE("tx16_forward");
   if (n < 0 || (n > 0 && (imgs == nullptr || coeffs == nullptr))) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(coeffs) & 15u) != 0) return TX16_EINVAL;
   std::vector<ImgParam> P(n);
@@ -189,6 +190,7 @@ tx16_status tx16_forward(const tx16_image* imgs, int32_t n, int32_t* coeffs, voi
 
 tx16_status tx16_quantise(const int32_t* coeffs, int64_t nblk, tx16_qparams qp, int32_t* levels,
                           void* stream) {
+  TX16_TRACE("tx16_quantise");
   if (nblk < 0 || !valid_qp(qp)) return TX16_EINVAL;
   if (nblk == 0) return TX16_OK;
   if (coeffs == nullptr || levels == nullptr) return TX16_EINVAL;
@@ -202,6 +204,7 @@ tx16_status tx16_quantise(const int32_t* coeffs, int64_t nblk, tx16_qparams qp, 
 
 tx16_status tx16_inverse(const int32_t* levels, const tx16_image* out, int32_t n, const tx16_qparams* qp,
                          void* stream) {
+  TX16_TRACE("tx16_inverse");
   if (n < 0 || (n > 0 && (levels == nullptr || out == nullptr || qp == nullptr))) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(levels) & 15u) != 0) return TX16_EINVAL;
   std::vector<ImgParam> P(n);
@@ -222,6 +225,7 @@ tx16_status tx16_inverse(const int32_t* levels, const tx16_image* out, int32_t n
 
 tx16_status tx16_codec_batch(const tx16_image* in, const tx16_image* out, int32_t n, const tx16_qparams* qp,
                              uint64_t* sse, int32_t* levels, void* stream) {
+  TX16_TRACE("tx16_codec_batch");
   if (n < 0 || (n > 0 && (in == nullptr || qp == nullptr))) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(levels) & 15u) != 0 || (reinterpret_cast<uintptr_t>(sse) & 7u) != 0)
     return TX16_EINVAL;
@@ -251,6 +255,7 @@ tx16_status tx16_codec_batch(const tx16_image* in, const tx16_image* out, int32_
 }
 
 tx16_status tx16_sse(const tx16_image* a, const tx16_image* b, int32_t n, uint64_t* sse, void* stream) {
+  TX16_TRACE("tx16_sse");
   if (n < 0 || (n > 0 && (a == nullptr || b == nullptr || sse == nullptr))) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(sse) & 7u) != 0) return TX16_EINVAL;
   std::vector<ImgParam> P(n);

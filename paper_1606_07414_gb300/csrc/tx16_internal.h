@@ -3,11 +3,25 @@
 
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 
 #include "tx16.h"
 
 namespace tx16 {
+
+// An NVTX range over one C-ABI call or serving stage, named after it, so that
+// profiler timelines (nsys, ncu --nvtx) group kernels by the call that issued
+// them.  NVTX v3 is header-only: without an attached tool a push or pop is a
+// call through an empty slot.
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
+#define TX16_TRACE(name) ::tx16::Trace tx16_trace_range_(name)
 
 constexpr int kTileBlocks = 16;            // 16x16 blocks per CTA iteration
 constexpr int kThreads = 16 * kTileBlocks;  // one thread per block row

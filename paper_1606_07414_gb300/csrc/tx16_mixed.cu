@@ -308,6 +308,7 @@ using namespace tx16;
 extern "C" tx16_status tx16_codec_mixed(const tx16_image* in, const tx16_image* out, int32_t n,
                                         const tx16_mixed_qparams* qp, uint8_t* split, uint64_t* sse,
                                         void* stream) {
+  TX16_TRACE("tx16_codec_mixed");
   if (n < 0 || (n > 0 && (in == nullptr || qp == nullptr))) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(sse) & 7u) != 0) return TX16_EINVAL;
   std::vector<MixedParam> M(n);

@@ -107,6 +107,7 @@ extern "C" {
 
 tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_t n, const tx16_qparams* qp,
                              tx16_plan** plan) {
+  TX16_TRACE("tx16_plan_create");
   if (plan == nullptr) return TX16_EINVAL;
   *plan = nullptr;
   if (n <= 0 || in == nullptr || qp == nullptr) return TX16_EINVAL;
@@ -172,6 +173,7 @@ tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_
 }
 
 tx16_status tx16_plan_run(tx16_plan* plan, uint64_t* sse, int32_t* levels, void* stream) {
+  TX16_TRACE("tx16_plan_run");
   if (plan == nullptr) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(sse) & 7u) != 0 || (reinterpret_cast<uintptr_t>(levels) & 15u) != 0)
     return TX16_EINVAL;
@@ -179,6 +181,7 @@ tx16_status tx16_plan_run(tx16_plan* plan, uint64_t* sse, int32_t* levels, void*
 }
 
 tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels, void* stream) {
+  TX16_TRACE("tx16_plan_run_graph");
   if (plan == nullptr) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(sse) & 7u) != 0 || (reinterpret_cast<uintptr_t>(levels) & 15u) != 0)
     return TX16_EINVAL;
@@ -217,6 +220,7 @@ tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels,
 }
 
 tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* stream) {
+  TX16_TRACE("tx16_plan_autotune");
   if (plan == nullptr) return TX16_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaDeviceProp prop;

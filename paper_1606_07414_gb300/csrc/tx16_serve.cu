@@ -235,6 +235,7 @@ void CUDART_CB slot_done(void* arg) {
 
 // Put one admitted group on a slot: copies in, one batched launch, copies out.
 tx16_status launch_group(tx16_server* s, Slot& slot) {
+  TX16_TRACE("tx16 serve: launch group");
   const int n = int(slot.reqs.size());
   std::vector<tx16_image> in(n), out(n);
   std::vector<tx16_qparams> qp(n);
@@ -264,6 +265,7 @@ tx16_status launch_group(tx16_server* s, Slot& slot) {
 }
 
 void retire(tx16_server* s, Slot& slot, tx16_status st) {
+  TX16_TRACE("tx16 serve: retire group");
   const Clock::time_point t = Clock::now();
   for (size_t i = 0; i < slot.reqs.size(); ++i) {
     Request* r = slot.reqs[i];
@@ -407,6 +409,7 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
 
 tx16_status tx16_serve_submit(tx16_server* s, const void* host_pixels, int32_t w, int32_t h, int32_t bits,
                               tx16_qparams qp, void* host_recon, uint64_t* ticket) {
+  TX16_TRACE("tx16_serve_submit");
   if (s == nullptr || host_pixels == nullptr || ticket == nullptr) return TX16_EINVAL;
   tx16_image probe{const_cast<void*>(host_pixels), w, h, int64_t(w) * (bits == 8 ? 1 : 2), bits};
   if ((reinterpret_cast<uintptr_t>(host_pixels) & 15u) != 0) probe.data = reinterpret_cast<void*>(16);
@@ -448,6 +451,7 @@ tx16_status tx16_serve_submit(tx16_server* s, const void* host_pixels, int32_t w
 }
 
 tx16_status tx16_serve_wait(tx16_server* s, uint64_t ticket, int32_t timeout_ms, double* psnr, double* latency_us) {
+  TX16_TRACE("tx16_serve_wait");
   if (s == nullptr) return TX16_EINVAL;
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->live.find(ticket);

@@ -329,6 +329,7 @@ using namespace tx16;
 
 extern "C" tx16_status tx16_ssim(const tx16_image* a, const tx16_image* b, int32_t n, double* mssim, float* map,
                                  void* stream) {
+  TX16_TRACE("tx16_ssim");
   if (n < 0 || (n > 0 && (a == nullptr || b == nullptr || mssim == nullptr))) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(mssim) & 7u) != 0 || (reinterpret_cast<uintptr_t>(map) & 3u) != 0)
     return TX16_EINVAL;

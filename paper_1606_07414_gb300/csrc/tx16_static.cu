@@ -63,6 +63,7 @@ tx16_status static_address(StaticWorkList** out) {
 extern "C" tx16_status tx16_codec_batch_static(const tx16_image* in, const tx16_image* out, int32_t n,
                                                const tx16_qparams* qp, uint64_t* sse, int32_t* levels,
                                                void* stream) {
+  TX16_TRACE("tx16_codec_batch_static");
   if (n < 0 || n > kStaticMaxImages) return TX16_EINVAL;  // beyond the fixed array
   if (n > 0 && (in == nullptr || qp == nullptr)) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(levels) & 15u) != 0 || (reinterpret_cast<uintptr_t>(sse) & 7u) != 0)

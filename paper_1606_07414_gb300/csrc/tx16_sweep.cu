@@ -214,6 +214,7 @@ using namespace tx16;
 
 extern "C" tx16_status tx16_zonal_sweep(const tx16_image* imgs, int32_t n, const int32_t* r_list, int32_t nr,
                                         uint64_t* sse, void* stream) {
+  TX16_TRACE("tx16_zonal_sweep");
   if (n < 0 || nr < 1 || nr > kSweepMaxR || r_list == nullptr) return TX16_EINVAL;
   if (n > 0 && (imgs == nullptr || sse == nullptr)) return TX16_EINVAL;
   if ((reinterpret_cast<uintptr_t>(sse) & 7u) != 0) return TX16_EINVAL;
