@@ -233,7 +233,7 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
     h_out = torch.empty_like(h_in).pin_memory()
     h_sse = torch.empty(FRAMES, dtype=torch.int64).pin_memory()
     qp = qparams(args.q, args.r)
-    chunk = 32
+    chunk = args.e2e_chunk
     copy_in = torch.cuda.Stream()
     copy_out = torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(FRAMES // chunk)]
@@ -880,6 +880,8 @@ def main():
     ap.add_argument("--serve-rates", default="1000,5000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--quick", action="store_true", help="headline number only")
+    ap.add_argument("--e2e-chunk", type=int, default=16,
+                    help="frames per chunk of the host-buffer pipeline (a divisor of the frame count)")
     ap.add_argument("--frames", type=int, default=FRAMES, help="smaller cases for profiling")
     ap.add_argument("--ssim-only", action="store_true",
                     help="time tx16_ssim alone on --frames frames and their reconstruction (profiling)")
