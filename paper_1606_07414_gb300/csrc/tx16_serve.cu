@@ -234,7 +234,7 @@ void CUDART_CB slot_done(void* arg) {
 }
 
 // Put one admitted group on a slot: copies in, one batched launch, copies out.
-tx16_status launch_group(tx16_server* s, Slot& slot) {
+tx16_status launch_group(Slot& slot) {
   TX16_TRACE("tx16 serve: launch group");
   const int n = int(slot.reqs.size());
   std::vector<tx16_image> in(n), out(n);
@@ -334,7 +334,7 @@ void worker_main(tx16_server* s) {
       slot.busy = true;
       // issue copies and the launch without holding the lock (submit stays cheap)
       lk.unlock();
-      const tx16_status st = launch_group(s, slot);
+      const tx16_status st = launch_group(slot);
       if (st != TX16_OK) cudaStreamSynchronize(slot.stream);
       lk.lock();
       if (st != TX16_OK) {

@@ -6,7 +6,6 @@ broken copies of it and show that every plausible mistake fails one of them.
 """
 import math
 import os
-import types
 
 import numpy as np
 import pytest
