@@ -274,6 +274,37 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
                   "ms_per_step": round(e2e_ms, 4), "pipeline": f"{FRAMES // chunk} chunks of {chunk} frames, "
                                                                "copy streams overlapping the kernel"}
 
+    # -- the small case: one 512 x 512 8-bit image (1024 blocks), zonal r = 16,
+    #    no quantiser; launch-latency bound, so reported in microseconds
+    from paper_1606_07414_gb300 import synth
+
+    img1 = torch.from_numpy(synth.ar1_image(1, 512, 512, 0.95)).cuda()
+    rec1 = torch.empty_like(img1)
+    sse1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    in1 = (tx16.tx16_image * 1)(tx16.image(img1))
+    out1 = (tx16.tx16_image * 1)(tx16.image(rec1))
+    qp1 = qparams(0.0, 16)
+
+    def small():
+        st = lib.tx16_codec_batch(in1, out1, 1, qp1, ctypes.c_void_p(sse1.data_ptr()), None, sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_codec_batch")
+
+    for _ in range(20):
+        small()
+    small_gpu_ms = _events_time(small, 500, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(200):
+        small()
+        torch.cuda.synchronize()
+    small_sync_us = (time.perf_counter() - t0) * 1e6 / 200
+    out["small_image"] = {
+        "workload": "one 512x512 uint8 AR(1) image (rho 0.95, seed 1), 1024 blocks, zonal r = 16, no quantiser",
+        "us_per_call_gpu": round(small_gpu_ms * 1e3, 2),
+        "us_per_call_synchronous": round(small_sync_us, 2),
+        "psnr_db": round(tx16.tx16_psnr([int(sse1.item())], [in1[0]])[0], 4)}
+
     # -- end to end with the kernel reading and writing the pinned host planes
     #    directly (mapped memory over the CPU-GPU link: no staging copies)
     hin = (tx16.tx16_image * FRAMES)(*[tx16.tx16_image(h_in[i].data_ptr(), W, H, W, 8) for i in range(FRAMES)])
