@@ -12,6 +12,8 @@ oracle computes block by block, plus properties checked on every output.
     first and last block of every image against the direct int64 product,
     bit-exact.  The forward path is data-independent arithmetic, so uniform
     random samples stand in for the AR(1) fields here.
+  * 2000 uneven images through one plan, and the serving mix's request shapes
+    through the server (below).
 """
 import numpy as np
 import pytest
@@ -92,3 +94,89 @@ def test_forward_full_size(tx):
     got = coeffs.view(n * nb, 256)[idx].cpu().numpy().reshape(-1, 16, 16)
     X = np.stack([_blocks(imgs[b // nb], [b % nb], nbx)[0] for b in g])
     assert np.array_equal(got, O.forward_direct(X.astype(np.int64)))
+
+
+def test_uneven_batch_full_size(tx):
+    """2000 images with sides drawn independently from the multiples of 16 in
+    [64, 4096] (3.3e7 blocks), zonal r in {8, 32, 128}, q = 16, as crops of
+    two 4096 x 4096 AR(1) fields: one plan, replayed as a CUDA graph.  Every
+    image's squared error equals the separate unfused SSE kernel's over the
+    same reconstruction; 3000 sampled blocks match the oracle bit for bit."""
+    import torch
+
+    n, side = 2000, 4096
+    Hs, Ws = synth.uneven_sizes(2016 + 9, n)
+    rs = synth.choice(2016 + 10, n, [8, 32, 128])
+    u = synth.uniforms(2016 + 11, 2 * n)
+    fields = [torch.from_numpy(synth.ar1_image(2016 + 700 + i, side, side, rho)).cuda()
+              for i, rho in enumerate((0.9, 0.97))]
+    ins, outs, qps = [], [], []
+    for i in range(n):
+        H, W = int(Hs[i]), int(Ws[i])
+        y = min(int(u[2 * i] * (side - H + 1)), side - H)
+        x = 16 * min(int(u[2 * i + 1] * ((side - W) // 16 + 1)), (side - W) // 16)
+        ins.append(fields[i % 2][y:y + H, x:x + W])
+        outs.append(torch.empty((H, W), dtype=torch.uint8, device="cuda"))
+        qps.append((16.0, int(rs[i])))
+    plan = tx.Plan(ins, outs, qps)
+    sse = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    plan.run_graph(sse=sse)
+    sse2 = torch.zeros(n, dtype=torch.int64, device="cuda")
+    tx.tx16_sse(ins, outs, sse2)
+    torch.cuda.synchronize()
+    assert torch.equal(sse, sse2)
+    rng = np.random.default_rng(2000)
+    by_r = {}
+    for i in rng.integers(0, n, 3000).tolist():
+        nbx = int(Ws[i]) // 16
+        b = int(rng.integers(0, (int(Hs[i]) // 16) * nbx))
+        y, x = (b // nbx) * 16, (b % nbx) * 16
+        X = ins[i][y:y + 16, x:x + 16].cpu().numpy()
+        R = outs[i][y:y + 16, x:x + 16].cpu().numpy()
+        by_r.setdefault(int(rs[i]), []).append((X, R))
+    for r, pairs in by_r.items():
+        X = np.stack([p[0] for p in pairs]).astype(np.int64)
+        got = np.stack([p[1] for p in pairs])
+        assert np.array_equal(got, oracle_blocks(X, 16.0, r, 8)["recon"]), r
+    plan.close()
+
+
+def test_serving_request_shapes_full_size(tx):
+    """The serving mix's request shapes at full size (256 x 256 and
+    1920 x 1088 uint8, 3840 x 2160 10-bit in uint16), each with its own q and
+    r, submitted together so that they are admitted and coded in groups:
+    every result equals a direct tx16_codec_batch call on the same image, bit
+    for bit, with the same PSNR, and sampled blocks match the oracle."""
+    import torch
+
+    kinds = synth.choice(5, 30, [0, 0, 0, 0, 0, 0, 1, 1, 1, 2])
+    qs = synth.choice(6, 30, [8.0, 16.0, 32.0])
+    rs = synth.choice(7, 30, [4, 16, 64, 256])
+    reqs = []
+    for i in range(30):
+        if kinds[i] == 0:
+            img, bits = synth.ar1_image(300 + i, 256, 256, 0.95), 8
+        elif kinds[i] == 1:
+            img, bits = synth.ar1_image(300 + i, 1088, 1920, 0.95), 8
+        else:
+            img, bits = synth.ar1_image(300 + i, 2160, 3840, 0.95, bits=10), 10
+        reqs.append((img, bits, float(qs[i]), int(rs[i])))
+    srv = tx.Server({"device_pool_mb": 2048, "streams": 3, "max_batch": 64})
+    outs = [np.zeros_like(img) for img, _, _, _ in reqs]
+    tickets = [srv.submit(img, q, r, out=o, bits=bits) for (img, bits, q, r), o in zip(reqs, outs)]
+    psnrs = [srv.wait(t)[0] for t in tickets]
+    srv.close()
+    rng = np.random.default_rng(30)
+    for (img, bits, q, r), o, p in zip(reqs, outs, psnrs):
+        d = torch.from_numpy(img.view(np.int16) if bits > 8 else img).cuda()
+        rec = torch.empty_like(d)
+        s = torch.zeros(1, dtype=torch.int64, device="cuda")
+        tx.tx16_codec_batch([tx.image(d, bits)], [tx.image(rec, bits)], [(q, r)], sse=s)
+        torch.cuda.synchronize()
+        assert np.array_equal(o, rec.cpu().numpy().view(img.dtype))
+        assert p == tx.tx16_psnr([int(s.item())], [tx.image(d, bits)])[0]
+        H, W = img.shape
+        nbx = W // 16
+        picks = rng.integers(0, (H // 16) * nbx, 40)
+        X = _blocks(img, picks, nbx).astype(np.int64)
+        assert np.array_equal(_blocks(o, picks, nbx), oracle_blocks(X, q, r, bits)["recon"])
