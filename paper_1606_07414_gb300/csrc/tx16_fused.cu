@@ -413,8 +413,15 @@ template <int MAXI>
 tx16_status launch_fused_modes(int zone, const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                                cudaStream_t stream) {
   const bool dst = imgs[0].dst != nullptr;
-  // up to 8 kept columns and no level output: one block per thread in registers
-  if (fused_bt_supports(zone, levels != nullptr)) return launch_fused_bt(zone, dst, imgs, n, sse, stream);
+  // up to 8 kept columns and no level output: one block per thread in
+  // registers -- unless the batch has fewer 32-block warp tiles than the GPU
+  // has SMs: then each warp would code a single tile, a whole block per
+  // thread in series, and the pair kernel (16 blocks over 128 threads) ends
+  // sooner
+  int64_t blocks = 0;
+  for (int i = 0; i < n; ++i) blocks += imgs[i].nblk;
+  const bool small = (blocks + 31) / 32 < int64_t(device_sm_count());
+  if (!small && fused_bt_supports(zone, levels != nullptr)) return launch_fused_bt(zone, dst, imgs, n, sse, stream);
   if (levels != nullptr)
     return dst ? launch_fused_zone<MAXI, true, true>(zone, imgs, n, sse, levels, stream)
                : launch_fused_zone<MAXI, true, false>(zone, imgs, n, sse, levels, stream);

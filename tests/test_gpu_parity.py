@@ -432,3 +432,26 @@ def test_codec_16bit_extreme_planes_clamp(tx, bits, q, r):
         rec = from_dev(outs[i], bits)
         assert np.array_equal(O.image_to_blocks(rec.astype(np.int64)), ref["recon"]), i
         assert int(sse[i].item()) == O.sse(im, rec), i
+
+
+@pytest.mark.parametrize("q,r", [(16.0, 16), (None, 8), (12.0, 32)])
+def test_codec_without_levels_ragged_many_images(tx, q, r):
+    """64 images of 80 x 272 (85 blocks each: two full 32-block warp tiles and
+    a ragged third), 5440 blocks in all: enough warp tiles for the
+    one-block-per-thread kernel, whose warps then cross image boundaries and
+    code ragged tails.  Every image bit-exact against the oracle."""
+    import torch
+
+    n, H, W = 64, 80, 272
+    imgs = [synth.ar1_image(5000 + i + r, H, W, 0.8 + 0.003 * i, 8) for i in range(n)]
+    keep = [to_dev(im) for im in imgs]
+    outs = [empty_like_img(H, W, 8, pad=16) for _ in range(n)]
+    sse = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_batch([tx.image(d) for d in keep], [tx.image(o) for o in outs], [(q, r)] * n, sse=sse)
+    torch.cuda.synchronize()
+    X = np.concatenate([O.image_to_blocks(im.astype(np.int64)) for im in imgs])
+    ref = oracle_blocks(X, q, r, 8)["recon"]
+    got = np.concatenate([O.image_to_blocks(from_dev(o, 8).astype(np.int64)) for o in outs])
+    assert np.array_equal(got, ref)
+    for i in range(n):
+        assert int(sse[i].item()) == O.sse(imgs[i], from_dev(outs[i], 8)), i
