@@ -31,16 +31,33 @@ ZERO = None
 class Net:
     """Symbolic DAG builder.  A value is ZERO or (node_id, sign)."""
 
-    def __init__(self):
+    def __init__(self, cse=False):
         self.nodes = []  # (kind, a_id, b_id) kind in add/sub ; leaves: ("in", name)
+        # cse: identical operations share one node; a - b and b - a share one
+        # node with opposite signs (binary32 round-to-nearest is symmetric
+        # under negation, so this changes no rounded value)
+        self.cse = cse
+        self.memo = {}
 
     def leaf(self, name):
         self.nodes.append(("in", name))
         return (len(self.nodes) - 1, 1)
 
     def _new(self, kind, a, b):
+        if self.cse:
+            key = (kind, min(a, b), max(a, b)) if kind == "add" else (kind, a, b)
+            if key in self.memo:
+                return self.memo[key]
         self.nodes.append((kind, a, b))
+        if self.cse:
+            self.memo[key] = len(self.nodes) - 1
         return len(self.nodes) - 1
+
+    def _sub(self, a, b):
+        """Node and sign of a - b."""
+        if self.cse and a > b:
+            return (self._new("sub", b, a), -1)
+        return (self._new("sub", a, b), 1)
 
     def add(self, x, y):
         if x is ZERO:
@@ -51,9 +68,9 @@ class Net:
         if sa == 1 and sb == 1:
             return (self._new("add", a, b), 1)
         if sa == 1 and sb == -1:
-            return (self._new("sub", a, b), 1)
+            return self._sub(a, b)
         if sa == -1 and sb == 1:
-            return (self._new("sub", b, a), 1)
+            return self._sub(b, a)
         return (self._new("add", a, b), -1)
 
     def neg(self, x):
@@ -187,6 +204,178 @@ def matrix_from_network(inverse=False):
     return M
 
 
+def node_values(net, inputs_value):
+    """Exact value of every node for the given leaf values."""
+    val = {}
+    for k, nd in enumerate(net.nodes):
+        if nd[0] == "in":
+            val[k] = inputs_value[nd[1]]
+        elif nd[0] == "add":
+            val[k] = val[nd[1]] + val[nd[2]]
+        else:
+            val[k] = val[nd[1]] - val[nd[2]]
+    return val
+
+
+def emit_nodes(net, outputs, in_names):
+    """Packed statements for the nodes the outputs need.  Returns (lines, outs,
+    adds) with outs[k] = (variable, sign) of output k, or None if it is zero."""
+    live = set()
+    stack = [o[0] for o in outputs if o is not ZERO]
+    while stack:
+        k = stack.pop()
+        if k in live:
+            continue
+        live.add(k)
+        if net.nodes[k][0] != "in":
+            stack += [net.nodes[k][1], net.nodes[k][2]]
+    names = {}
+    lines = []
+    for k in sorted(live):
+        kind = net.nodes[k][0]
+        if kind == "in":
+            names[k] = in_names[net.nodes[k][1]]
+            continue
+        a, b = names[net.nodes[k][1]], names[net.nodes[k][2]]
+        op = "__fadd2_rn" if kind == "add" else "sub2"
+        lines.append(f"const float2 t{k} = {op}({a}, {b});")
+        names[k] = f"t{k}"
+    outs = [None if o is ZERO else (names[o[0]], o[1]) for o in outputs]
+    adds = sum(1 for k in live if net.nodes[k][0] != "in")
+    return lines, outs, adds
+
+
+def _lane(term, h):
+    """Scalar lane h of a signed packed value (variable, sign)."""
+    name, s = term
+    return ("-" if s < 0 else "") + f"{name}.{'xy'[h]}"
+
+
+class ScalarSums:
+    """Scalar additions of lanes, each distinct expression emitted once."""
+
+    def __init__(self, prefix):
+        self.prefix = prefix
+        self.memo = {}
+        self.lines = []
+
+    def add(self, p, q, h):
+        # p + q (each a signed term or None) on lane h; returns an expression
+        if p is None and q is None:
+            return "0.f"
+        if p is None or q is None:
+            return _lane(p if q is None else q, h)
+        a, b = sorted((_lane(p, h), _lane(q, h)))
+        key = (a, b)
+        if key not in self.memo:
+            nm = f"{self.prefix}{len(self.memo)}"
+            self.lines.append(f"const float {nm} = __fadd_rn({a}, {b});")
+            self.memo[key] = nm
+        return self.memo[key]
+
+
+def emit_transposing(w, T, rnd):
+    """Networks of the one-block-per-thread codec, which pairs rows (i, 15 - i)
+    in the two lanes of a float2 so that the first butterfly of the column
+    pass (rows i and 15 - i) and the last one of the inverse column pass
+    become scalar additions across the lanes, writing their results straight
+    into the pairing the next pass uses (no register moves).  Samples enter as
+    2^23 + 256 x: every node is then a multiple of 256 below 2^32 in
+    magnitude, exact in binary32 with no bias correction in M1."""
+    # forward row pass on rows (i, 15 - i), then the column M1 across them
+    for V in sorted({v for _, v in ZONES}):
+        net = Net(cse=True)
+        x = [net.leaf(i) for i in range(16)]
+        y = net.forward(x)[:V]
+        lines, outs, adds = emit_nodes(net, y, [f"X[{i}]" for i in range(16)])
+        assert all(o is not None for o in outs)
+        for _ in range(20):
+            xs = [rnd.randint(0, 255) for _ in range(16)]
+            check(net, y, xs, [sum(T[k][m] * xs[m] for m in range(16)) for k in range(V)])
+        w(f"// forward row pass on two rows (lanes: row i, row 15 - i), outputs v < {V}, then the")
+        w(f"// first column butterfly across the lanes: S[c] = (a_i[2c], a_i[2c+1]) with")
+        w(f"// a_i = row i + row 15 - i, D[c] the same for a_(15-i) = row i - row 15 - i (true")
+        w(f"// signs); {adds} pair additions and {2 * V} scalar additions")
+        w(f"struct FwdRowT{V} {{")
+        w(f"  __device__ static __forceinline__ void run(const float2 (&X)[16], float2 (&S)[{V // 2}], "
+          f"float2 (&D)[{V // 2}]) {{")
+        for ln in lines:
+            w("    " + ln)
+        for c in range(V // 2):
+            for arr, dsign in (("S", 1), ("D", -1)):
+                comps = []
+                for h in (0, 1):
+                    nm, s = outs[2 * c + h]
+                    comps.append(f"__fadd_rn({_lane((nm, s), 0)}, {_lane((nm, s * dsign), 1)})")
+                w(f"    {arr}[{c}] = make_float2({comps[0]}, {comps[1]});")
+        w("  }")
+        w("};")
+        w("")
+    # forward column pass from the M1 outputs a[0..15]
+    for U in sorted({u for u, _ in ZONES}):
+        net = Net(cse=True)
+        a = [net.leaf(i) for i in range(16)]
+        b = [a[g] for g in G1]
+        e = net.m4(net.m3(net.m2(b)))
+        y = [e[g] for g in G2][:U]
+        lines, outs, adds = emit_nodes(net, y, [f"a[{i}]" for i in range(16)])
+        assert all(o is not None for o in outs)
+        for _ in range(20):
+            xs = [rnd.randint(-4096, 4096) for _ in range(16)]
+            av = [xs[i] + xs[15 - i] for i in range(8)] + [xs[7 - i] - xs[8 + i] for i in range(8)]
+            check(net, y, av, [sum(T[k][m] * xs[m] for m in range(16)) for k in range(U)])
+        signs = [o[1] for o in outs] + [0] * (16 - U)
+        w(f"// forward column pass after M1 (inputs a = M1 x), outputs u < {U}:")
+        w(f"// n[u] = sign[u] * (T x)[u]; {adds} pair additions")
+        w(f"struct FwdColM{U} {{")
+        w(sign_fn(signs))
+        w(f"  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[{U}]) {{")
+        for ln in lines:
+            w("    " + ln)
+        for u in range(U):
+            w(f"    n[{u}] = {outs[u][0]};")
+        w("  }")
+        w("};")
+        w("")
+    # inverse column pass with its last butterfly (M1) scalar, into row pairs
+    for U in sorted({u for u, _ in ZONES}):
+        net = Net(cse=True)
+        ins = [net.leaf(i) if i < U else ZERO for i in range(16)]
+        e = [None] * 16
+        for i in range(16):
+            e[G2[i]] = ins[i]
+        c = net.m2(net.m3(net.m4(e)))
+        pre = [None] * 16
+        for i in range(16):
+            pre[G1[i]] = c[i]
+        lines, outs, adds = emit_nodes(net, pre, [f"w[{i}]" for i in range(16)])
+        ss = ScalarSums("s")
+        body = []
+        for i in range(8):
+            p, q = outs[i], outs[15 - i]
+            qn = None if q is None else (q[0], -q[1])
+            for h in (0, 1):
+                zi = ss.add(p, q, h)
+                zj = ss.add(p, qn, h)
+                body.append(f"Z[{i}][{h}] = make_float2({zi}, {zj});")
+        for _ in range(20):
+            ws = [rnd.randint(-5000, 5000) if i < U else 0 for i in range(16)]
+            val = node_values(net, ws)
+            pv = [0 if o is ZERO else o[1] * val[o[0]] for o in pre]
+            z = [pv[i] + pv[15 - i] for i in range(8)] + [pv[7 - i] - pv[8 + i] for i in range(8)]
+            assert z == [sum(T[m][k] * ws[m] for m in range(16)) for k in range(16)]
+        w(f"// inverse column pass, inputs u < {U} (true values; lanes: columns 2c, 2c+1), with its")
+        w(f"// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;")
+        w(f"// {adds} pair additions and {len(ss.memo)} scalar additions")
+        w(f"struct InvColT{U} {{")
+        w(f"  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {{")
+        for ln in lines + ss.lines + body:
+            w("    " + ln)
+        w("  }")
+        w("};")
+        w("")
+
+
 ZONES = [(3, 4), (5, 6), (7, 8), (11, 10), (16, 16)]  # (rows U, columns V) kept
 
 
@@ -318,6 +507,7 @@ def main():
         w("  }")
         w("};")
         w("")
+    emit_transposing(w, T, rnd)
     w(f"// sign of each output of the (unpruned) forward network: row-pass outputs")
     w(f"// are stored unsigned; the column thread folds this sign into its scale.")
     w(f"constexpr unsigned kFwdNegMask = 0x{sum(1 << i for i, x in enumerate(fwd_sign) if x < 0):04x}u;")

@@ -1134,6 +1134,775 @@ struct InvRow16 {
   }
 };
 
+// forward row pass on two rows (lanes: row i, row 15 - i), outputs v < 4, then the
+// first column butterfly across the lanes: S[c] = (a_i[2c], a_i[2c+1]) with
+// a_i = row i + row 15 - i, D[c] the same for a_(15-i) = row i - row 15 - i (true
+// signs); 32 pair additions and 8 scalar additions
+struct FwdRowT4 {
+  __device__ static __forceinline__ void run(const float2 (&X)[16], float2 (&S)[2], float2 (&D)[2]) {
+    const float2 t16 = __fadd2_rn(X[0], X[15]);
+    const float2 t17 = sub2(X[7], X[8]);
+    const float2 t18 = __fadd2_rn(X[1], X[14]);
+    const float2 t19 = sub2(X[6], X[9]);
+    const float2 t20 = __fadd2_rn(X[2], X[13]);
+    const float2 t21 = sub2(X[5], X[10]);
+    const float2 t22 = __fadd2_rn(X[3], X[12]);
+    const float2 t23 = sub2(X[4], X[11]);
+    const float2 t24 = __fadd2_rn(X[4], X[11]);
+    const float2 t25 = sub2(X[3], X[12]);
+    const float2 t26 = __fadd2_rn(X[5], X[10]);
+    const float2 t27 = sub2(X[2], X[13]);
+    const float2 t28 = __fadd2_rn(X[6], X[9]);
+    const float2 t29 = sub2(X[1], X[14]);
+    const float2 t30 = __fadd2_rn(X[7], X[8]);
+    const float2 t31 = sub2(X[0], X[15]);
+    const float2 t32 = __fadd2_rn(t16, t30);
+    const float2 t34 = __fadd2_rn(t18, t28);
+    const float2 t36 = __fadd2_rn(t20, t26);
+    const float2 t38 = __fadd2_rn(t22, t24);
+    const float2 t39 = sub2(t16, t30);
+    const float2 t40 = __fadd2_rn(t17, t19);
+    const float2 t42 = __fadd2_rn(t23, t21);
+    const float2 t44 = __fadd2_rn(t25, t27);
+    const float2 t46 = __fadd2_rn(t31, t29);
+    const float2 t48 = __fadd2_rn(t32, t38);
+    const float2 t49 = __fadd2_rn(t34, t36);
+    const float2 t52 = __fadd2_rn(t40, t46);
+    const float2 t53 = __fadd2_rn(t42, t44);
+    const float2 t55 = sub2(t40, t46);
+    const float2 t56 = __fadd2_rn(t48, t49);
+    const float2 t58 = __fadd2_rn(t52, t53);
+    S[0] = make_float2(__fadd_rn(t56.x, t56.y), __fadd_rn(t58.x, t58.y));
+    D[0] = make_float2(__fadd_rn(t56.x, -t56.y), __fadd_rn(t58.x, -t58.y));
+    S[1] = make_float2(__fadd_rn(t39.x, t39.y), __fadd_rn(-t55.x, -t55.y));
+    D[1] = make_float2(__fadd_rn(t39.x, -t39.y), __fadd_rn(-t55.x, t55.y));
+  }
+};
+
+// forward row pass on two rows (lanes: row i, row 15 - i), outputs v < 6, then the
+// first column butterfly across the lanes: S[c] = (a_i[2c], a_i[2c+1]) with
+// a_i = row i + row 15 - i, D[c] the same for a_(15-i) = row i - row 15 - i (true
+// signs); 34 pair additions and 12 scalar additions
+struct FwdRowT6 {
+  __device__ static __forceinline__ void run(const float2 (&X)[16], float2 (&S)[3], float2 (&D)[3]) {
+    const float2 t16 = __fadd2_rn(X[0], X[15]);
+    const float2 t17 = sub2(X[7], X[8]);
+    const float2 t18 = __fadd2_rn(X[1], X[14]);
+    const float2 t19 = sub2(X[6], X[9]);
+    const float2 t20 = __fadd2_rn(X[2], X[13]);
+    const float2 t21 = sub2(X[5], X[10]);
+    const float2 t22 = __fadd2_rn(X[3], X[12]);
+    const float2 t23 = sub2(X[4], X[11]);
+    const float2 t24 = __fadd2_rn(X[4], X[11]);
+    const float2 t25 = sub2(X[3], X[12]);
+    const float2 t26 = __fadd2_rn(X[5], X[10]);
+    const float2 t27 = sub2(X[2], X[13]);
+    const float2 t28 = __fadd2_rn(X[6], X[9]);
+    const float2 t29 = sub2(X[1], X[14]);
+    const float2 t30 = __fadd2_rn(X[7], X[8]);
+    const float2 t31 = sub2(X[0], X[15]);
+    const float2 t32 = __fadd2_rn(t16, t30);
+    const float2 t34 = __fadd2_rn(t18, t28);
+    const float2 t36 = __fadd2_rn(t20, t26);
+    const float2 t38 = __fadd2_rn(t22, t24);
+    const float2 t39 = sub2(t16, t30);
+    const float2 t40 = __fadd2_rn(t17, t19);
+    const float2 t42 = __fadd2_rn(t23, t21);
+    const float2 t44 = __fadd2_rn(t25, t27);
+    const float2 t46 = __fadd2_rn(t31, t29);
+    const float2 t48 = __fadd2_rn(t32, t38);
+    const float2 t49 = __fadd2_rn(t34, t36);
+    const float2 t51 = sub2(t32, t38);
+    const float2 t52 = __fadd2_rn(t40, t46);
+    const float2 t53 = __fadd2_rn(t42, t44);
+    const float2 t55 = sub2(t40, t46);
+    const float2 t56 = __fadd2_rn(t48, t49);
+    const float2 t58 = __fadd2_rn(t52, t53);
+    const float2 t59 = sub2(t52, t53);
+    S[0] = make_float2(__fadd_rn(t56.x, t56.y), __fadd_rn(t58.x, t58.y));
+    D[0] = make_float2(__fadd_rn(t56.x, -t56.y), __fadd_rn(t58.x, -t58.y));
+    S[1] = make_float2(__fadd_rn(t39.x, t39.y), __fadd_rn(-t55.x, -t55.y));
+    D[1] = make_float2(__fadd_rn(t39.x, -t39.y), __fadd_rn(-t55.x, t55.y));
+    S[2] = make_float2(__fadd_rn(t51.x, t51.y), __fadd_rn(t59.x, t59.y));
+    D[2] = make_float2(__fadd_rn(t51.x, -t51.y), __fadd_rn(t59.x, -t59.y));
+  }
+};
+
+// forward row pass on two rows (lanes: row i, row 15 - i), outputs v < 8, then the
+// first column butterfly across the lanes: S[c] = (a_i[2c], a_i[2c+1]) with
+// a_i = row i + row 15 - i, D[c] the same for a_(15-i) = row i - row 15 - i (true
+// signs); 36 pair additions and 16 scalar additions
+struct FwdRowT8 {
+  __device__ static __forceinline__ void run(const float2 (&X)[16], float2 (&S)[4], float2 (&D)[4]) {
+    const float2 t16 = __fadd2_rn(X[0], X[15]);
+    const float2 t17 = sub2(X[7], X[8]);
+    const float2 t18 = __fadd2_rn(X[1], X[14]);
+    const float2 t19 = sub2(X[6], X[9]);
+    const float2 t20 = __fadd2_rn(X[2], X[13]);
+    const float2 t21 = sub2(X[5], X[10]);
+    const float2 t22 = __fadd2_rn(X[3], X[12]);
+    const float2 t23 = sub2(X[4], X[11]);
+    const float2 t24 = __fadd2_rn(X[4], X[11]);
+    const float2 t25 = sub2(X[3], X[12]);
+    const float2 t26 = __fadd2_rn(X[5], X[10]);
+    const float2 t27 = sub2(X[2], X[13]);
+    const float2 t28 = __fadd2_rn(X[6], X[9]);
+    const float2 t29 = sub2(X[1], X[14]);
+    const float2 t30 = __fadd2_rn(X[7], X[8]);
+    const float2 t31 = sub2(X[0], X[15]);
+    const float2 t32 = __fadd2_rn(t16, t30);
+    const float2 t34 = __fadd2_rn(t18, t28);
+    const float2 t35 = sub2(t20, t26);
+    const float2 t36 = __fadd2_rn(t20, t26);
+    const float2 t38 = __fadd2_rn(t22, t24);
+    const float2 t39 = sub2(t16, t30);
+    const float2 t40 = __fadd2_rn(t17, t19);
+    const float2 t42 = __fadd2_rn(t23, t21);
+    const float2 t44 = __fadd2_rn(t25, t27);
+    const float2 t46 = __fadd2_rn(t31, t29);
+    const float2 t47 = sub2(t17, t19);
+    const float2 t48 = __fadd2_rn(t32, t38);
+    const float2 t49 = __fadd2_rn(t34, t36);
+    const float2 t51 = sub2(t32, t38);
+    const float2 t52 = __fadd2_rn(t40, t46);
+    const float2 t53 = __fadd2_rn(t42, t44);
+    const float2 t55 = sub2(t40, t46);
+    const float2 t56 = __fadd2_rn(t48, t49);
+    const float2 t58 = __fadd2_rn(t52, t53);
+    const float2 t59 = sub2(t52, t53);
+    S[0] = make_float2(__fadd_rn(t56.x, t56.y), __fadd_rn(t58.x, t58.y));
+    D[0] = make_float2(__fadd_rn(t56.x, -t56.y), __fadd_rn(t58.x, -t58.y));
+    S[1] = make_float2(__fadd_rn(t39.x, t39.y), __fadd_rn(-t55.x, -t55.y));
+    D[1] = make_float2(__fadd_rn(t39.x, -t39.y), __fadd_rn(-t55.x, t55.y));
+    S[2] = make_float2(__fadd_rn(t51.x, t51.y), __fadd_rn(t59.x, t59.y));
+    D[2] = make_float2(__fadd_rn(t51.x, -t51.y), __fadd_rn(t59.x, -t59.y));
+    S[3] = make_float2(__fadd_rn(-t35.x, -t35.y), __fadd_rn(t47.x, t47.y));
+    D[3] = make_float2(__fadd_rn(-t35.x, t35.y), __fadd_rn(t47.x, -t47.y));
+  }
+};
+
+// forward row pass on two rows (lanes: row i, row 15 - i), outputs v < 10, then the
+// first column butterfly across the lanes: S[c] = (a_i[2c], a_i[2c+1]) with
+// a_i = row i + row 15 - i, D[c] the same for a_(15-i) = row i - row 15 - i (true
+// signs); 38 pair additions and 20 scalar additions
+struct FwdRowT10 {
+  __device__ static __forceinline__ void run(const float2 (&X)[16], float2 (&S)[5], float2 (&D)[5]) {
+    const float2 t16 = __fadd2_rn(X[0], X[15]);
+    const float2 t17 = sub2(X[7], X[8]);
+    const float2 t18 = __fadd2_rn(X[1], X[14]);
+    const float2 t19 = sub2(X[6], X[9]);
+    const float2 t20 = __fadd2_rn(X[2], X[13]);
+    const float2 t21 = sub2(X[5], X[10]);
+    const float2 t22 = __fadd2_rn(X[3], X[12]);
+    const float2 t23 = sub2(X[4], X[11]);
+    const float2 t24 = __fadd2_rn(X[4], X[11]);
+    const float2 t25 = sub2(X[3], X[12]);
+    const float2 t26 = __fadd2_rn(X[5], X[10]);
+    const float2 t27 = sub2(X[2], X[13]);
+    const float2 t28 = __fadd2_rn(X[6], X[9]);
+    const float2 t29 = sub2(X[1], X[14]);
+    const float2 t30 = __fadd2_rn(X[7], X[8]);
+    const float2 t31 = sub2(X[0], X[15]);
+    const float2 t32 = __fadd2_rn(t16, t30);
+    const float2 t34 = __fadd2_rn(t18, t28);
+    const float2 t35 = sub2(t20, t26);
+    const float2 t36 = __fadd2_rn(t20, t26);
+    const float2 t38 = __fadd2_rn(t22, t24);
+    const float2 t39 = sub2(t16, t30);
+    const float2 t40 = __fadd2_rn(t17, t19);
+    const float2 t42 = __fadd2_rn(t23, t21);
+    const float2 t43 = sub2(t25, t27);
+    const float2 t44 = __fadd2_rn(t25, t27);
+    const float2 t46 = __fadd2_rn(t31, t29);
+    const float2 t47 = sub2(t17, t19);
+    const float2 t48 = __fadd2_rn(t32, t38);
+    const float2 t49 = __fadd2_rn(t34, t36);
+    const float2 t51 = sub2(t32, t38);
+    const float2 t52 = __fadd2_rn(t40, t46);
+    const float2 t53 = __fadd2_rn(t42, t44);
+    const float2 t55 = sub2(t40, t46);
+    const float2 t56 = __fadd2_rn(t48, t49);
+    const float2 t57 = sub2(t48, t49);
+    const float2 t58 = __fadd2_rn(t52, t53);
+    const float2 t59 = sub2(t52, t53);
+    S[0] = make_float2(__fadd_rn(t56.x, t56.y), __fadd_rn(t58.x, t58.y));
+    D[0] = make_float2(__fadd_rn(t56.x, -t56.y), __fadd_rn(t58.x, -t58.y));
+    S[1] = make_float2(__fadd_rn(t39.x, t39.y), __fadd_rn(-t55.x, -t55.y));
+    D[1] = make_float2(__fadd_rn(t39.x, -t39.y), __fadd_rn(-t55.x, t55.y));
+    S[2] = make_float2(__fadd_rn(t51.x, t51.y), __fadd_rn(t59.x, t59.y));
+    D[2] = make_float2(__fadd_rn(t51.x, -t51.y), __fadd_rn(t59.x, -t59.y));
+    S[3] = make_float2(__fadd_rn(-t35.x, -t35.y), __fadd_rn(t47.x, t47.y));
+    D[3] = make_float2(__fadd_rn(-t35.x, t35.y), __fadd_rn(t47.x, -t47.y));
+    S[4] = make_float2(__fadd_rn(t57.x, t57.y), __fadd_rn(t43.x, t43.y));
+    D[4] = make_float2(__fadd_rn(t57.x, -t57.y), __fadd_rn(t43.x, -t43.y));
+  }
+};
+
+// forward row pass on two rows (lanes: row i, row 15 - i), outputs v < 16, then the
+// first column butterfly across the lanes: S[c] = (a_i[2c], a_i[2c+1]) with
+// a_i = row i + row 15 - i, D[c] the same for a_(15-i) = row i - row 15 - i (true
+// signs); 44 pair additions and 32 scalar additions
+struct FwdRowT16 {
+  __device__ static __forceinline__ void run(const float2 (&X)[16], float2 (&S)[8], float2 (&D)[8]) {
+    const float2 t16 = __fadd2_rn(X[0], X[15]);
+    const float2 t17 = sub2(X[7], X[8]);
+    const float2 t18 = __fadd2_rn(X[1], X[14]);
+    const float2 t19 = sub2(X[6], X[9]);
+    const float2 t20 = __fadd2_rn(X[2], X[13]);
+    const float2 t21 = sub2(X[5], X[10]);
+    const float2 t22 = __fadd2_rn(X[3], X[12]);
+    const float2 t23 = sub2(X[4], X[11]);
+    const float2 t24 = __fadd2_rn(X[4], X[11]);
+    const float2 t25 = sub2(X[3], X[12]);
+    const float2 t26 = __fadd2_rn(X[5], X[10]);
+    const float2 t27 = sub2(X[2], X[13]);
+    const float2 t28 = __fadd2_rn(X[6], X[9]);
+    const float2 t29 = sub2(X[1], X[14]);
+    const float2 t30 = __fadd2_rn(X[7], X[8]);
+    const float2 t31 = sub2(X[0], X[15]);
+    const float2 t32 = __fadd2_rn(t16, t30);
+    const float2 t33 = sub2(t22, t24);
+    const float2 t34 = __fadd2_rn(t18, t28);
+    const float2 t35 = sub2(t20, t26);
+    const float2 t36 = __fadd2_rn(t20, t26);
+    const float2 t37 = sub2(t18, t28);
+    const float2 t38 = __fadd2_rn(t22, t24);
+    const float2 t39 = sub2(t16, t30);
+    const float2 t40 = __fadd2_rn(t17, t19);
+    const float2 t41 = sub2(t29, t31);
+    const float2 t42 = __fadd2_rn(t23, t21);
+    const float2 t43 = sub2(t25, t27);
+    const float2 t44 = __fadd2_rn(t25, t27);
+    const float2 t45 = sub2(t21, t23);
+    const float2 t46 = __fadd2_rn(t31, t29);
+    const float2 t47 = sub2(t17, t19);
+    const float2 t48 = __fadd2_rn(t32, t38);
+    const float2 t49 = __fadd2_rn(t34, t36);
+    const float2 t50 = sub2(t34, t36);
+    const float2 t51 = sub2(t32, t38);
+    const float2 t52 = __fadd2_rn(t40, t46);
+    const float2 t53 = __fadd2_rn(t42, t44);
+    const float2 t54 = sub2(t42, t44);
+    const float2 t55 = sub2(t40, t46);
+    const float2 t56 = __fadd2_rn(t48, t49);
+    const float2 t57 = sub2(t48, t49);
+    const float2 t58 = __fadd2_rn(t52, t53);
+    const float2 t59 = sub2(t52, t53);
+    S[0] = make_float2(__fadd_rn(t56.x, t56.y), __fadd_rn(t58.x, t58.y));
+    D[0] = make_float2(__fadd_rn(t56.x, -t56.y), __fadd_rn(t58.x, -t58.y));
+    S[1] = make_float2(__fadd_rn(t39.x, t39.y), __fadd_rn(-t55.x, -t55.y));
+    D[1] = make_float2(__fadd_rn(t39.x, -t39.y), __fadd_rn(-t55.x, t55.y));
+    S[2] = make_float2(__fadd_rn(t51.x, t51.y), __fadd_rn(t59.x, t59.y));
+    D[2] = make_float2(__fadd_rn(t51.x, -t51.y), __fadd_rn(t59.x, -t59.y));
+    S[3] = make_float2(__fadd_rn(-t35.x, -t35.y), __fadd_rn(t47.x, t47.y));
+    D[3] = make_float2(__fadd_rn(-t35.x, t35.y), __fadd_rn(t47.x, -t47.y));
+    S[4] = make_float2(__fadd_rn(t57.x, t57.y), __fadd_rn(t43.x, t43.y));
+    D[4] = make_float2(__fadd_rn(t57.x, -t57.y), __fadd_rn(t43.x, -t43.y));
+    S[5] = make_float2(__fadd_rn(-t37.x, -t37.y), __fadd_rn(-t54.x, -t54.y));
+    D[5] = make_float2(__fadd_rn(-t37.x, t37.y), __fadd_rn(-t54.x, t54.y));
+    S[6] = make_float2(__fadd_rn(-t50.x, -t50.y), __fadd_rn(-t41.x, -t41.y));
+    D[6] = make_float2(__fadd_rn(-t50.x, t50.y), __fadd_rn(-t41.x, t41.y));
+    S[7] = make_float2(__fadd_rn(-t33.x, -t33.y), __fadd_rn(t45.x, t45.y));
+    D[7] = make_float2(__fadd_rn(-t33.x, t33.y), __fadd_rn(t45.x, -t45.y));
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 3:
+// n[u] = sign[u] * (T x)[u]; 15 pair additions
+struct FwdColM3 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfff8u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[3]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 5:
+// n[u] = sign[u] * (T x)[u]; 17 pair additions
+struct FwdColM5 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0008u, 0xffe0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[5]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 7:
+// n[u] = sign[u] * (T x)[u]; 19 pair additions
+struct FwdColM7 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0048u, 0xff80u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[7]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 11:
+// n[u] = sign[u] * (T x)[u]; 23 pair additions
+struct FwdColM11 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0448u, 0xf800u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[11]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t21 = sub2(a[1], a[6]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t27 = sub2(a[12], a[13]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+    n[9] = t27;
+    n[10] = t21;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 16:
+// n[u] = sign[u] * (T x)[u]; 28 pair additions
+struct FwdColM16 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x7c48u, 0x0000u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[16]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t17 = sub2(a[3], a[4]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t21 = sub2(a[1], a[6]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t25 = sub2(a[14], a[15]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t27 = sub2(a[12], a[13]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t29 = sub2(a[10], a[11]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t34 = sub2(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t38 = sub2(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+    n[9] = t27;
+    n[10] = t21;
+    n[11] = t38;
+    n[12] = t34;
+    n[13] = t25;
+    n[14] = t17;
+    n[15] = t29;
+  }
+};
+
+// inverse column pass, inputs u < 3 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 2 pair additions and 12 scalar additions
+struct InvColT3 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t3 = __fadd2_rn(w[0], w[2]);
+    const float2 t4 = sub2(w[0], w[2]);
+    const float s0 = __fadd_rn(t3.x, w[1].x);
+    const float s1 = __fadd_rn(-w[1].x, t3.x);
+    const float s2 = __fadd_rn(t3.y, w[1].y);
+    const float s3 = __fadd_rn(-w[1].y, t3.y);
+    const float s4 = __fadd_rn(w[0].x, w[1].x);
+    const float s5 = __fadd_rn(-w[1].x, w[0].x);
+    const float s6 = __fadd_rn(w[0].y, w[1].y);
+    const float s7 = __fadd_rn(-w[1].y, w[0].y);
+    const float s8 = __fadd_rn(t4.x, w[1].x);
+    const float s9 = __fadd_rn(-w[1].x, t4.x);
+    const float s10 = __fadd_rn(t4.y, w[1].y);
+    const float s11 = __fadd_rn(-w[1].y, t4.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s4, s5);
+    Z[2][1] = make_float2(s6, s7);
+    Z[3][0] = make_float2(s4, s5);
+    Z[3][1] = make_float2(s6, s7);
+    Z[4][0] = make_float2(s4, s5);
+    Z[4][1] = make_float2(s6, s7);
+    Z[5][0] = make_float2(s4, s5);
+    Z[5][1] = make_float2(s6, s7);
+    Z[6][0] = make_float2(s4, s5);
+    Z[6][1] = make_float2(s6, s7);
+    Z[7][0] = make_float2(s8, s9);
+    Z[7][1] = make_float2(s10, s11);
+  }
+};
+
+// inverse column pass, inputs u < 5 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 6 pair additions and 24 scalar additions
+struct InvColT5 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t5 = __fadd2_rn(w[0], w[4]);
+    const float2 t6 = sub2(w[0], w[4]);
+    const float2 t7 = sub2(w[1], w[3]);
+    const float2 t8 = __fadd2_rn(w[1], w[3]);
+    const float2 t9 = __fadd2_rn(t5, w[2]);
+    const float2 t10 = sub2(w[2], t5);
+    const float s0 = __fadd_rn(t8.x, t9.x);
+    const float s1 = __fadd_rn(-t8.x, t9.x);
+    const float s2 = __fadd_rn(t8.y, t9.y);
+    const float s3 = __fadd_rn(-t8.y, t9.y);
+    const float s4 = __fadd_rn(t8.x, w[0].x);
+    const float s5 = __fadd_rn(-t8.x, w[0].x);
+    const float s6 = __fadd_rn(t8.y, w[0].y);
+    const float s7 = __fadd_rn(-t8.y, w[0].y);
+    const float s8 = __fadd_rn(w[0].x, w[1].x);
+    const float s9 = __fadd_rn(-w[1].x, w[0].x);
+    const float s10 = __fadd_rn(w[0].y, w[1].y);
+    const float s11 = __fadd_rn(-w[1].y, w[0].y);
+    const float s12 = __fadd_rn(t6.x, w[1].x);
+    const float s13 = __fadd_rn(-w[1].x, t6.x);
+    const float s14 = __fadd_rn(t6.y, w[1].y);
+    const float s15 = __fadd_rn(-w[1].y, t6.y);
+    const float s16 = __fadd_rn(t7.x, w[0].x);
+    const float s17 = __fadd_rn(-t7.x, w[0].x);
+    const float s18 = __fadd_rn(t7.y, w[0].y);
+    const float s19 = __fadd_rn(-t7.y, w[0].y);
+    const float s20 = __fadd_rn(-t10.x, t7.x);
+    const float s21 = __fadd_rn(-t10.x, -t7.x);
+    const float s22 = __fadd_rn(-t10.y, t7.y);
+    const float s23 = __fadd_rn(-t10.y, -t7.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s12, s13);
+    Z[4][1] = make_float2(s14, s15);
+    Z[5][0] = make_float2(s8, s9);
+    Z[5][1] = make_float2(s10, s11);
+    Z[6][0] = make_float2(s16, s17);
+    Z[6][1] = make_float2(s18, s19);
+    Z[7][0] = make_float2(s20, s21);
+    Z[7][1] = make_float2(s22, s23);
+  }
+};
+
+// inverse column pass, inputs u < 7 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 10 pair additions and 28 scalar additions
+struct InvColT7 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t7 = __fadd2_rn(w[1], w[5]);
+    const float2 t8 = sub2(w[1], w[5]);
+    const float2 t9 = __fadd2_rn(w[0], w[4]);
+    const float2 t10 = sub2(w[0], w[4]);
+    const float2 t11 = sub2(w[3], t7);
+    const float2 t12 = __fadd2_rn(t7, w[3]);
+    const float2 t13 = __fadd2_rn(t9, w[2]);
+    const float2 t14 = __fadd2_rn(w[0], w[6]);
+    const float2 t15 = sub2(w[0], w[6]);
+    const float2 t16 = sub2(w[2], t9);
+    const float s0 = __fadd_rn(t12.x, t13.x);
+    const float s1 = __fadd_rn(-t12.x, t13.x);
+    const float s2 = __fadd_rn(t12.y, t13.y);
+    const float s3 = __fadd_rn(-t12.y, t13.y);
+    const float s4 = __fadd_rn(t12.x, w[0].x);
+    const float s5 = __fadd_rn(-t12.x, w[0].x);
+    const float s6 = __fadd_rn(t12.y, w[0].y);
+    const float s7 = __fadd_rn(-t12.y, w[0].y);
+    const float s8 = __fadd_rn(t15.x, t8.x);
+    const float s9 = __fadd_rn(-t8.x, t15.x);
+    const float s10 = __fadd_rn(t15.y, t8.y);
+    const float s11 = __fadd_rn(-t8.y, t15.y);
+    const float s12 = __fadd_rn(t10.x, t8.x);
+    const float s13 = __fadd_rn(-t8.x, t10.x);
+    const float s14 = __fadd_rn(t10.y, t8.y);
+    const float s15 = __fadd_rn(-t8.y, t10.y);
+    const float s16 = __fadd_rn(t14.x, t8.x);
+    const float s17 = __fadd_rn(-t8.x, t14.x);
+    const float s18 = __fadd_rn(t14.y, t8.y);
+    const float s19 = __fadd_rn(-t8.y, t14.y);
+    const float s20 = __fadd_rn(-t11.x, w[0].x);
+    const float s21 = __fadd_rn(t11.x, w[0].x);
+    const float s22 = __fadd_rn(-t11.y, w[0].y);
+    const float s23 = __fadd_rn(t11.y, w[0].y);
+    const float s24 = __fadd_rn(-t11.x, -t16.x);
+    const float s25 = __fadd_rn(-t16.x, t11.x);
+    const float s26 = __fadd_rn(-t11.y, -t16.y);
+    const float s27 = __fadd_rn(-t16.y, t11.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s12, s13);
+    Z[4][1] = make_float2(s14, s15);
+    Z[5][0] = make_float2(s16, s17);
+    Z[5][1] = make_float2(s18, s19);
+    Z[6][0] = make_float2(s20, s21);
+    Z[6][1] = make_float2(s22, s23);
+    Z[7][0] = make_float2(s24, s25);
+    Z[7][1] = make_float2(s26, s27);
+  }
+};
+
+// inverse column pass, inputs u < 11 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 18 pair additions and 32 scalar additions
+struct InvColT11 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t11 = __fadd2_rn(w[0], w[8]);
+    const float2 t12 = sub2(w[0], w[8]);
+    const float2 t13 = __fadd2_rn(w[1], w[5]);
+    const float2 t14 = sub2(w[1], w[5]);
+    const float2 t15 = __fadd2_rn(t11, w[4]);
+    const float2 t16 = sub2(w[4], t11);
+    const float2 t17 = sub2(w[3], t13);
+    const float2 t18 = __fadd2_rn(t13, w[3]);
+    const float2 t19 = __fadd2_rn(t15, w[2]);
+    const float2 t20 = sub2(w[10], t12);
+    const float2 t21 = __fadd2_rn(t12, w[6]);
+    const float2 t22 = sub2(w[6], t12);
+    const float2 t23 = __fadd2_rn(t12, w[10]);
+    const float2 t24 = sub2(w[2], t15);
+    const float2 t25 = sub2(w[7], t17);
+    const float2 t26 = sub2(w[9], t14);
+    const float2 t27 = __fadd2_rn(t14, w[9]);
+    const float2 t28 = __fadd2_rn(t17, w[7]);
+    const float s0 = __fadd_rn(t18.x, t19.x);
+    const float s1 = __fadd_rn(-t18.x, t19.x);
+    const float s2 = __fadd_rn(t18.y, t19.y);
+    const float s3 = __fadd_rn(-t18.y, t19.y);
+    const float s4 = __fadd_rn(-t20.x, t18.x);
+    const float s5 = __fadd_rn(-t18.x, -t20.x);
+    const float s6 = __fadd_rn(-t20.y, t18.y);
+    const float s7 = __fadd_rn(-t18.y, -t20.y);
+    const float s8 = __fadd_rn(-t22.x, -t26.x);
+    const float s9 = __fadd_rn(-t22.x, t26.x);
+    const float s10 = __fadd_rn(-t22.y, -t26.y);
+    const float s11 = __fadd_rn(-t22.y, t26.y);
+    const float s12 = __fadd_rn(-t16.x, t27.x);
+    const float s13 = __fadd_rn(-t16.x, -t27.x);
+    const float s14 = __fadd_rn(-t16.y, t27.y);
+    const float s15 = __fadd_rn(-t16.y, -t27.y);
+    const float s16 = __fadd_rn(-t16.x, t14.x);
+    const float s17 = __fadd_rn(-t14.x, -t16.x);
+    const float s18 = __fadd_rn(-t16.y, t14.y);
+    const float s19 = __fadd_rn(-t14.y, -t16.y);
+    const float s20 = __fadd_rn(t14.x, t21.x);
+    const float s21 = __fadd_rn(-t14.x, t21.x);
+    const float s22 = __fadd_rn(t14.y, t21.y);
+    const float s23 = __fadd_rn(-t14.y, t21.y);
+    const float s24 = __fadd_rn(-t28.x, t23.x);
+    const float s25 = __fadd_rn(t23.x, t28.x);
+    const float s26 = __fadd_rn(-t28.y, t23.y);
+    const float s27 = __fadd_rn(t23.y, t28.y);
+    const float s28 = __fadd_rn(-t24.x, t25.x);
+    const float s29 = __fadd_rn(-t24.x, -t25.x);
+    const float s30 = __fadd_rn(-t24.y, t25.y);
+    const float s31 = __fadd_rn(-t24.y, -t25.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s16, s17);
+    Z[4][1] = make_float2(s18, s19);
+    Z[5][0] = make_float2(s20, s21);
+    Z[5][1] = make_float2(s22, s23);
+    Z[6][0] = make_float2(s24, s25);
+    Z[6][1] = make_float2(s26, s27);
+    Z[7][0] = make_float2(s28, s29);
+    Z[7][1] = make_float2(s30, s31);
+  }
+};
+
+// inverse column pass, inputs u < 16 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 28 pair additions and 32 scalar additions
+struct InvColT16 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t16 = __fadd2_rn(w[0], w[8]);
+    const float2 t17 = sub2(w[0], w[8]);
+    const float2 t18 = __fadd2_rn(w[1], w[5]);
+    const float2 t19 = sub2(w[1], w[5]);
+    const float2 t20 = __fadd2_rn(t16, w[4]);
+    const float2 t21 = sub2(w[12], t17);
+    const float2 t22 = __fadd2_rn(t17, w[12]);
+    const float2 t23 = sub2(w[4], t16);
+    const float2 t24 = sub2(w[3], t18);
+    const float2 t25 = sub2(w[11], t19);
+    const float2 t26 = __fadd2_rn(t19, w[11]);
+    const float2 t27 = __fadd2_rn(t18, w[3]);
+    const float2 t28 = __fadd2_rn(t20, w[2]);
+    const float2 t29 = sub2(w[14], t23);
+    const float2 t30 = __fadd2_rn(t21, w[10]);
+    const float2 t31 = __fadd2_rn(t22, w[6]);
+    const float2 t32 = sub2(w[6], t22);
+    const float2 t33 = sub2(w[10], t21);
+    const float2 t34 = __fadd2_rn(t23, w[14]);
+    const float2 t35 = sub2(w[2], t20);
+    const float2 t36 = sub2(w[7], t24);
+    const float2 t37 = sub2(w[13], t27);
+    const float2 t38 = __fadd2_rn(t25, w[15]);
+    const float2 t39 = sub2(w[9], t26);
+    const float2 t40 = __fadd2_rn(t26, w[9]);
+    const float2 t41 = sub2(w[15], t25);
+    const float2 t42 = __fadd2_rn(t27, w[13]);
+    const float2 t43 = __fadd2_rn(t24, w[7]);
+    const float s0 = __fadd_rn(t28.x, t42.x);
+    const float s1 = __fadd_rn(-t42.x, t28.x);
+    const float s2 = __fadd_rn(t28.y, t42.y);
+    const float s3 = __fadd_rn(-t42.y, t28.y);
+    const float s4 = __fadd_rn(-t30.x, -t37.x);
+    const float s5 = __fadd_rn(-t30.x, t37.x);
+    const float s6 = __fadd_rn(-t30.y, -t37.y);
+    const float s7 = __fadd_rn(-t30.y, t37.y);
+    const float s8 = __fadd_rn(-t32.x, -t39.x);
+    const float s9 = __fadd_rn(-t32.x, t39.x);
+    const float s10 = __fadd_rn(-t32.y, -t39.y);
+    const float s11 = __fadd_rn(-t32.y, t39.y);
+    const float s12 = __fadd_rn(-t34.x, t40.x);
+    const float s13 = __fadd_rn(-t34.x, -t40.x);
+    const float s14 = __fadd_rn(-t34.y, t40.y);
+    const float s15 = __fadd_rn(-t34.y, -t40.y);
+    const float s16 = __fadd_rn(-t38.x, t29.x);
+    const float s17 = __fadd_rn(t29.x, t38.x);
+    const float s18 = __fadd_rn(-t38.y, t29.y);
+    const float s19 = __fadd_rn(t29.y, t38.y);
+    const float s20 = __fadd_rn(t31.x, t41.x);
+    const float s21 = __fadd_rn(-t41.x, t31.x);
+    const float s22 = __fadd_rn(t31.y, t41.y);
+    const float s23 = __fadd_rn(-t41.y, t31.y);
+    const float s24 = __fadd_rn(-t43.x, t33.x);
+    const float s25 = __fadd_rn(t33.x, t43.x);
+    const float s26 = __fadd_rn(-t43.y, t33.y);
+    const float s27 = __fadd_rn(t33.y, t43.y);
+    const float s28 = __fadd_rn(-t35.x, t36.x);
+    const float s29 = __fadd_rn(-t35.x, -t36.x);
+    const float s30 = __fadd_rn(-t35.y, t36.y);
+    const float s31 = __fadd_rn(-t35.y, -t36.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s16, s17);
+    Z[4][1] = make_float2(s18, s19);
+    Z[5][0] = make_float2(s20, s21);
+    Z[5][1] = make_float2(s22, s23);
+    Z[6][0] = make_float2(s24, s25);
+    Z[6][1] = make_float2(s26, s27);
+    Z[7][0] = make_float2(s28, s29);
+    Z[7][1] = make_float2(s30, s31);
+  }
+};
+
 // sign of each output of the (unpruned) forward network: row-pass outputs
 // are stored unsigned; the column thread folds this sign into its scale.
 constexpr unsigned kFwdNegMask = 0xdc48u;
