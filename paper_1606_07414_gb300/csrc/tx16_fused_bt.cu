@@ -1,29 +1,38 @@
-// Fused codec for 8-bit planes, one 16x16 block per thread, entirely in
-// registers (zonal classes with at most 8 kept columns, no level output).
+// Fused codec, one 16x16 block per thread, entirely in registers (zonal
+// classes with at most 8 kept columns, no level output), for 8-bit planes and
+// for 9..12-bit planes in uint16.
 //
 // Mapping.  A warp codes a tile of 32 consecutive blocks of one image, lane l
 // block 32 t + l, so each 16-byte row load of a warp reads 32 horizontally
-// adjacent blocks: 512 contiguous bytes.  Warps take tiles grid-stride.
-//   row pass     the block's rows two at a time: float2 = (row 2p, row 2p+1),
-//                16 samples -> the V kept columns (forward row network)
-//   column pass  the kept columns two at a time: float2 = (column 2c,
-//                column 2c+1), re-paired in registers from the row pass;
-//                forward column network, S-merged quantiser, inverse column
-//                network
-//   row pass     re-paired into (row 2p, row 2p+1) again: inverse row
-//                network, rounding, 16-byte stores, squared error
-// No shared-memory exchange and no barrier.  Shared memory holds each
-// thread's 16 input rows (one stage by default: cp.async refills it with the
-// warp's next tile once the current rows are used, and the other warps of the
-// SM cover that latency; two stages are a compile-time option), the inverse
-// column results of the parked column pairs, and a small per-warp table of
-// the quantiser constants of the image being coded (each lane of a column
-// pair has its own column's scale and sign).  The squared error reads the
-// staged rows again.
+// adjacent blocks: 512 contiguous bytes.  Warps take tiles grid-stride, or
+// claim them from a work list.
+//   row pass     rows i and 15 - i of the block in the two lanes of a float2
+//                (i = 0..7): forward row network to the V kept columns, then
+//                the column pass's first butterfly (M1 pairs rows i and
+//                15 - i) as scalar additions across the lanes, written as
+//                column pairs (column 2c, column 2c + 1)
+//   column pass  per column pair: the rest of the forward column network,
+//                the S-merged quantiser, the inverse column network whose
+//                last butterfly (M1 again) writes (row i, row 15 - i) pairs
+//   row pass     per row pair: inverse row network, rounding, 16-byte
+//                stores of rows i and 15 - i, squared error
+// No register moves between the passes, no shared-memory exchange and no
+// barrier.  Shared memory holds each thread's 16 input rows (cp.async, one
+// stage: refilled with the warp's next tile once the current rows are used,
+// the other warps of the SM covering that latency), the column pairs parked
+// there to save registers (their column-pass inputs, then in the same slots
+// their inverse results), and a small per-warp table of the quantiser
+// constants of the image being coded.  The squared error reads the staged
+// rows again.
 //
-// The arithmetic is that of the two-blocks-per-pair kernel (tx16_fused.cu) on
-// differently paired lanes: the same generated networks, the same binary32
-// quantiser steps and the same exact rounding, so results are identical.
+// Exactness.  Samples enter as 2^23 + 256 x: every node of the forward
+// transform is a multiple of 256 below 2^32 in magnitude (exact in binary32),
+// so M1 needs no bias correction; the column pass yields 256 (T X T^t) plus
+// 2^31 at (0, 0), removed exactly, and the 1/256 is folded into the
+// quantiser's scale.  The quantiser and the inverse follow the library's
+// binary32 definition (each stage output one rounded operation on two stage
+// inputs, the same as the two-blocks-per-pair kernel in tx16_fused.cu), and
+// the sample rounding is exact.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -110,34 +119,10 @@ struct BtLimits<ZoneC> {
 // classes e(u) = 0, 1, 2.
 template <int U, int NP>
 struct PairConsts {
-  float2 fs[U][NP];  // quantiser: sign_v f ; no quantiser: sign_v D'_u D'_v / 256 ; 0 outside the zone
+  float2 fs[U][NP];  // sign_u f / 256 (quantiser) or sign_u D'_u D'_v / 2^16 (none); 0 outside the zone
   float2 gg[3][NP];  // g
   float2 gc[3][NP];  // -2^23 g
 };
-
-template <int U, int NP>
-__device__ __forceinline__ void fill_consts(const ImgParam& I, PairConsts<U, NP>& Q, int lane) {
-  const bool quant = (I.flags & kQuantFlag) != 0;
-  float* q = reinterpret_cast<float*>(&Q);
-  for (int idx = lane; idx < U * 2 * NP; idx += 32) {
-    const int u = idx / (2 * NP);
-    const int v = idx - u * 2 * NP;  // = 2 c + half
-    const int k = scale_class(u) + scale_class(v);
-    const float sv = ((kFwdNegMask >> v) & 1u) ? -1.f : 1.f;
-    const float val = quant ? sv * I.f[k] : sv * float(1 << k) * (1.f / 256.f);
-    q[idx] = u < int(I.colh[v]) ? val : 0.f;
-  }
-  constexpr int kPer = 6 * NP;  // floats per g table
-  for (int idx = lane; idx < 2 * kPer; idx += 32) {
-    const int tab = idx / kPer;
-    const int rem = idx - tab * kPer;
-    const int e = rem / (2 * NP);
-    const int v = rem - e * 2 * NP;
-    const int k = e + scale_class(v);
-    q[U * 2 * NP + idx] = quant ? (tab == 0 ? I.g[k] : -8388608.f * I.g[k]) : 0.f;
-  }
-  __syncwarp();
-}
 
 // 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros and
 // reads nothing.  The "memory" clobber keeps the compiler from moving shared
@@ -234,26 +219,6 @@ constexpr int cz_pairs() {
 template <class Z, int SB = 1>
 constexpr int cz_bytes() { return cz_pairs<Z, SB>() * 16 * 32 * bt_warps<Z, SB>() * 8; }
 
-// The 4 * SB words of staged row `row` of this thread (slots row * SB + h).
-template <int SB>
-__device__ __forceinline__ void load_row_words(const uint8_t* rows, int row, int slot_bytes, unsigned (&w)[4 * SB]) {
-#pragma unroll
-  for (int h = 0; h < SB; ++h) {
-    const uint4 v = *reinterpret_cast<const uint4*>(rows + (row * SB + h) * slot_bytes);
-    w[4 * h] = v.x;
-    w[4 * h + 1] = v.y;
-    w[4 * h + 2] = v.z;
-    w[4 * h + 3] = v.w;
-  }
-}
-
-// 2^23 + sample j of a staged row, as a float (exact for samples < 2^16)
-template <int SB>
-__device__ __forceinline__ float biased_sample(const unsigned (&w)[4 * SB], int j) {
-  if (SB == 1) return biased(w[j >> 2], j & 3);
-  return __uint_as_float(__byte_perm(w[j >> 1], 0x4B000000u, (j & 1) ? 0x7532u : 0x7510u));
-}
-
 // Tile schedules of one warp (every call is warp-uniform).  StaticWarps: warp
 // w takes tiles w, w + W, w + 2W, ... (W warps in the grid).  DynamicWarps:
 // the warp claims chunks of tiles from a counter of the work list, the next
@@ -288,274 +253,6 @@ struct DynamicWarps {
     return s;
   }
 };
-
-// The codec over the tiles a schedule hands this warp.  imgs: the launch's
-// descriptors (tile0 in warp tiles, ascending), in kernel parameters or in a
-// device work list.
-// SB: bytes per sample (1: 8-bit planes; 2: 9..12-bit planes in uint16).
-// Staged rows: slot (row * SB + half) holds 16 bytes of each thread's row.
-template <class Z, bool DST, int SB, class Sched>
-__device__ __forceinline__ void bt_tiles(const ImgParam* __restrict__ imgs, int nimg, int ntiles,
-                                         unsigned long long* sse, Sched& sched) {
-  static_assert(SB == 1 || SB == 2, "8- or 16-bit samples");
-  constexpr int kBtWarps = bt_warps<Z, SB>();
-  constexpr int kBtThreads = 32 * kBtWarps;
-  constexpr int kStageBytes = stage_bytes<Z, SB>();
-  constexpr int kSlot = kBtThreads * 16;  // bytes of one staged slot
-  constexpr int kCzSmem = cz_pairs<Z, SB>();  // parked column pairs
-  static_assert(kCzSmem < Z::V / 2, "at least one column pair stays in registers");
-  constexpr int V = Z::V;
-  constexpr int NP = V / 2;
-  static_assert(V % 2 == 0, "column pairs");
-  extern __shared__ __align__(16) uint8_t rows_smem[];  // 2 stages
-  __shared__ PairConsts<Z::U, NP> consts[kBtWarps];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  PairConsts<Z::U, NP>& Q = consts[wib];
-  int t = sched.first();
-  if (t < 0) return;
-  constexpr int kStages = stages<Z, SB>();  // 2: the next tile is fetched during this one
-  static_assert(kStages == 1 || kStages == 2, "one or two input stages");
-  constexpr bool kRolling = rolling_refill<Z, SB>();
-  uint8_t* const cz_park = rows_smem + kStages * kStageBytes + threadIdx.x * 8;
-
-  // Where this thread's block of tile tt (image kk) is read from: its first
-  // row and the row pitch, or, past the image's end, the image base with
-  // pitch 0 and no bytes (the copies then fill zeros).
-  struct RowSrc {
-    const uint8_t* g;
-    int64_t pitch;
-    int bytes;
-  };
-  auto row_src = [&](int kk, int tt) {
-    const ImgParam& I = imgs[kk];
-    const int blk = (tt - I.tile0) * kWarpTile + lane;
-    const uint8_t* src = static_cast<const uint8_t*>(I.src);
-    if (blk >= I.nblk) return RowSrc{src, 0, 0};
-    const int2 c = block_coords(I.div_magic, I.nbx, blk);
-    return RowSrc{src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16 * SB, I.src_pitch, 16};
-  };
-  // rows [i0, i1) of a block into stage st, as one commit group
-  auto fetch_rows = [&](const RowSrc& r, int st, int i0, int i1) {
-    uint8_t* s = rows_smem + st * kStageBytes + threadIdx.x * 16;
-#pragma unroll
-    for (int i = i0; i < i1; ++i)
-#pragma unroll
-      for (int h = 0; h < SB; ++h) cp_async16(s + (i * SB + h) * kSlot, r.g + int64_t(i) * r.pitch + 16 * h, r.bytes);
-    cp_async_commit();
-  };
-  // the 16 rows of this thread's block of tile tt (image kk) into stage st
-  auto prefetch = [&](int kk, int tt, int st) { fetch_rows(row_src(kk, tt), st, 0, 16); };
-  auto tile_end_of = [&](int kk) { return kk + 1 < nimg ? imgs[kk + 1].tile0 : ntiles; };
-
-  // the image of the tile being coded (k) and of the tile being fetched (kn)
-  int k = image_of_tile(imgs, nimg, t);
-  int kn = k;
-  int end_k = tile_end_of(k), end_kn = end_k;
-  prefetch(k, t, 0);
-  fill_consts<Z::U, NP>(imgs[k], Q, lane);
-  unsigned long long acc = 0;
-  int stage = 0;
-  // One stage, rolling refill: the rows of the next tile are fetched row pair
-  // by row pair as the inverse pass of this tile finishes with them (one
-  // commit group per pair, in order), and the forward pass of the next tile
-  // waits for each pair only when it needs it.  "rolling" says that the
-  // current tile's rows arrived that way.  Otherwise one stage is refilled
-  // with all 16 rows after the tile.
-  bool rolling = false;
-
-  while (t >= 0) {
-    const int tn = sched.next(t);
-    if (tn >= 0 && tn >= end_kn) {
-      kn = image_of_tile(imgs, nimg, tn);
-      end_kn = tile_end_of(kn);
-    }
-    if (kStages == 2 && tn >= 0) {
-      // fetch the next tile of this warp while this one is coded
-      prefetch(kn, tn, stage ^ 1);
-      cp_async_wait<1>();
-    } else if (kStages == 2 || !rolling) {
-      cp_async_wait<0>();
-    }
-    const RowSrc next = (kRolling && tn >= 0) ? row_src(kn, tn) : RowSrc{nullptr, 0, 0};
-    if (t >= end_k) {  // warp-uniform: a later image
-      if (sse) flush_sse(sse, imgs[k].out_index, acc);
-      acc = 0;
-      k = image_of_tile(imgs, nimg, t);
-      end_k = tile_end_of(k);
-      __syncwarp();
-      fill_consts<Z::U, NP>(imgs[k], Q, lane);
-    }
-    const ImgParam& I = imgs[k];
-    const bool quant = (I.flags & kQuantFlag) != 0;
-    const int blk = (t - I.tile0) * kWarpTile + lane;
-    const bool valid = blk < I.nblk;
-    const int2 c = valid ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
-    const uint8_t* rows = rows_smem + stage * kStageBytes + threadIdx.x * 16;  // slot 0 of this thread
-    // this thread's block in the output plane (the image's first block for a
-    // lane past its end, which stores nothing)
-    const int64_t dpitch = DST ? I.dst_pitch : 0;
-    uint8_t* const dblk = DST ? static_cast<uint8_t*>(I.dst) + int64_t(c.x) * 16 * dpitch + c.y * 16 * SB : nullptr;
-
-    // ---- forward row pass: R[p][v] = (row 2p, row 2p + 1) at column v ----
-    float2 R[8][V];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      if (kRolling && rolling) cp_async_wait_n(7 - p);  // row pair p of this tile has arrived
-      unsigned wa[4 * SB], wb[4 * SB];
-      load_row_words<SB>(rows, 2 * p, kSlot, wa);
-      load_row_words<SB>(rows, 2 * p + 1, kSlot, wb);
-      float2 X[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) X[j] = make_float2(biased_sample<SB>(wa, j), biased_sample<SB>(wb, j));
-      float2 y[16];
-      Z::FwdRow::run(X, y);
-#pragma unroll
-      for (int v = 0; v < V; ++v) R[p][v] = y[v];
-    }
-
-    // ---- column pass: column pair cp = (2 cp, 2 cp + 1) ----
-    float2 Cz[16][NP];
-#pragma unroll
-    for (int cp = 0; cp < NP; ++cp) {
-      float2 x[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float2 r0 = R[i >> 1][2 * cp], r1 = R[i >> 1][2 * cp + 1];
-        x[i] = (i & 1) ? make_float2(r0.y, r1.y) : make_float2(r0.x, r1.x);
-      }
-      float2 n[16];
-      Z::FwdCol::run(x, n);  // n[u] = FwdCol::sign(u) * (row-pass sign of v) * Y[u][v]
-      float2 w[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) w[u] = make_float2(0.f, 0.f);
-      if (quant) {
-#pragma unroll
-        for (int u = 0; u < Z::U; ++u) {
-          const int e = scale_class(u);
-          const float2 tq = __fmul2_rn(n[u], Q.fs[u][cp]);
-          const float2 a = make_float2(fabsf(tq.x), fabsf(tq.y));
-          const float2 m = __fadd2_rd(__fadd2_rd(a, f2(0.5f)), f2(8388608.f));  // 2^23 + floor(|t| + 1/2)
-          float2 q = __ffma2_rn(m, Q.gg[e][cp], Q.gc[e][cp]);                 // fl32(level * g)
-          q.x = __uint_as_float(__float_as_uint(q.x) | (__float_as_uint(tq.x) & 0x80000000u));
-          q.y = __uint_as_float(__float_as_uint(q.y) | (__float_as_uint(tq.y) & 0x80000000u));
-          w[u] = q;
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < Z::U; ++u) w[u] = __fmul2_rn(n[u], Q.fs[u][cp]);
-      }
-      float2 z[16];
-      Z::InvCol::run(w, z);  // z[i] = (T^t W)[i][2 cp .. 2 cp + 1] (with the network's signs)
-      if (cp < kCzSmem) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) st_shared_f2(cz_park + (cp * 16 + i) * (kBtThreads * 8), z[i]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) Cz[i][cp] = z[i];
-      }
-    }
-
-    // ---- inverse row pass, rounding, store, SSE: rows 2p and 2p + 1 ----
-    unsigned s1 = 0;  // squared error of this tile's block
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      float2 wv[16];
-#pragma unroll
-      for (int v = 0; v < 16; ++v) {
-        if (v < V) {
-          const int cp = v >> 1;
-          const bool parked = cp < kCzSmem;
-          const float2 a = parked ? ld_shared_f2(cz_park + (cp * 16 + 2 * p) * (kBtThreads * 8)) : Cz[2 * p][cp];
-          const float2 b = parked ? ld_shared_f2(cz_park + (cp * 16 + 2 * p + 1) * (kBtThreads * 8)) : Cz[2 * p + 1][cp];
-          wv[v] = (v & 1) ? make_float2(a.y, b.y) : make_float2(a.x, b.x);
-        } else {
-          wv[v] = make_float2(0.f, 0.f);
-        }
-      }
-      float2 z[16];
-      Z::InvRow::run(wv, z);  // z[j] = sign[j] * X_tilde[row][j]
-      if (SB == 1) {
-        // sample = clip(floor(X + 1/2), 0, 255): the bits of
-        // RD(RD(X + 1/2) 2^-149), clamped and packed four to a word
-        int na[16], nb[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float2 r = Z::InvRow::sign(j) >= 0 ? __fadd2_rd(z[j], f2(0.5f)) : sub2_rd(f2(0.5f), z[j]);
-          const float2 n = floor_bits2(r);
-          na[j] = __float_as_int(n.x);
-          nb[j] = __float_as_int(n.y);
-        }
-        unsigned xa[4], xb[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          xa[q] = pack4_sat_u8(na[4 * q], na[4 * q + 1], na[4 * q + 2], na[4 * q + 3]);
-          xb[q] = pack4_sat_u8(nb[4 * q], nb[4 * q + 1], nb[4 * q + 2], nb[4 * q + 3]);
-        }
-        if (DST) {
-          uint8_t* drow = dblk + 2 * p * dpitch;
-          if (valid) __stcs(reinterpret_cast<uint4*>(drow), make_uint4(xa[0], xa[1], xa[2], xa[3]));
-          if (valid) __stcs(reinterpret_cast<uint4*>(drow + dpitch), make_uint4(xb[0], xb[1], xb[2], xb[3]));
-        }
-        // SSE = sum |x - y|^2 by bytes (vabsdiff4, then dp4a); a block past
-        // the image's end was staged as zeros and reconstructs to zeros
-        const uint4 a = *reinterpret_cast<const uint4*>(rows + (2 * p) * kSlot);
-        const uint4 b = *reinterpret_cast<const uint4*>(rows + (2 * p + 1) * kSlot);
-        const unsigned ia[4] = {a.x, a.y, a.z, a.w}, ib[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const unsigned da = __vabsdiffu4(ia[q], xa[q]), db = __vabsdiffu4(ib[q], xb[q]);
-          s1 = __dp4a(da, da, s1);
-          s1 = __dp4a(db, db, s1);
-        }
-      } else {
-        // sample = clip(floor(X + 1/2), 0, peak): the bits of
-        // RD(RD(X + 1/2) 2^-149), clamped and packed two to a word
-        const unsigned peak2 = ((1u << (imgs[k].flags & 0xff)) - 1u) * 0x10001u;
-        unsigned ya[8], yb[8];  // reconstructed rows 2p and 2p + 1, two samples per word
-#pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          int va[2], vb[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const float2 r = Z::InvRow::sign(j + e) >= 0 ? __fadd2_rd(z[j + e], f2(0.5f))
-                                                         : sub2_rd(f2(0.5f), z[j + e]);
-            const float2 n = floor_bits2(r);
-            va[e] = __float_as_int(n.x);
-            vb[e] = __float_as_int(n.y);
-          }
-          ya[j >> 1] = pack2_sat_u16(va[0], va[1], peak2);
-          yb[j >> 1] = pack2_sat_u16(vb[0], vb[1], peak2);
-        }
-        if (DST) {
-          uint8_t* drow = dblk + 2 * p * dpitch;
-          if (valid) __stcs(reinterpret_cast<uint4*>(drow), make_uint4(ya[0], ya[1], ya[2], ya[3]));
-          if (valid) __stcs(reinterpret_cast<uint4*>(drow) + 1, make_uint4(ya[4], ya[5], ya[6], ya[7]));
-          if (valid) __stcs(reinterpret_cast<uint4*>(drow + dpitch), make_uint4(yb[0], yb[1], yb[2], yb[3]));
-          if (valid) __stcs(reinterpret_cast<uint4*>(drow + dpitch) + 1, make_uint4(yb[4], yb[5], yb[6], yb[7]));
-        }
-        // SSE: integer differences of the staged samples and the reconstruction
-        unsigned wa[8], wb[8];
-        load_row_words<2>(rows, 2 * p, kSlot, wa);
-        load_row_words<2>(rows, 2 * p + 1, kSlot, wb);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int d0 = int(wa[q] & 0xffffu) - int(ya[q] & 0xffffu), d1 = int(wa[q] >> 16) - int(ya[q] >> 16);
-          const int d2 = int(wb[q] & 0xffffu) - int(yb[q] & 0xffffu), d3 = int(wb[q] >> 16) - int(yb[q] >> 16);
-          s1 += unsigned(d0 * d0) + unsigned(d1 * d1) + unsigned(d2 * d2) + unsigned(d3 * d3);
-        }
-      }
-      // rows 2p and 2p + 1 of the stage are used: refill them for the next tile
-      if (kRolling && tn >= 0) fetch_rows(next, 0, 2 * p, 2 * p + 2);
-    }
-    acc += s1;
-    if (kStages == 1 && !kRolling && tn >= 0) prefetch(kn, tn, 0);  // the used rows replaced at once
-    rolling = kRolling && tn >= 0;
-    t = tn;
-    stage ^= (kStages - 1);
-  }
-  if (sse) flush_sse(sse, imgs[k].out_index, acc);
-}
 
 // ---------------------------------------------------------------------------
 // Bulk-copy staging: the copy engine (cp.async.bulk, completing on an
@@ -1019,18 +716,6 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
   if (sse) flush_sse(sse, imgs[k].out_index, acc);
 }
 
-// Body of the kernels: the row-pair flow (1) or the earlier row/column
-// re-pairing in registers (0).
-#ifndef TX16_BT_FLOW
-#define TX16_BT_FLOW 1
-#endif
-template <class Z, bool DST, int SB, class Sched>
-__device__ __forceinline__ void bt_body(const ImgParam* __restrict__ imgs, int nimg, int ntiles,
-                                        unsigned long long* sse, Sched& sched) {
-  if (TX16_BT_FLOW == 1) bt_tiles_t<Z, DST, SB>(imgs, nimg, ntiles, sse, sched);
-  else bt_tiles<Z, DST, SB>(imgs, nimg, ntiles, sse, sched);
-}
-
 // resident CTAs per SM the registers are budgeted for: the class's setting
 // for 8-bit samples, TX16_BT16_MINCTAS for 16-bit samples (wider staging,
 // more live values in the rounding)
@@ -1045,7 +730,7 @@ __global__ void __launch_bounds__(32 * bt_warps<Z, SB>(), min_ctas<Z, SB>())
     fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
   StaticWarps sched{int(blockIdx.x) * bt_warps<Z, SB>() + int(threadIdx.x >> 5),
                     int(gridDim.x) * bt_warps<Z, SB>(), P.ntiles};
-  bt_body<Z, DST, SB>(P.img, P.nimg, P.ntiles, P.sse, sched);
+  bt_tiles_t<Z, DST, SB>(P.img, P.nimg, P.ntiles, P.sse, sched);
 }
 
 template <class Z, bool DST>
@@ -1053,7 +738,7 @@ __global__ void __launch_bounds__(32 * BtLimits<Z>::kWarps, BtLimits<Z>::kMinCta
     fused_bt_list_kernel(const ImgParam* __restrict__ imgs, int nimg, int ntiles, unsigned* counter, int chunk,
                          unsigned long long* sse) {
   DynamicWarps sched{counter, ntiles, chunk, 0, 0};
-  bt_body<Z, DST, 1>(imgs, nimg, ntiles, sse, sched);
+  bt_tiles_t<Z, DST, 1>(imgs, nimg, ntiles, sse, sched);
 }
 
 template <int MAXI, class Z, bool DST, int SB>
