@@ -712,10 +712,13 @@ def _serving(tx16, torch, np, args):
 # CPU oracle timing (the reference arm and the cpu_baseline key)
 # ---------------------------------------------------------------------------
 def _oracle_frame(job):
-    frame, q, r = job
+    """One frame through the float64 oracle codec; the forward transform by
+    the 44-addition factorisation (path B) unless the job says 'direct'."""
+    frame, q, r = job[:3]
+    forward = job[3] if len(job) > 3 else "factored"
     from oracle import tx16_oracle as O
 
-    O.codec_image(frame, q, r, 8, "fp64")
+    O.codec_image(frame, q, r, 8, "fp64", forward=forward)
     return frame.shape
 
 
@@ -725,7 +728,11 @@ def _oracle_frame_timed(job):
     return time.perf_counter() - t0
 
 
-def cpu_oracle_rate(frames_np, q, r, pool=None, cores=None):
+def cpu_oracle_rate(frames_np, q, r, pool=None, cores=None, single=True):
+    """The oracle's rate on the host cores: frames_np through the float64
+    codec with the factorised forward transform (path B), one frame per task
+    on `cores` single-threaded processes; with `single`, also one frame on one
+    core by each forward path (factorisation and direct matrix products)."""
     import multiprocessing as mp
 
     cores = cores or os.cpu_count() or 1
@@ -736,19 +743,28 @@ def cpu_oracle_rate(frames_np, q, r, pool=None, cores=None):
         pool = mp.get_context("spawn").Pool(cores)
         pool.map(_oracle_frame, [(frames_np[0][:16, :16], q, r)] * cores)  # warm the workers
     t0 = time.perf_counter()
-    pool.map(_oracle_frame, [(f, q, r) for f in frames_np], chunksize=1)
+    pool.map(_oracle_frame, [(f, q, r, "factored") for f in frames_np], chunksize=1)
     dt = time.perf_counter() - t0
-    t1 = pool.apply(_oracle_frame_timed, ((frames_np[0], q, r),))  # one frame, one core
+    out = {}
+    if single:
+        nblk1 = (frames_np.shape[1] // 16) * (frames_np.shape[2] // 16)
+        for fw in ("factored", "direct"):
+            t1 = pool.apply(_oracle_frame_timed, ((frames_np[0], q, r, fw),))  # one frame, one core
+            key = "single_thread" if fw == "factored" else "single_thread_direct_matmul"
+            out[key] = {"value": round(nblk1 / t1 / 1e6, 5), "unit": UNIT, "cores": 1,
+                        "sample": f"one frame in one single-threaded process, forward by "
+                                  f"{'the factorisation' if fw == 'factored' else 'int64 matrix products'}, "
+                                  f"{t1:.3f} s"}
     if own:
         pool.close()
         pool.join()
     nblk = len(frames_np) * (frames_np.shape[1] // 16) * (frames_np.shape[2] // 16)
-    nblk1 = (frames_np.shape[1] // 16) * (frames_np.shape[2] // 16)
-    return {"value": round(nblk / dt / 1e6, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(frames_np)} of the {FRAMES} frames (float64 oracle codec_image, one frame per "
-                      f"task, {cores} single-threaded processes), {dt:.2f} s wall",
-            "single_thread": {"value": round(nblk1 / t1 / 1e6, 5), "unit": UNIT, "cores": 1,
-                              "sample": f"one frame in one single-threaded process, {t1:.3f} s"}}
+    res = {"value": round(nblk / dt / 1e6, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(frames_np)} of the {FRAMES} frames (float64 oracle codec_image, forward by the "
+                     f"44-addition factorisation; one frame per task, {cores} single-threaded processes), "
+                     f"{dt:.2f} s wall"}
+    res.update(out)
+    return res
 
 
 def run_reference(args):
@@ -768,11 +784,11 @@ def run_reference(args):
     pool = mp.get_context("spawn").Pool(cores)
     pool.map(_oracle_frame, [(frames[0][:16, :16], args.q, args.r)] * cores)
     for _ in range(args.warmup):
-        cpu_oracle_rate(frames[:1], args.q, args.r, pool, cores)
+        cpu_oracle_rate(frames[:1], args.q, args.r, pool, cores, single=False)
     rates = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        rates.append(cpu_oracle_rate(frames, args.q, args.r, pool, cores))
+        rates.append(cpu_oracle_rate(frames, args.q, args.r, pool, cores, single=False))
     dt = time.perf_counter() - t0
     pool.close()
     pool.join()
@@ -781,10 +797,12 @@ def run_reference(args):
     line = {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "i64+f64", "data": "synthetic",
-            "config": _workload(args.q, args.r), "impl": "reference",
+            "config": dict(_workload(args.q, args.r), frames_coded_per_step=len(frames)),
+            "impl": "reference",
             "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step: {len(frames)} of the workload's frames (one per core) through "
-                                       f"the float64 oracle on {cores} single-threaded processes"},
+                             "sample": f"each step codes {len(frames)} of the workload's {FRAMES} frames (one per "
+                                       f"core) through the float64 oracle (forward by the factorisation) on "
+                                       f"{cores} single-threaded processes"},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -14,10 +14,17 @@
  *            JPEG convention extended to 16x16                       (Sec. 3.1)
  *
  * Every transform runs through the 44-addition factorisation
- * T = P2 M4 M3 M2 P1 M1 (Sec. 2.2) in exact int32; S is merged into the
- * quantiser (Sec. 2.1, last paragraph), so the only floating point on the
- * device is one binary32 multiply per kept coefficient each way and the
- * binary32 inverse network.
+ * T = P2 M4 M3 M2 P1 M1 (Sec. 2.2), and the forward transform is exact:
+ *   - the fused codec kernels evaluate the forward network on packed binary32
+ *     lanes holding integers (samples enter as 2^23 + 256 x or as integers
+ *     below 2^24), every intermediate an integer multiple of a power of two
+ *     small enough to be represented exactly, so Y = T X T^t bit for bit;
+ *     their no-quantiser inverse is exact the same way (values k / 256);
+ *   - the forward-only, general and unfused kernels use int32.
+ * S is merged into the quantiser (Sec. 2.1, last paragraph): with a
+ * quantiser, the level is taken from one binary32 product per kept
+ * coefficient, the dequantised coefficient is one binary32 product, and the
+ * inverse network runs in binary32, stage by stage as factorised.
  *
  * Conventions for every call below:
  *   - Pointers named "device" are CUDA device pointers owned by the caller;
@@ -383,6 +390,11 @@ void tx16_serve_destroy(tx16_server* server);
  *     two calls whose work overlaps on the GPU (different streams, or
  *     different host threads without ordering) race on the array.  Order such
  *     calls on one stream, or wait for one before issuing the next;
+ *   - the descriptors reach the array through the parameters of small
+ *     kernels launched on `stream` (up to 224 descriptors each), which also
+ *     clear the tile counters and sse; the host copy of the list is not read
+ *     after the call returns, and the call does not wait for earlier work on
+ *     its stream;
  *   - the first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current) and keeps it; make that
  *     first call before any stream capture.

@@ -404,7 +404,7 @@ def psnr(sse_value: int, H: int, W: int, bits: int) -> float:
 
 
 def codec_image(img: np.ndarray, q: float | None, r: int, bits: int = 8,
-                precision: str = "fp64") -> dict:
+                precision: str = "fp64", forward: str = "direct") -> dict:
     """The whole Sec. 3.1 codec on one image: blocks, Y = T X T^t, zonal
     (+ uniform) quantisation, inverse, rearrangement, SSE and PSNR.
 
@@ -413,10 +413,18 @@ def codec_image(img: np.ndarray, q: float | None, r: int, bits: int = 8,
     * q > 0, precision 'fp64': float64 throughout (the definition).
     * q > 0, precision 'fp32': rounding decisions in binary32 along the
       factorisation (``quantise(..., 'fp32')`` and ``inverse_fp32``).
+    * forward: 'direct' (int64 matrix products, ``forward_direct``) or
+      'factored' (the 44-addition factorisation of Sec. 2.2 stage by stage,
+      ``forward_factored``); both give the same Y exactly.
     """
     H, W = img.shape
     X = image_to_blocks(np.asarray(img, dtype=np.int64))
-    Y = forward_direct(X)
+    if forward == "direct":
+        Y = forward_direct(X)
+    elif forward == "factored":
+        Y = forward_factored(X)
+    else:
+        raise ValueError("forward must be 'direct' or 'factored'")
     if q is None:
         levels = np.where(zonal_mask(r), Y, 0)
         rec = pixels_from_exact(inverse_exact_zonal(Y, r), bits)

@@ -159,6 +159,32 @@ def test_new_entry_points_reject_bad_arguments_before_any_device_call(lib):
     assert lib.tx16_codec_mixed(good, None, 0, ctypes.cast(m, ctypes.c_void_p), None, None, None) == tx16.TX16_OK
 
 
+def test_static_entry_point_rejects_bad_arguments_before_any_device_call(lib):
+    """tx16_codec_batch_static checks its arguments on the host: the batch size
+    against its fixed array, alignment of the level and error buffers, and
+    every descriptor and quantiser, launching nothing on error."""
+    from paper_1606_07414_gb300 import tx16
+
+    E = tx16.TX16_EINVAL
+    qp1 = (tx16.tx16_qparams * 1)(tx16.tx16_qparams(8.0, 16))
+    good = (tx16.tx16_image * 1)(_img(32, 32))
+    f = lib.tx16_codec_batch_static
+    assert f(good, None, -1, qp1, None, None, None) == E
+    big = tx16.TX16_STATIC_MAX_IMAGES + 1
+    assert f((tx16.tx16_image * big)(*[_img(32, 32)] * big), None, big,
+             (tx16.tx16_qparams * big)(*[tx16.tx16_qparams(8.0, 16)] * big), None, None, None) == E
+    assert f(None, None, 1, qp1, None, None, None) == E
+    assert f(good, None, 1, None, None, None, None) == E
+    assert f(good, None, 1, qp1, ctypes.c_void_p(0x20004), None, None) == E  # sse not 8-byte aligned
+    assert f(good, None, 1, qp1, None, ctypes.c_void_p(0x20008), None) == E  # levels not 16-byte aligned
+    assert f((tx16.tx16_image * 1)(_img(30, 32)), None, 1, qp1, None, None, None) == E
+    assert f(good, (tx16.tx16_image * 1)(_img(32, 48)), 1, qp1, None, None, None) == E
+    assert f(good, (tx16.tx16_image * 1)(_img(32, 32, bits=10, pitch=64)), 1, qp1, None, None, None) == E
+    for q, r in [(8.0, 0), (8.0, 257), (float("inf"), 16), (float("nan"), 16)]:
+        assert f(good, None, 1, (tx16.tx16_qparams * 1)(tx16.tx16_qparams(q, r)), None, None, None) == E
+    assert f(good, None, 0, qp1, None, None, None) == tx16.TX16_OK  # empty batch: a no-op
+
+
 def test_build_refuses_flush_to_zero_flags(monkeypatch):
     """The fused kernels' sample rounding goes through subnormal binary32
     values, so extra nvcc flags that flush them are refused before compiling."""

@@ -187,6 +187,8 @@ def check_perfect_reconstruction(o):
         assert np.array_equal(num, 256 * X)
         res = o.codec_image(img, None, 256, bits)
         assert res["sse"] == 0 and res["psnr"] == math.inf
+        res = o.codec_image(img, None, 256, bits, forward="factored")
+        assert res["sse"] == 0 and np.array_equal(res["Y"], Y)
 
 
 def check_dc_only_is_block_mean(o):
