@@ -17,6 +17,8 @@
 // keeps it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "tx16_internal.h"
@@ -39,6 +41,38 @@ struct StaticWorkList {
 };
 
 static __device__ __align__(256) unsigned char g_static_work_list[sizeof(StaticWorkList)];
+
+// The descriptors reach the device array through the parameters of a small
+// kernel launched on the caller's stream (at most kUploadChunk per launch):
+// kernel parameters are copied when the launch is issued, so the host
+// staging below is free again as soon as the call returns and the call never
+// waits for earlier work on the stream (a copy from pageable host memory
+// would).
+constexpr int kUploadChunk = 224;
+
+struct UploadParams {
+  int32_t offset;          // first table entry written
+  int32_t count;           // entries in p
+  int32_t clear;           // 1: also zero the tile counters and sse[0..nsse)
+  int32_t nsse;
+  unsigned long long* sse;  // device, or nullptr
+  StaticWorkList* list;     // device address of g_static_work_list
+  ImgParam p[kUploadChunk];
+};
+static_assert(sizeof(UploadParams) < 32000, "kernel parameters too large");
+static_assert(sizeof(ImgParam) % 4 == 0, "descriptors copied as 32-bit words");
+
+__global__ void static_upload_kernel(const __grid_constant__ UploadParams P) {
+  const unsigned* src = reinterpret_cast<const unsigned*>(P.p);
+  unsigned* dst = reinterpret_cast<unsigned*>(P.list->table + P.offset);
+  const int words = P.count * int(sizeof(ImgParam) / 4);
+  for (int w = int(threadIdx.x); w < words; w += int(blockDim.x)) dst[w] = src[w];
+  if (P.clear) {
+    if (threadIdx.x < unsigned(kStaticRuns)) P.list->counters[threadIdx.x] = 0u;
+    if (P.sse != nullptr)
+      for (int i = int(threadIdx.x); i < P.nsse; i += int(blockDim.x)) P.sse[i] = 0ull;
+  }
+}
 
 std::mutex g_static_mu;                  // one call at a time builds and uploads the list
 StaticWorkList* g_static_addr[64] = {};  // per device: address of g_static_work_list
@@ -110,15 +144,22 @@ extern "C" tx16_status tx16_codec_batch_static(const tx16_image* in, const tx16_
       ++count[c];
     }
   }
-  // upload the list (the host staging array may be reused once this returns:
-  // a copy from pageable memory is staged before the call returns) and clear
-  // what the kernels count from zero
-  if (cudaMemcpyAsync(dev->table, g_host_table, sizeof(ImgParam) * size_t(m), cudaMemcpyHostToDevice, st) !=
-          cudaSuccess ||
-      cudaMemsetAsync(dev->counters, 0, sizeof(dev->counters), st) != cudaSuccess)
-    return TX16_ECUDA;
-  if (sse != nullptr && cudaMemsetAsync(sse, 0, sizeof(uint64_t) * size_t(n), st) != cudaSuccess)
-    return TX16_ECUDA;
+  // upload the list and clear what the kernels count from zero (see
+  // static_upload_kernel)
+  {
+    UploadParams U;
+    U.list = dev;
+    U.sse = reinterpret_cast<unsigned long long*>(sse);
+    U.nsse = n;
+    for (int off = 0; off < m || off == 0; off += kUploadChunk) {
+      U.offset = off;
+      U.count = std::min(kUploadChunk, m - off);
+      U.clear = off == 0 ? 1 : 0;
+      std::memcpy(U.p, g_host_table + off, sizeof(ImgParam) * size_t(U.count));
+      static_upload_kernel<<<1, 256, 0, st>>>(U);
+      if (cudaGetLastError() != cudaSuccess) return TX16_ECUDA;
+    }
+  }
   unsigned long long* s64 = reinterpret_cast<unsigned long long*>(sse);
   for (int c = 0; c < kStaticRuns; ++c) {
     if (count[c] == 0) continue;

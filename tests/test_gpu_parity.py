@@ -264,20 +264,24 @@ def test_wide_and_tall_images(tx):
 
 
 # --------------------------------------------------------------------------
-# Codec without level output (the one-block-per-thread kernel for up to 8
-# kept columns, the pair kernel beyond): several images per launch, tiles
-# that straddle images, and batches large enough that every warp codes
-# tiles of several images in turn.
+# Codec without level output: several images per launch, tiles that straddle
+# images, and batches large enough that every warp codes tiles of several
+# images in turn.  A batch with fewer 32-block warp tiles than the GPU has
+# SMs runs on the two-blocks-per-pair kernel; a larger one, for up to 8 kept
+# columns, on the one-block-per-thread kernel.  `repeat` copies of the set of
+# shapes give both: 1 copy (25 warp tiles) the pair kernel, 20 copies (500
+# warp tiles) the one-block-per-thread kernel.
 # --------------------------------------------------------------------------
 NOLEV_CASES = [(16.0, 8), (None, 8), (16.0, 16), (None, 16), (12.0, 32), (None, 32), (16.0, 64), (8.0, 200)]
 
 
+@pytest.mark.parametrize("repeat", [1, 20])
 @pytest.mark.parametrize("q,r", NOLEV_CASES)
-def test_codec_without_levels_batch(tx, q, r):
+def test_codec_without_levels_batch(tx, q, r, repeat):
     import torch
 
-    shapes = [(16, 16), (80, 272), (48, 528), (16, 512), (160, 640), (32, 32), (32, 48), (64, 16)]
-    imgs = [synth.ar1_image(700 + i + r, h, w, 0.9 + 0.01 * i, 8) for i, (h, w) in enumerate(shapes)]
+    shapes = [(16, 16), (80, 272), (48, 528), (16, 512), (160, 640), (32, 32), (32, 48), (64, 16)] * repeat
+    imgs = [synth.ar1_image(700 + i + r, h, w, 0.9 + 0.01 * (i % 8), 8) for i, (h, w) in enumerate(shapes)]
     keep = [to_dev(im) for im in imgs]
     outs = [empty_like_img(h, w, 8, pad=16) for h, w in shapes]
     sse = torch.full((len(imgs),), -1, dtype=torch.int64, device="cuda")
@@ -375,8 +379,10 @@ def test_codec_16bit_2160p_frame(tx):
 # --------------------------------------------------------------------------
 # Clamping at both ends of the sample range: planes of extreme samples whose
 # zonal reconstructions overshoot far below 0 and above the peak (Gibbs-like
-# ringing), through the one-block-per-thread kernels (no levels, r <= 32),
-# the pair kernel (levels requested, or r > 32) and the 16-bit path
+# ringing), through the one-block-per-thread kernels (no levels, r <= 32, a
+# batch of at least one warp tile per SM: `repeat` = 30 copies of the seven
+# planes, 210 warp tiles), the pair kernel (levels requested, r > 32, or the
+# seven planes alone) and the 16-bit path
 # --------------------------------------------------------------------------
 def _extreme_planes(bits):
     peak = (1 << bits) - 1
@@ -392,13 +398,14 @@ def _extreme_planes(bits):
     return [p.astype(dt) for p in planes]
 
 
-@pytest.mark.parametrize("q,r,levels", [(None, 32, False), (None, 16, False), (64.0, 4, False), (64.0, 16, False),
-                                        (16.0, 32, False), (8.0, 16, True), (64.0, 64, False), (32.0, 256, True),
-                                        (None, 150, True)])
-def test_codec_extreme_planes_clamp(tx, q, r, levels):
+@pytest.mark.parametrize("q,r,levels,repeat", [(None, 32, False, 30), (None, 16, False, 30), (64.0, 4, False, 30),
+                                               (64.0, 16, False, 30), (16.0, 32, False, 30), (64.0, 16, False, 1),
+                                               (8.0, 16, True, 1), (64.0, 64, False, 1), (32.0, 256, True, 1),
+                                               (None, 150, True, 1)])
+def test_codec_extreme_planes_clamp(tx, q, r, levels, repeat):
     import torch
 
-    planes = _extreme_planes(8)
+    planes = _extreme_planes(8) * repeat
     keep = [to_dev(p) for p in planes]
     outs = [empty_like_img(64, 96, 8, pad=16) for _ in planes]
     sse = torch.full((len(planes),), -1, dtype=torch.int64, device="cuda")
