@@ -818,11 +818,12 @@ def _measured_peak():
 
 def _codec_kernel_name(r):
     """The fused kernel the library picks for an 8-bit batch with zone Z_r
-    and no level output (one block per thread up to 8 kept columns)."""
-    for rmax, zone in ((8, "Zone<3,4>"), (16, "Zone<5,6>"), (32, "Zone<7,8>")):
+    and no level output: the one-block-per-thread kernel of the zonal class
+    (index 0..5, r_max 8, 16, 32, 64, 128, 256)."""
+    for c, rmax in enumerate((8, 16, 32, 64, 128, 256)):
         if r <= rmax:
-            return f"tx16::fused_bt_kernel<256, {zone}, DST=true> (one block per thread)"
-    return "tx16::fused_u8_kernel<256, Zone, LEV=false, DST=true> (two blocks per thread pair)"
+            return f"tx16::fused_bt_kernel<256, {c}, DST=true, 1> (one block per thread, class r <= {rmax})"
+    return None
 
 
 def _traffic_per_launch():

@@ -311,8 +311,9 @@ def emit_transposing(w, T, rnd):
         w("  }")
         w("};")
         w("")
-    # forward column pass from the M1 outputs a[0..15]
-    for U in sorted({u for u, _ in ZONES}):
+    # forward column pass from the M1 outputs a[0..15]; every output count
+    # (a column pair keeps the rows of its taller column's zone)
+    for U in range(1, 17):
         net = Net(cse=True)
         a = [net.leaf(i) for i in range(16)]
         b = [a[g] for g in G1]
@@ -338,7 +339,7 @@ def emit_transposing(w, T, rnd):
         w("};")
         w("")
     # inverse column pass with its last butterfly (M1) scalar, into row pairs
-    for U in sorted({u for u, _ in ZONES}):
+    for U in range(1, 17):
         net = Net(cse=True)
         ins = [net.leaf(i) if i < U else ZERO for i in range(16)]
         e = [None] * 16
@@ -374,6 +375,16 @@ def emit_transposing(w, T, rnd):
         w("  }")
         w("};")
         w("")
+    w("// the column-pass networks of a column pair keeping rows u < H")
+    w("template <int H>")
+    w("struct ColNets;")
+    for U in range(1, 17):
+        w(f"template <>")
+        w(f"struct ColNets<{U}> {{")
+        w(f"  using FC = FwdColM{U};")
+        w(f"  using IC = InvColT{U};")
+        w("};")
+    w("")
 
 
 ZONES = [(3, 4), (5, 6), (7, 8), (11, 10), (16, 16)]  # (rows U, columns V) kept

@@ -1,0 +1,13 @@
+// One-block-per-thread codec, zonal class A (r <= 8): the kernels of
+// tx16_fused_bt.cuh instantiated for this class alone, so that the classes
+// compile in parallel.
+#include "tx16_fused_bt.cuh"
+
+namespace tx16 {
+
+template tx16_status bt_batch<0>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
+template tx16_status bt_list<0>(bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
+                                 cudaStream_t);
+template int bt_list_ctas<0>(bool);
+
+}  // namespace tx16

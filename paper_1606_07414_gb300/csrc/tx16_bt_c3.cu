@@ -1,0 +1,13 @@
+// One-block-per-thread codec, zonal class D (r <= 64): the kernels of
+// tx16_fused_bt.cuh instantiated for this class alone, so that the classes
+// compile in parallel.
+#include "tx16_fused_bt.cuh"
+
+namespace tx16 {
+
+template tx16_status bt_batch<3>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
+template tx16_status bt_list<3>(bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
+                                 cudaStream_t);
+template int bt_list_ctas<3>(bool);
+
+}  // namespace tx16

@@ -500,19 +500,26 @@ bool fused_eligible(const ImgParam& p) {
   return bits == 8 && (!(p.flags & kQuantFlag) || p.g[0] * 16.0f >= kFusedMinQ);
 }
 
-// Smallest zone class covering every image of the launch (extents of Z_r).
+// Smallest zonal class covering every image of the launch: class c holds the
+// zones inside Z_rmax(c) (r_max = 8, 16, 32, 64, 128, 256), compared column by
+// column (zig-zag zones nest, so this is the class of the largest r).  The
+// pair kernel codes classes 4 and 5 with the full 16 x 16 networks.
 int fused_zone_class(const ImgParam* imgs, int n) {
-  int U = 0, V = 0;
+  static const struct Heights {
+    uint8_t h[6][16];
+    Heights() {
+      for (int c = 0; c < 6; ++c) zonal_column_heights(bt_class_rmax(c), h[c]);
+    }
+  } H;
+  uint8_t need[16] = {};
   for (int i = 0; i < n; ++i)
-    for (int v = 0; v < 16; ++v)
-      if (imgs[i].colh[v] > 0) {
-        U = std::max(U, int(imgs[i].colh[v]));
-        V = std::max(V, v + 1);
-      }
-  const int cu[4] = {3, 5, 7, 11}, cv[4] = {4, 6, 8, 10};
-  for (int c = 0; c < 4; ++c)
-    if (U <= cu[c] && V <= cv[c]) return c;
-  return 4;
+    for (int v = 0; v < 16; ++v) need[v] = std::max(need[v], imgs[i].colh[v]);
+  for (int c = 0; c < 5; ++c) {
+    bool in = true;
+    for (int v = 0; v < 16; ++v) in = in && need[v] <= H.h[c][v];
+    if (in) return c;
+  }
+  return 5;
 }
 
 tx16_status launch_fused_u8(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,

@@ -73,7 +73,7 @@ void quant_constants(float q, float f[5], float g[5]);
 constexpr float kFusedMinQ = 1.0f / 256.0f;
 tx16_status launch_fused_u8(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                             cudaStream_t stream);
-int fused_zone_class(const ImgParam* imgs, int n);
+int fused_zone_class(const ImgParam* imgs, int n);  // 0..5: r_max 8, 16, 32, 64, 128, 256
 bool fused_eligible(const ImgParam& p);  // 8-bit samples and q >= kFusedMinQ (or no q)
 // Work-list launch: descriptors in device memory (tile0 relative to the list,
 // ascending), tiles claimed `chunk` at a time from *counter (zeroed before).
@@ -90,6 +90,8 @@ tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, uns
 // of 32 blocks (bt_warp_tiles), relative to the list and ascending; warps
 // claim `chunk` tiles at a time from *counter (zeroed before the launch).
 int bt_warp_tiles(int nblk);
+int bt_class_rmax(int zone);           // largest r of zonal class `zone` (0..5)
+int fused_bt_warps_per_cta(int zone);  // warps per CTA of the one-block-per-thread kernel
 tx16_status launch_fused_bt_list(int zone, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter,
                                  int chunk, int ctas_per_sm, unsigned long long* sse, cudaStream_t stream);
 int fused_bt_list_max_ctas(int zone, bool dst);  // resident CTAs per SM

@@ -1407,6 +1407,46 @@ struct FwdRowT16 {
   }
 };
 
+// forward column pass after M1 (inputs a = M1 x), outputs u < 1:
+// n[u] = sign[u] * (T x)[u]; 7 pair additions
+struct FwdColM1 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfffeu, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[1]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    n[0] = t40;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 2:
+// n[u] = sign[u] * (T x)[u]; 14 pair additions
+struct FwdColM2 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfffcu, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[2]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+  }
+};
+
 // forward column pass after M1 (inputs a = M1 x), outputs u < 3:
 // n[u] = sign[u] * (T x)[u]; 15 pair additions
 struct FwdColM3 {
@@ -1430,6 +1470,34 @@ struct FwdColM3 {
     n[0] = t40;
     n[1] = t42;
     n[2] = t23;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 4:
+// n[u] = sign[u] * (T x)[u]; 16 pair additions
+struct FwdColM4 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0008u, 0xfff0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[4]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
   }
 };
 
@@ -1460,6 +1528,38 @@ struct FwdColM5 {
     n[2] = t23;
     n[3] = t39;
     n[4] = t35;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 6:
+// n[u] = sign[u] * (T x)[u]; 18 pair additions
+struct FwdColM6 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0008u, 0xffc0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[6]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
   }
 };
 
@@ -1494,6 +1594,120 @@ struct FwdColM7 {
     n[4] = t35;
     n[5] = t43;
     n[6] = t19;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 8:
+// n[u] = sign[u] * (T x)[u]; 20 pair additions
+struct FwdColM8 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0048u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[8]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 9:
+// n[u] = sign[u] * (T x)[u]; 21 pair additions
+struct FwdColM9 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0048u, 0xfe00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[9]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 10:
+// n[u] = sign[u] * (T x)[u]; 22 pair additions
+struct FwdColM10 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0048u, 0xfc00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[10]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t27 = sub2(a[12], a[13]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+    n[9] = t27;
   }
 };
 
@@ -1536,6 +1750,194 @@ struct FwdColM11 {
     n[8] = t41;
     n[9] = t27;
     n[10] = t21;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 12:
+// n[u] = sign[u] * (T x)[u]; 24 pair additions
+struct FwdColM12 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0c48u, 0xf000u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[12]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t21 = sub2(a[1], a[6]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t27 = sub2(a[12], a[13]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t38 = sub2(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+    n[9] = t27;
+    n[10] = t21;
+    n[11] = t38;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 13:
+// n[u] = sign[u] * (T x)[u]; 25 pair additions
+struct FwdColM13 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x1c48u, 0xe000u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[13]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t21 = sub2(a[1], a[6]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t27 = sub2(a[12], a[13]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t34 = sub2(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t38 = sub2(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+    n[9] = t27;
+    n[10] = t21;
+    n[11] = t38;
+    n[12] = t34;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 14:
+// n[u] = sign[u] * (T x)[u]; 26 pair additions
+struct FwdColM14 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x3c48u, 0xc000u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[14]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t21 = sub2(a[1], a[6]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t25 = sub2(a[14], a[15]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t27 = sub2(a[12], a[13]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t34 = sub2(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t38 = sub2(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+    n[9] = t27;
+    n[10] = t21;
+    n[11] = t38;
+    n[12] = t34;
+    n[13] = t25;
+  }
+};
+
+// forward column pass after M1 (inputs a = M1 x), outputs u < 15:
+// n[u] = sign[u] * (T x)[u]; 27 pair additions
+struct FwdColM15 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x7c48u, 0x8000u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[16], float2 (&n)[15]) {
+    const float2 t16 = __fadd2_rn(a[0], a[7]);
+    const float2 t17 = sub2(a[3], a[4]);
+    const float2 t18 = __fadd2_rn(a[1], a[6]);
+    const float2 t19 = sub2(a[2], a[5]);
+    const float2 t20 = __fadd2_rn(a[2], a[5]);
+    const float2 t21 = sub2(a[1], a[6]);
+    const float2 t22 = __fadd2_rn(a[3], a[4]);
+    const float2 t23 = sub2(a[0], a[7]);
+    const float2 t24 = __fadd2_rn(a[8], a[9]);
+    const float2 t25 = sub2(a[14], a[15]);
+    const float2 t26 = __fadd2_rn(a[11], a[10]);
+    const float2 t27 = sub2(a[12], a[13]);
+    const float2 t28 = __fadd2_rn(a[12], a[13]);
+    const float2 t30 = __fadd2_rn(a[15], a[14]);
+    const float2 t31 = sub2(a[8], a[9]);
+    const float2 t32 = __fadd2_rn(t16, t22);
+    const float2 t33 = __fadd2_rn(t18, t20);
+    const float2 t34 = sub2(t18, t20);
+    const float2 t35 = sub2(t16, t22);
+    const float2 t36 = __fadd2_rn(t24, t30);
+    const float2 t37 = __fadd2_rn(t26, t28);
+    const float2 t38 = sub2(t26, t28);
+    const float2 t39 = sub2(t24, t30);
+    const float2 t40 = __fadd2_rn(t32, t33);
+    const float2 t41 = sub2(t32, t33);
+    const float2 t42 = __fadd2_rn(t36, t37);
+    const float2 t43 = sub2(t36, t37);
+    n[0] = t40;
+    n[1] = t42;
+    n[2] = t23;
+    n[3] = t39;
+    n[4] = t35;
+    n[5] = t43;
+    n[6] = t19;
+    n[7] = t31;
+    n[8] = t41;
+    n[9] = t27;
+    n[10] = t21;
+    n[11] = t38;
+    n[12] = t34;
+    n[13] = t25;
+    n[14] = t17;
   }
 };
 
@@ -1591,6 +1993,58 @@ struct FwdColM16 {
   }
 };
 
+// inverse column pass, inputs u < 1 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 0 pair additions and 0 scalar additions
+struct InvColT1 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    Z[0][0] = make_float2(w[0].x, w[0].x);
+    Z[0][1] = make_float2(w[0].y, w[0].y);
+    Z[1][0] = make_float2(w[0].x, w[0].x);
+    Z[1][1] = make_float2(w[0].y, w[0].y);
+    Z[2][0] = make_float2(w[0].x, w[0].x);
+    Z[2][1] = make_float2(w[0].y, w[0].y);
+    Z[3][0] = make_float2(w[0].x, w[0].x);
+    Z[3][1] = make_float2(w[0].y, w[0].y);
+    Z[4][0] = make_float2(w[0].x, w[0].x);
+    Z[4][1] = make_float2(w[0].y, w[0].y);
+    Z[5][0] = make_float2(w[0].x, w[0].x);
+    Z[5][1] = make_float2(w[0].y, w[0].y);
+    Z[6][0] = make_float2(w[0].x, w[0].x);
+    Z[6][1] = make_float2(w[0].y, w[0].y);
+    Z[7][0] = make_float2(w[0].x, w[0].x);
+    Z[7][1] = make_float2(w[0].y, w[0].y);
+  }
+};
+
+// inverse column pass, inputs u < 2 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 0 pair additions and 4 scalar additions
+struct InvColT2 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float s0 = __fadd_rn(w[0].x, w[1].x);
+    const float s1 = __fadd_rn(-w[1].x, w[0].x);
+    const float s2 = __fadd_rn(w[0].y, w[1].y);
+    const float s3 = __fadd_rn(-w[1].y, w[0].y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s0, s1);
+    Z[1][1] = make_float2(s2, s3);
+    Z[2][0] = make_float2(s0, s1);
+    Z[2][1] = make_float2(s2, s3);
+    Z[3][0] = make_float2(s0, s1);
+    Z[3][1] = make_float2(s2, s3);
+    Z[4][0] = make_float2(s0, s1);
+    Z[4][1] = make_float2(s2, s3);
+    Z[5][0] = make_float2(s0, s1);
+    Z[5][1] = make_float2(s2, s3);
+    Z[6][0] = make_float2(s0, s1);
+    Z[6][1] = make_float2(s2, s3);
+    Z[7][0] = make_float2(s0, s1);
+    Z[7][1] = make_float2(s2, s3);
+  }
+};
+
 // inverse column pass, inputs u < 3 (true values; lanes: columns 2c, 2c+1), with its
 // last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
 // 2 pair additions and 12 scalar additions
@@ -1629,6 +2083,54 @@ struct InvColT3 {
   }
 };
 
+// inverse column pass, inputs u < 4 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 4 pair additions and 20 scalar additions
+struct InvColT4 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t4 = sub2(w[1], w[3]);
+    const float2 t5 = __fadd2_rn(w[1], w[3]);
+    const float2 t6 = __fadd2_rn(w[0], w[2]);
+    const float2 t7 = sub2(w[0], w[2]);
+    const float s0 = __fadd_rn(t5.x, t6.x);
+    const float s1 = __fadd_rn(-t5.x, t6.x);
+    const float s2 = __fadd_rn(t5.y, t6.y);
+    const float s3 = __fadd_rn(-t5.y, t6.y);
+    const float s4 = __fadd_rn(t5.x, w[0].x);
+    const float s5 = __fadd_rn(-t5.x, w[0].x);
+    const float s6 = __fadd_rn(t5.y, w[0].y);
+    const float s7 = __fadd_rn(-t5.y, w[0].y);
+    const float s8 = __fadd_rn(w[0].x, w[1].x);
+    const float s9 = __fadd_rn(-w[1].x, w[0].x);
+    const float s10 = __fadd_rn(w[0].y, w[1].y);
+    const float s11 = __fadd_rn(-w[1].y, w[0].y);
+    const float s12 = __fadd_rn(t4.x, w[0].x);
+    const float s13 = __fadd_rn(-t4.x, w[0].x);
+    const float s14 = __fadd_rn(t4.y, w[0].y);
+    const float s15 = __fadd_rn(-t4.y, w[0].y);
+    const float s16 = __fadd_rn(t4.x, t7.x);
+    const float s17 = __fadd_rn(-t4.x, t7.x);
+    const float s18 = __fadd_rn(t4.y, t7.y);
+    const float s19 = __fadd_rn(-t4.y, t7.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s8, s9);
+    Z[3][1] = make_float2(s10, s11);
+    Z[4][0] = make_float2(s8, s9);
+    Z[4][1] = make_float2(s10, s11);
+    Z[5][0] = make_float2(s8, s9);
+    Z[5][1] = make_float2(s10, s11);
+    Z[6][0] = make_float2(s12, s13);
+    Z[6][1] = make_float2(s14, s15);
+    Z[7][0] = make_float2(s16, s17);
+    Z[7][1] = make_float2(s18, s19);
+  }
+};
+
 // inverse column pass, inputs u < 5 (true values; lanes: columns 2c, 2c+1), with its
 // last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
 // 6 pair additions and 24 scalar additions
@@ -1664,6 +2166,62 @@ struct InvColT5 {
     const float s21 = __fadd_rn(-t10.x, -t7.x);
     const float s22 = __fadd_rn(-t10.y, t7.y);
     const float s23 = __fadd_rn(-t10.y, -t7.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s12, s13);
+    Z[4][1] = make_float2(s14, s15);
+    Z[5][0] = make_float2(s8, s9);
+    Z[5][1] = make_float2(s10, s11);
+    Z[6][0] = make_float2(s16, s17);
+    Z[6][1] = make_float2(s18, s19);
+    Z[7][0] = make_float2(s20, s21);
+    Z[7][1] = make_float2(s22, s23);
+  }
+};
+
+// inverse column pass, inputs u < 6 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 8 pair additions and 24 scalar additions
+struct InvColT6 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t6 = __fadd2_rn(w[1], w[5]);
+    const float2 t7 = sub2(w[1], w[5]);
+    const float2 t8 = __fadd2_rn(w[0], w[4]);
+    const float2 t9 = sub2(w[0], w[4]);
+    const float2 t10 = sub2(w[3], t6);
+    const float2 t11 = __fadd2_rn(t6, w[3]);
+    const float2 t12 = __fadd2_rn(t8, w[2]);
+    const float2 t13 = sub2(w[2], t8);
+    const float s0 = __fadd_rn(t11.x, t12.x);
+    const float s1 = __fadd_rn(-t11.x, t12.x);
+    const float s2 = __fadd_rn(t11.y, t12.y);
+    const float s3 = __fadd_rn(-t11.y, t12.y);
+    const float s4 = __fadd_rn(t11.x, w[0].x);
+    const float s5 = __fadd_rn(-t11.x, w[0].x);
+    const float s6 = __fadd_rn(t11.y, w[0].y);
+    const float s7 = __fadd_rn(-t11.y, w[0].y);
+    const float s8 = __fadd_rn(t7.x, w[0].x);
+    const float s9 = __fadd_rn(-t7.x, w[0].x);
+    const float s10 = __fadd_rn(t7.y, w[0].y);
+    const float s11 = __fadd_rn(-t7.y, w[0].y);
+    const float s12 = __fadd_rn(t7.x, t9.x);
+    const float s13 = __fadd_rn(-t7.x, t9.x);
+    const float s14 = __fadd_rn(t7.y, t9.y);
+    const float s15 = __fadd_rn(-t7.y, t9.y);
+    const float s16 = __fadd_rn(-t10.x, w[0].x);
+    const float s17 = __fadd_rn(t10.x, w[0].x);
+    const float s18 = __fadd_rn(-t10.y, w[0].y);
+    const float s19 = __fadd_rn(t10.y, w[0].y);
+    const float s20 = __fadd_rn(-t10.x, -t13.x);
+    const float s21 = __fadd_rn(-t13.x, t10.x);
+    const float s22 = __fadd_rn(-t10.y, -t13.y);
+    const float s23 = __fadd_rn(-t13.y, t10.y);
     Z[0][0] = make_float2(s0, s1);
     Z[0][1] = make_float2(s2, s3);
     Z[1][0] = make_float2(s4, s5);
@@ -1745,6 +2303,208 @@ struct InvColT7 {
   }
 };
 
+// inverse column pass, inputs u < 8 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 12 pair additions and 28 scalar additions
+struct InvColT8 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t8 = __fadd2_rn(w[1], w[5]);
+    const float2 t9 = sub2(w[1], w[5]);
+    const float2 t10 = __fadd2_rn(w[0], w[4]);
+    const float2 t11 = sub2(w[0], w[4]);
+    const float2 t12 = sub2(w[3], t8);
+    const float2 t13 = __fadd2_rn(t8, w[3]);
+    const float2 t14 = __fadd2_rn(t10, w[2]);
+    const float2 t15 = __fadd2_rn(w[0], w[6]);
+    const float2 t16 = sub2(w[0], w[6]);
+    const float2 t17 = sub2(w[2], t10);
+    const float2 t18 = sub2(w[7], t12);
+    const float2 t19 = __fadd2_rn(t12, w[7]);
+    const float s0 = __fadd_rn(t13.x, t14.x);
+    const float s1 = __fadd_rn(-t13.x, t14.x);
+    const float s2 = __fadd_rn(t13.y, t14.y);
+    const float s3 = __fadd_rn(-t13.y, t14.y);
+    const float s4 = __fadd_rn(t13.x, w[0].x);
+    const float s5 = __fadd_rn(-t13.x, w[0].x);
+    const float s6 = __fadd_rn(t13.y, w[0].y);
+    const float s7 = __fadd_rn(-t13.y, w[0].y);
+    const float s8 = __fadd_rn(t16.x, t9.x);
+    const float s9 = __fadd_rn(-t9.x, t16.x);
+    const float s10 = __fadd_rn(t16.y, t9.y);
+    const float s11 = __fadd_rn(-t9.y, t16.y);
+    const float s12 = __fadd_rn(t11.x, t9.x);
+    const float s13 = __fadd_rn(-t9.x, t11.x);
+    const float s14 = __fadd_rn(t11.y, t9.y);
+    const float s15 = __fadd_rn(-t9.y, t11.y);
+    const float s16 = __fadd_rn(t15.x, t9.x);
+    const float s17 = __fadd_rn(-t9.x, t15.x);
+    const float s18 = __fadd_rn(t15.y, t9.y);
+    const float s19 = __fadd_rn(-t9.y, t15.y);
+    const float s20 = __fadd_rn(-t19.x, w[0].x);
+    const float s21 = __fadd_rn(t19.x, w[0].x);
+    const float s22 = __fadd_rn(-t19.y, w[0].y);
+    const float s23 = __fadd_rn(t19.y, w[0].y);
+    const float s24 = __fadd_rn(-t17.x, t18.x);
+    const float s25 = __fadd_rn(-t17.x, -t18.x);
+    const float s26 = __fadd_rn(-t17.y, t18.y);
+    const float s27 = __fadd_rn(-t17.y, -t18.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s12, s13);
+    Z[4][1] = make_float2(s14, s15);
+    Z[5][0] = make_float2(s16, s17);
+    Z[5][1] = make_float2(s18, s19);
+    Z[6][0] = make_float2(s20, s21);
+    Z[6][1] = make_float2(s22, s23);
+    Z[7][0] = make_float2(s24, s25);
+    Z[7][1] = make_float2(s26, s27);
+  }
+};
+
+// inverse column pass, inputs u < 9 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 14 pair additions and 28 scalar additions
+struct InvColT9 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t9 = __fadd2_rn(w[0], w[8]);
+    const float2 t10 = sub2(w[0], w[8]);
+    const float2 t11 = __fadd2_rn(w[1], w[5]);
+    const float2 t12 = sub2(w[1], w[5]);
+    const float2 t13 = __fadd2_rn(t9, w[4]);
+    const float2 t14 = sub2(w[4], t9);
+    const float2 t15 = sub2(w[3], t11);
+    const float2 t16 = __fadd2_rn(t11, w[3]);
+    const float2 t17 = __fadd2_rn(t13, w[2]);
+    const float2 t18 = __fadd2_rn(t10, w[6]);
+    const float2 t19 = sub2(w[6], t10);
+    const float2 t20 = sub2(w[2], t13);
+    const float2 t21 = sub2(w[7], t15);
+    const float2 t22 = __fadd2_rn(t15, w[7]);
+    const float s0 = __fadd_rn(t16.x, t17.x);
+    const float s1 = __fadd_rn(-t16.x, t17.x);
+    const float s2 = __fadd_rn(t16.y, t17.y);
+    const float s3 = __fadd_rn(-t16.y, t17.y);
+    const float s4 = __fadd_rn(t10.x, t16.x);
+    const float s5 = __fadd_rn(-t16.x, t10.x);
+    const float s6 = __fadd_rn(t10.y, t16.y);
+    const float s7 = __fadd_rn(-t16.y, t10.y);
+    const float s8 = __fadd_rn(-t19.x, t12.x);
+    const float s9 = __fadd_rn(-t12.x, -t19.x);
+    const float s10 = __fadd_rn(-t19.y, t12.y);
+    const float s11 = __fadd_rn(-t12.y, -t19.y);
+    const float s12 = __fadd_rn(-t14.x, t12.x);
+    const float s13 = __fadd_rn(-t12.x, -t14.x);
+    const float s14 = __fadd_rn(-t14.y, t12.y);
+    const float s15 = __fadd_rn(-t12.y, -t14.y);
+    const float s16 = __fadd_rn(t12.x, t18.x);
+    const float s17 = __fadd_rn(-t12.x, t18.x);
+    const float s18 = __fadd_rn(t12.y, t18.y);
+    const float s19 = __fadd_rn(-t12.y, t18.y);
+    const float s20 = __fadd_rn(-t22.x, t10.x);
+    const float s21 = __fadd_rn(t10.x, t22.x);
+    const float s22 = __fadd_rn(-t22.y, t10.y);
+    const float s23 = __fadd_rn(t10.y, t22.y);
+    const float s24 = __fadd_rn(-t20.x, t21.x);
+    const float s25 = __fadd_rn(-t20.x, -t21.x);
+    const float s26 = __fadd_rn(-t20.y, t21.y);
+    const float s27 = __fadd_rn(-t20.y, -t21.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s12, s13);
+    Z[4][1] = make_float2(s14, s15);
+    Z[5][0] = make_float2(s16, s17);
+    Z[5][1] = make_float2(s18, s19);
+    Z[6][0] = make_float2(s20, s21);
+    Z[6][1] = make_float2(s22, s23);
+    Z[7][0] = make_float2(s24, s25);
+    Z[7][1] = make_float2(s26, s27);
+  }
+};
+
+// inverse column pass, inputs u < 10 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 16 pair additions and 32 scalar additions
+struct InvColT10 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t10 = __fadd2_rn(w[0], w[8]);
+    const float2 t11 = sub2(w[0], w[8]);
+    const float2 t12 = __fadd2_rn(w[1], w[5]);
+    const float2 t13 = sub2(w[1], w[5]);
+    const float2 t14 = __fadd2_rn(t10, w[4]);
+    const float2 t15 = sub2(w[4], t10);
+    const float2 t16 = sub2(w[3], t12);
+    const float2 t17 = __fadd2_rn(t12, w[3]);
+    const float2 t18 = __fadd2_rn(t14, w[2]);
+    const float2 t19 = __fadd2_rn(t11, w[6]);
+    const float2 t20 = sub2(w[6], t11);
+    const float2 t21 = sub2(w[2], t14);
+    const float2 t22 = sub2(w[7], t16);
+    const float2 t23 = sub2(w[9], t13);
+    const float2 t24 = __fadd2_rn(t13, w[9]);
+    const float2 t25 = __fadd2_rn(t16, w[7]);
+    const float s0 = __fadd_rn(t17.x, t18.x);
+    const float s1 = __fadd_rn(-t17.x, t18.x);
+    const float s2 = __fadd_rn(t17.y, t18.y);
+    const float s3 = __fadd_rn(-t17.y, t18.y);
+    const float s4 = __fadd_rn(t11.x, t17.x);
+    const float s5 = __fadd_rn(-t17.x, t11.x);
+    const float s6 = __fadd_rn(t11.y, t17.y);
+    const float s7 = __fadd_rn(-t17.y, t11.y);
+    const float s8 = __fadd_rn(-t20.x, -t23.x);
+    const float s9 = __fadd_rn(-t20.x, t23.x);
+    const float s10 = __fadd_rn(-t20.y, -t23.y);
+    const float s11 = __fadd_rn(-t20.y, t23.y);
+    const float s12 = __fadd_rn(-t15.x, t24.x);
+    const float s13 = __fadd_rn(-t15.x, -t24.x);
+    const float s14 = __fadd_rn(-t15.y, t24.y);
+    const float s15 = __fadd_rn(-t15.y, -t24.y);
+    const float s16 = __fadd_rn(-t15.x, t13.x);
+    const float s17 = __fadd_rn(-t13.x, -t15.x);
+    const float s18 = __fadd_rn(-t15.y, t13.y);
+    const float s19 = __fadd_rn(-t13.y, -t15.y);
+    const float s20 = __fadd_rn(t13.x, t19.x);
+    const float s21 = __fadd_rn(-t13.x, t19.x);
+    const float s22 = __fadd_rn(t13.y, t19.y);
+    const float s23 = __fadd_rn(-t13.y, t19.y);
+    const float s24 = __fadd_rn(-t25.x, t11.x);
+    const float s25 = __fadd_rn(t11.x, t25.x);
+    const float s26 = __fadd_rn(-t25.y, t11.y);
+    const float s27 = __fadd_rn(t11.y, t25.y);
+    const float s28 = __fadd_rn(-t21.x, t22.x);
+    const float s29 = __fadd_rn(-t21.x, -t22.x);
+    const float s30 = __fadd_rn(-t21.y, t22.y);
+    const float s31 = __fadd_rn(-t21.y, -t22.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s16, s17);
+    Z[4][1] = make_float2(s18, s19);
+    Z[5][0] = make_float2(s20, s21);
+    Z[5][1] = make_float2(s22, s23);
+    Z[6][0] = make_float2(s24, s25);
+    Z[6][1] = make_float2(s26, s27);
+    Z[7][0] = make_float2(s28, s29);
+    Z[7][1] = make_float2(s30, s31);
+  }
+};
+
 // inverse column pass, inputs u < 11 (true values; lanes: columns 2c, 2c+1), with its
 // last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
 // 18 pair additions and 32 scalar additions
@@ -1800,6 +2560,322 @@ struct InvColT11 {
     const float s29 = __fadd_rn(-t24.x, -t25.x);
     const float s30 = __fadd_rn(-t24.y, t25.y);
     const float s31 = __fadd_rn(-t24.y, -t25.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s16, s17);
+    Z[4][1] = make_float2(s18, s19);
+    Z[5][0] = make_float2(s20, s21);
+    Z[5][1] = make_float2(s22, s23);
+    Z[6][0] = make_float2(s24, s25);
+    Z[6][1] = make_float2(s26, s27);
+    Z[7][0] = make_float2(s28, s29);
+    Z[7][1] = make_float2(s30, s31);
+  }
+};
+
+// inverse column pass, inputs u < 12 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 20 pair additions and 32 scalar additions
+struct InvColT12 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t12 = __fadd2_rn(w[0], w[8]);
+    const float2 t13 = sub2(w[0], w[8]);
+    const float2 t14 = __fadd2_rn(w[1], w[5]);
+    const float2 t15 = sub2(w[1], w[5]);
+    const float2 t16 = __fadd2_rn(t12, w[4]);
+    const float2 t17 = sub2(w[4], t12);
+    const float2 t18 = sub2(w[3], t14);
+    const float2 t19 = sub2(w[11], t15);
+    const float2 t20 = __fadd2_rn(t15, w[11]);
+    const float2 t21 = __fadd2_rn(t14, w[3]);
+    const float2 t22 = __fadd2_rn(t16, w[2]);
+    const float2 t23 = sub2(w[10], t13);
+    const float2 t24 = __fadd2_rn(t13, w[6]);
+    const float2 t25 = sub2(w[6], t13);
+    const float2 t26 = __fadd2_rn(t13, w[10]);
+    const float2 t27 = sub2(w[2], t16);
+    const float2 t28 = sub2(w[7], t18);
+    const float2 t29 = sub2(w[9], t20);
+    const float2 t30 = __fadd2_rn(t20, w[9]);
+    const float2 t31 = __fadd2_rn(t18, w[7]);
+    const float s0 = __fadd_rn(t21.x, t22.x);
+    const float s1 = __fadd_rn(-t21.x, t22.x);
+    const float s2 = __fadd_rn(t21.y, t22.y);
+    const float s3 = __fadd_rn(-t21.y, t22.y);
+    const float s4 = __fadd_rn(-t23.x, t21.x);
+    const float s5 = __fadd_rn(-t21.x, -t23.x);
+    const float s6 = __fadd_rn(-t23.y, t21.y);
+    const float s7 = __fadd_rn(-t21.y, -t23.y);
+    const float s8 = __fadd_rn(-t25.x, -t29.x);
+    const float s9 = __fadd_rn(-t25.x, t29.x);
+    const float s10 = __fadd_rn(-t25.y, -t29.y);
+    const float s11 = __fadd_rn(-t25.y, t29.y);
+    const float s12 = __fadd_rn(-t17.x, t30.x);
+    const float s13 = __fadd_rn(-t17.x, -t30.x);
+    const float s14 = __fadd_rn(-t17.y, t30.y);
+    const float s15 = __fadd_rn(-t17.y, -t30.y);
+    const float s16 = __fadd_rn(-t17.x, -t19.x);
+    const float s17 = __fadd_rn(-t17.x, t19.x);
+    const float s18 = __fadd_rn(-t17.y, -t19.y);
+    const float s19 = __fadd_rn(-t17.y, t19.y);
+    const float s20 = __fadd_rn(-t19.x, t24.x);
+    const float s21 = __fadd_rn(t19.x, t24.x);
+    const float s22 = __fadd_rn(-t19.y, t24.y);
+    const float s23 = __fadd_rn(t19.y, t24.y);
+    const float s24 = __fadd_rn(-t31.x, t26.x);
+    const float s25 = __fadd_rn(t26.x, t31.x);
+    const float s26 = __fadd_rn(-t31.y, t26.y);
+    const float s27 = __fadd_rn(t26.y, t31.y);
+    const float s28 = __fadd_rn(-t27.x, t28.x);
+    const float s29 = __fadd_rn(-t27.x, -t28.x);
+    const float s30 = __fadd_rn(-t27.y, t28.y);
+    const float s31 = __fadd_rn(-t27.y, -t28.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s16, s17);
+    Z[4][1] = make_float2(s18, s19);
+    Z[5][0] = make_float2(s20, s21);
+    Z[5][1] = make_float2(s22, s23);
+    Z[6][0] = make_float2(s24, s25);
+    Z[6][1] = make_float2(s26, s27);
+    Z[7][0] = make_float2(s28, s29);
+    Z[7][1] = make_float2(s30, s31);
+  }
+};
+
+// inverse column pass, inputs u < 13 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 22 pair additions and 32 scalar additions
+struct InvColT13 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t13 = __fadd2_rn(w[0], w[8]);
+    const float2 t14 = sub2(w[0], w[8]);
+    const float2 t15 = __fadd2_rn(w[1], w[5]);
+    const float2 t16 = sub2(w[1], w[5]);
+    const float2 t17 = __fadd2_rn(t13, w[4]);
+    const float2 t18 = sub2(w[12], t14);
+    const float2 t19 = __fadd2_rn(t14, w[12]);
+    const float2 t20 = sub2(w[4], t13);
+    const float2 t21 = sub2(w[3], t15);
+    const float2 t22 = sub2(w[11], t16);
+    const float2 t23 = __fadd2_rn(t16, w[11]);
+    const float2 t24 = __fadd2_rn(t15, w[3]);
+    const float2 t25 = __fadd2_rn(t17, w[2]);
+    const float2 t26 = __fadd2_rn(t18, w[10]);
+    const float2 t27 = __fadd2_rn(t19, w[6]);
+    const float2 t28 = sub2(w[6], t19);
+    const float2 t29 = sub2(w[10], t18);
+    const float2 t30 = sub2(w[2], t17);
+    const float2 t31 = sub2(w[7], t21);
+    const float2 t32 = sub2(w[9], t23);
+    const float2 t33 = __fadd2_rn(t23, w[9]);
+    const float2 t34 = __fadd2_rn(t21, w[7]);
+    const float s0 = __fadd_rn(t24.x, t25.x);
+    const float s1 = __fadd_rn(-t24.x, t25.x);
+    const float s2 = __fadd_rn(t24.y, t25.y);
+    const float s3 = __fadd_rn(-t24.y, t25.y);
+    const float s4 = __fadd_rn(-t26.x, t24.x);
+    const float s5 = __fadd_rn(-t24.x, -t26.x);
+    const float s6 = __fadd_rn(-t26.y, t24.y);
+    const float s7 = __fadd_rn(-t24.y, -t26.y);
+    const float s8 = __fadd_rn(-t28.x, -t32.x);
+    const float s9 = __fadd_rn(-t28.x, t32.x);
+    const float s10 = __fadd_rn(-t28.y, -t32.y);
+    const float s11 = __fadd_rn(-t28.y, t32.y);
+    const float s12 = __fadd_rn(-t20.x, t33.x);
+    const float s13 = __fadd_rn(-t20.x, -t33.x);
+    const float s14 = __fadd_rn(-t20.y, t33.y);
+    const float s15 = __fadd_rn(-t20.y, -t33.y);
+    const float s16 = __fadd_rn(-t20.x, -t22.x);
+    const float s17 = __fadd_rn(-t20.x, t22.x);
+    const float s18 = __fadd_rn(-t20.y, -t22.y);
+    const float s19 = __fadd_rn(-t20.y, t22.y);
+    const float s20 = __fadd_rn(-t22.x, t27.x);
+    const float s21 = __fadd_rn(t22.x, t27.x);
+    const float s22 = __fadd_rn(-t22.y, t27.y);
+    const float s23 = __fadd_rn(t22.y, t27.y);
+    const float s24 = __fadd_rn(-t34.x, t29.x);
+    const float s25 = __fadd_rn(t29.x, t34.x);
+    const float s26 = __fadd_rn(-t34.y, t29.y);
+    const float s27 = __fadd_rn(t29.y, t34.y);
+    const float s28 = __fadd_rn(-t30.x, t31.x);
+    const float s29 = __fadd_rn(-t30.x, -t31.x);
+    const float s30 = __fadd_rn(-t30.y, t31.y);
+    const float s31 = __fadd_rn(-t30.y, -t31.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s16, s17);
+    Z[4][1] = make_float2(s18, s19);
+    Z[5][0] = make_float2(s20, s21);
+    Z[5][1] = make_float2(s22, s23);
+    Z[6][0] = make_float2(s24, s25);
+    Z[6][1] = make_float2(s26, s27);
+    Z[7][0] = make_float2(s28, s29);
+    Z[7][1] = make_float2(s30, s31);
+  }
+};
+
+// inverse column pass, inputs u < 14 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 24 pair additions and 32 scalar additions
+struct InvColT14 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t14 = __fadd2_rn(w[0], w[8]);
+    const float2 t15 = sub2(w[0], w[8]);
+    const float2 t16 = __fadd2_rn(w[1], w[5]);
+    const float2 t17 = sub2(w[1], w[5]);
+    const float2 t18 = __fadd2_rn(t14, w[4]);
+    const float2 t19 = sub2(w[12], t15);
+    const float2 t20 = __fadd2_rn(t15, w[12]);
+    const float2 t21 = sub2(w[4], t14);
+    const float2 t22 = sub2(w[3], t16);
+    const float2 t23 = sub2(w[11], t17);
+    const float2 t24 = __fadd2_rn(t17, w[11]);
+    const float2 t25 = __fadd2_rn(t16, w[3]);
+    const float2 t26 = __fadd2_rn(t18, w[2]);
+    const float2 t27 = __fadd2_rn(t19, w[10]);
+    const float2 t28 = __fadd2_rn(t20, w[6]);
+    const float2 t29 = sub2(w[6], t20);
+    const float2 t30 = sub2(w[10], t19);
+    const float2 t31 = sub2(w[2], t18);
+    const float2 t32 = sub2(w[7], t22);
+    const float2 t33 = sub2(w[13], t25);
+    const float2 t34 = sub2(w[9], t24);
+    const float2 t35 = __fadd2_rn(t24, w[9]);
+    const float2 t36 = __fadd2_rn(t25, w[13]);
+    const float2 t37 = __fadd2_rn(t22, w[7]);
+    const float s0 = __fadd_rn(t26.x, t36.x);
+    const float s1 = __fadd_rn(-t36.x, t26.x);
+    const float s2 = __fadd_rn(t26.y, t36.y);
+    const float s3 = __fadd_rn(-t36.y, t26.y);
+    const float s4 = __fadd_rn(-t27.x, -t33.x);
+    const float s5 = __fadd_rn(-t27.x, t33.x);
+    const float s6 = __fadd_rn(-t27.y, -t33.y);
+    const float s7 = __fadd_rn(-t27.y, t33.y);
+    const float s8 = __fadd_rn(-t29.x, -t34.x);
+    const float s9 = __fadd_rn(-t29.x, t34.x);
+    const float s10 = __fadd_rn(-t29.y, -t34.y);
+    const float s11 = __fadd_rn(-t29.y, t34.y);
+    const float s12 = __fadd_rn(-t21.x, t35.x);
+    const float s13 = __fadd_rn(-t21.x, -t35.x);
+    const float s14 = __fadd_rn(-t21.y, t35.y);
+    const float s15 = __fadd_rn(-t21.y, -t35.y);
+    const float s16 = __fadd_rn(-t21.x, -t23.x);
+    const float s17 = __fadd_rn(-t21.x, t23.x);
+    const float s18 = __fadd_rn(-t21.y, -t23.y);
+    const float s19 = __fadd_rn(-t21.y, t23.y);
+    const float s20 = __fadd_rn(-t23.x, t28.x);
+    const float s21 = __fadd_rn(t23.x, t28.x);
+    const float s22 = __fadd_rn(-t23.y, t28.y);
+    const float s23 = __fadd_rn(t23.y, t28.y);
+    const float s24 = __fadd_rn(-t37.x, t30.x);
+    const float s25 = __fadd_rn(t30.x, t37.x);
+    const float s26 = __fadd_rn(-t37.y, t30.y);
+    const float s27 = __fadd_rn(t30.y, t37.y);
+    const float s28 = __fadd_rn(-t31.x, t32.x);
+    const float s29 = __fadd_rn(-t31.x, -t32.x);
+    const float s30 = __fadd_rn(-t31.y, t32.y);
+    const float s31 = __fadd_rn(-t31.y, -t32.y);
+    Z[0][0] = make_float2(s0, s1);
+    Z[0][1] = make_float2(s2, s3);
+    Z[1][0] = make_float2(s4, s5);
+    Z[1][1] = make_float2(s6, s7);
+    Z[2][0] = make_float2(s8, s9);
+    Z[2][1] = make_float2(s10, s11);
+    Z[3][0] = make_float2(s12, s13);
+    Z[3][1] = make_float2(s14, s15);
+    Z[4][0] = make_float2(s16, s17);
+    Z[4][1] = make_float2(s18, s19);
+    Z[5][0] = make_float2(s20, s21);
+    Z[5][1] = make_float2(s22, s23);
+    Z[6][0] = make_float2(s24, s25);
+    Z[6][1] = make_float2(s26, s27);
+    Z[7][0] = make_float2(s28, s29);
+    Z[7][1] = make_float2(s30, s31);
+  }
+};
+
+// inverse column pass, inputs u < 15 (true values; lanes: columns 2c, 2c+1), with its
+// last butterfly (M1) done per lane: Z[i][h] = (z_i, z_(15-i)) of lane h, true values;
+// 26 pair additions and 32 scalar additions
+struct InvColT15 {
+  __device__ static __forceinline__ void run(const float2 (&w)[16], float2 (&Z)[8][2]) {
+    const float2 t15 = __fadd2_rn(w[0], w[8]);
+    const float2 t16 = sub2(w[0], w[8]);
+    const float2 t17 = __fadd2_rn(w[1], w[5]);
+    const float2 t18 = sub2(w[1], w[5]);
+    const float2 t19 = __fadd2_rn(t15, w[4]);
+    const float2 t20 = sub2(w[12], t16);
+    const float2 t21 = __fadd2_rn(t16, w[12]);
+    const float2 t22 = sub2(w[4], t15);
+    const float2 t23 = sub2(w[3], t17);
+    const float2 t24 = sub2(w[11], t18);
+    const float2 t25 = __fadd2_rn(t18, w[11]);
+    const float2 t26 = __fadd2_rn(t17, w[3]);
+    const float2 t27 = __fadd2_rn(t19, w[2]);
+    const float2 t28 = sub2(w[14], t22);
+    const float2 t29 = __fadd2_rn(t20, w[10]);
+    const float2 t30 = __fadd2_rn(t21, w[6]);
+    const float2 t31 = sub2(w[6], t21);
+    const float2 t32 = sub2(w[10], t20);
+    const float2 t33 = __fadd2_rn(t22, w[14]);
+    const float2 t34 = sub2(w[2], t19);
+    const float2 t35 = sub2(w[7], t23);
+    const float2 t36 = sub2(w[13], t26);
+    const float2 t37 = sub2(w[9], t25);
+    const float2 t38 = __fadd2_rn(t25, w[9]);
+    const float2 t39 = __fadd2_rn(t26, w[13]);
+    const float2 t40 = __fadd2_rn(t23, w[7]);
+    const float s0 = __fadd_rn(t27.x, t39.x);
+    const float s1 = __fadd_rn(-t39.x, t27.x);
+    const float s2 = __fadd_rn(t27.y, t39.y);
+    const float s3 = __fadd_rn(-t39.y, t27.y);
+    const float s4 = __fadd_rn(-t29.x, -t36.x);
+    const float s5 = __fadd_rn(-t29.x, t36.x);
+    const float s6 = __fadd_rn(-t29.y, -t36.y);
+    const float s7 = __fadd_rn(-t29.y, t36.y);
+    const float s8 = __fadd_rn(-t31.x, -t37.x);
+    const float s9 = __fadd_rn(-t31.x, t37.x);
+    const float s10 = __fadd_rn(-t31.y, -t37.y);
+    const float s11 = __fadd_rn(-t31.y, t37.y);
+    const float s12 = __fadd_rn(-t33.x, t38.x);
+    const float s13 = __fadd_rn(-t33.x, -t38.x);
+    const float s14 = __fadd_rn(-t33.y, t38.y);
+    const float s15 = __fadd_rn(-t33.y, -t38.y);
+    const float s16 = __fadd_rn(-t24.x, t28.x);
+    const float s17 = __fadd_rn(t24.x, t28.x);
+    const float s18 = __fadd_rn(-t24.y, t28.y);
+    const float s19 = __fadd_rn(t24.y, t28.y);
+    const float s20 = __fadd_rn(-t24.x, t30.x);
+    const float s21 = __fadd_rn(t24.x, t30.x);
+    const float s22 = __fadd_rn(-t24.y, t30.y);
+    const float s23 = __fadd_rn(t24.y, t30.y);
+    const float s24 = __fadd_rn(-t40.x, t32.x);
+    const float s25 = __fadd_rn(t32.x, t40.x);
+    const float s26 = __fadd_rn(-t40.y, t32.y);
+    const float s27 = __fadd_rn(t32.y, t40.y);
+    const float s28 = __fadd_rn(-t34.x, t35.x);
+    const float s29 = __fadd_rn(-t34.x, -t35.x);
+    const float s30 = __fadd_rn(-t34.y, t35.y);
+    const float s31 = __fadd_rn(-t34.y, -t35.y);
     Z[0][0] = make_float2(s0, s1);
     Z[0][1] = make_float2(s2, s3);
     Z[1][0] = make_float2(s4, s5);
@@ -1901,6 +2977,90 @@ struct InvColT16 {
     Z[7][0] = make_float2(s28, s29);
     Z[7][1] = make_float2(s30, s31);
   }
+};
+
+// the column-pass networks of a column pair keeping rows u < H
+template <int H>
+struct ColNets;
+template <>
+struct ColNets<1> {
+  using FC = FwdColM1;
+  using IC = InvColT1;
+};
+template <>
+struct ColNets<2> {
+  using FC = FwdColM2;
+  using IC = InvColT2;
+};
+template <>
+struct ColNets<3> {
+  using FC = FwdColM3;
+  using IC = InvColT3;
+};
+template <>
+struct ColNets<4> {
+  using FC = FwdColM4;
+  using IC = InvColT4;
+};
+template <>
+struct ColNets<5> {
+  using FC = FwdColM5;
+  using IC = InvColT5;
+};
+template <>
+struct ColNets<6> {
+  using FC = FwdColM6;
+  using IC = InvColT6;
+};
+template <>
+struct ColNets<7> {
+  using FC = FwdColM7;
+  using IC = InvColT7;
+};
+template <>
+struct ColNets<8> {
+  using FC = FwdColM8;
+  using IC = InvColT8;
+};
+template <>
+struct ColNets<9> {
+  using FC = FwdColM9;
+  using IC = InvColT9;
+};
+template <>
+struct ColNets<10> {
+  using FC = FwdColM10;
+  using IC = InvColT10;
+};
+template <>
+struct ColNets<11> {
+  using FC = FwdColM11;
+  using IC = InvColT11;
+};
+template <>
+struct ColNets<12> {
+  using FC = FwdColM12;
+  using IC = InvColT12;
+};
+template <>
+struct ColNets<13> {
+  using FC = FwdColM13;
+  using IC = InvColT13;
+};
+template <>
+struct ColNets<14> {
+  using FC = FwdColM14;
+  using IC = InvColT14;
+};
+template <>
+struct ColNets<15> {
+  using FC = FwdColM15;
+  using IC = InvColT15;
+};
+template <>
+struct ColNets<16> {
+  using FC = FwdColM16;
+  using IC = InvColT16;
 };
 
 // sign of each output of the (unpruned) forward network: row-pass outputs

@@ -35,7 +35,7 @@ using namespace tx16;
 namespace {
 
 struct ClassRun {
-  int zone;        // 0..4 fused zone class, -1: general kernel (by value, host table)
+  int zone;        // 0..5 fused zone class, -1: general kernel (by value, host table)
   int first;       // first descriptor of the run in the table
   int count;       // descriptors in the run
   int ntiles;      // tiles of the run (16 blocks, pair kernel)
@@ -129,7 +129,7 @@ tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_
   cudaGetDevice(&p->device);
   p->n = n;
   p->has_dst = out != nullptr;
-  for (int c = -1; c <= 4; ++c) {
+  for (int c = -1; c <= 5; ++c) {
     ClassRun r{c, int(p->table.size()), 0, 0, 0, 1, c >= 0 && fused_bt_supports(c, false), 0, 0, 1};
     for (int i = 0; i < n; ++i) {
       if (cls[i] != c) continue;
@@ -150,7 +150,7 @@ tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_
       r.chunk = std::max(1, std::min(16, r.ntiles / std::max(1, ctas * 8)));
     }
     if (r.bt) {
-      const int warps = fused_bt_list_max_ctas(c, p->has_dst) * device_sm_count() * 4;
+      const int warps = fused_bt_list_max_ctas(c, p->has_dst) * device_sm_count() * fused_bt_warps_per_cta(c);
       r.bt_chunk = std::max(1, std::min(16, r.bt_ntiles / std::max(1, warps * 8)));
     }
     p->runs.push_back(r);

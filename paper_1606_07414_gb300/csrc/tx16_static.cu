@@ -33,7 +33,7 @@ using namespace tx16;
 namespace {
 
 constexpr int kStaticMaxImages = 1024;  // TX16_STATIC_MAX_IMAGES in include/tx16.h
-constexpr int kStaticRuns = 6;          // zone classes 0..4 + the general kernel
+constexpr int kStaticRuns = 7;          // zone classes 0..5 + the general kernel
 
 struct StaticWorkList {
   ImgParam table[kStaticMaxImages];
