@@ -284,20 +284,38 @@ tx16_status tx16_plan_run(tx16_plan* plan, uint64_t* sse, int32_t* levels, void*
  * when sse/levels change or after autotuning), replayed on `stream`. */
 tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels, void* stream);
 
-/* Time the schedule candidates (resident CTAs per SM, tiles per claim) of
- * each group on the plan's own data and keep the fastest.  The schedule tuned
- * is that of the kernel a run without levels uses (groups with at most 8 kept
- * columns: one 16x16 block per thread, warps claiming 32-block tiles).  cache_path: a
- * text file of tuned schedules keyed by device, group and size class (read
- * and extended), or NULL.  Synchronous on `stream`; writes the outputs. */
+/* Time the schedule candidates of each group on the plan's own data and keep
+ * the fastest.  The schedule tuned is that of the kernel a run without levels
+ * uses.  For the groups of r <= 64 (one 16x16 block per thread, warps claiming
+ * 32-block tiles) the candidates are the kernel's compiled configurations
+ * (warps per CTA, column pairs parked in shared memory, input stages: see
+ * tx16_plan_variant) and, for each, the resident CTAs per SM and the tiles
+ * per claim; for the others, the CTAs per SM and tiles per claim.
+ * cache_path: a text file of tuned schedules keyed by device, group and size
+ * class (read and extended), or NULL.  Synchronous on `stream`; writes the
+ * outputs. */
 tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* stream);
 
 /* Introspection: number of groups and, for the first max_runs of them, the
- * zone class (0..4, -1 = general kernel), tiles, CTAs per SM (0 = all that
- * fit) and tiles per claim of the kernel a run without levels uses.  Host
- * arrays; any of them may be NULL. */
+ * zone class (0..5 for r <= 8, 16, 32, 64, 128, 256; -1 = general kernel),
+ * tiles, CTAs per SM (0 = all that fit) and tiles per claim of the kernel a
+ * run without levels uses.  Host arrays; any of them may be NULL. */
 tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, int32_t* tiles,
                            int32_t* ctas_per_sm, int32_t* chunk, int32_t max_runs);
+
+/* The compiled configuration group `run` uses (groups of r <= 64): its index
+ * (-1 for a group without configurations), warps per CTA, column pairs parked
+ * in shared memory and input stages.  Any output may be NULL.  TX16_EINVAL
+ * for a run index out of range. */
+tx16_status tx16_plan_variant(const tx16_plan* plan, int32_t run, int32_t* variant, int32_t* warps_per_cta,
+                              int32_t* parked_pairs, int32_t* stages);
+
+/* Pin the schedule of group `run`: configuration index (0 for groups without
+ * configurations), resident CTAs per SM (0 = all that fit) and tiles per
+ * claim (>= 1).  Results do not depend on the schedule.  TX16_EINVAL for a
+ * run of the general kernel or out-of-range values. */
+tx16_status tx16_plan_set_schedule(tx16_plan* plan, int32_t run, int32_t variant, int32_t ctas_per_sm,
+                                   int32_t chunk);
 
 /* Free the plan's device memory and graph.  NULL is ignored. */
 void tx16_plan_destroy(tx16_plan* plan);

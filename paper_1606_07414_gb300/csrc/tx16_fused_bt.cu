@@ -14,18 +14,22 @@ extern template tx16_status bt_batch<0>(bool, int, const ImgParam*, int, unsigne
 extern template tx16_status bt_batch<1>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 extern template tx16_status bt_batch<2>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 extern template tx16_status bt_batch<3>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
-extern template tx16_status bt_list<0>(bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
-                                       cudaStream_t);
-extern template tx16_status bt_list<1>(bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
-                                       cudaStream_t);
-extern template tx16_status bt_list<2>(bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
-                                       cudaStream_t);
-extern template tx16_status bt_list<3>(bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
-                                       cudaStream_t);
-extern template int bt_list_ctas<0>(bool);
-extern template int bt_list_ctas<1>(bool);
-extern template int bt_list_ctas<2>(bool);
-extern template int bt_list_ctas<3>(bool);
+extern template tx16_status bt_list<0>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
+                                       unsigned long long*, cudaStream_t);
+extern template tx16_status bt_list<1>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
+                                       unsigned long long*, cudaStream_t);
+extern template tx16_status bt_list<2>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
+                                       unsigned long long*, cudaStream_t);
+extern template tx16_status bt_list<3>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
+                                       unsigned long long*, cudaStream_t);
+extern template int bt_list_ctas<0>(int, bool);
+extern template void bt_variant_info<0>(int, int*, int*, int*);
+extern template int bt_list_ctas<1>(int, bool);
+extern template void bt_variant_info<1>(int, int*, int*, int*);
+extern template int bt_list_ctas<2>(int, bool);
+extern template void bt_variant_info<2>(int, int*, int*, int*);
+extern template int bt_list_ctas<3>(int, bool);
+extern template void bt_variant_info<3>(int, int*, int*, int*);
 
 // Zonal classes routed to this kernel for 8-bit samples (bit c for class c;
 // compile-time tunable): A..D.  Classes E and F (r > 64) measured slower here
@@ -64,24 +68,37 @@ int fused_bt_warps_per_cta(int zone) {
   }
 }
 
-tx16_status launch_fused_bt_list(int zone, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter,
-                                 int chunk, int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
+tx16_status launch_fused_bt_list(int zone, int variant, bool dst, const ImgParam* d_imgs, int nimg, int ntiles,
+                                 unsigned* counter, int chunk, int ctas_per_sm, unsigned long long* sse,
+                                 cudaStream_t stream) {
   switch (zone) {
-    case 0: return bt_list<0>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
-    case 1: return bt_list<1>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
-    case 2: return bt_list<2>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
-    case 3: return bt_list<3>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 0: return bt_list<0>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 1: return bt_list<1>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 2: return bt_list<2>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 3: return bt_list<3>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
     default: return TX16_EINVAL;
   }
 }
 
-int fused_bt_list_max_ctas(int zone, bool dst) {
+int fused_bt_list_max_ctas(int zone, int variant, bool dst) {
   switch (zone) {
-    case 0: return bt_list_ctas<0>(dst);
-    case 1: return bt_list_ctas<1>(dst);
-    case 2: return bt_list_ctas<2>(dst);
-    case 3: return bt_list_ctas<3>(dst);
+    case 0: return bt_list_ctas<0>(variant, dst);
+    case 1: return bt_list_ctas<1>(variant, dst);
+    case 2: return bt_list_ctas<2>(variant, dst);
+    case 3: return bt_list_ctas<3>(variant, dst);
     default: return 0;
+  }
+}
+
+int fused_bt_variants(int zone) { return fused_bt_supports(zone, false) ? kBtVariants : 0; }
+
+void fused_bt_variant_info(int zone, int variant, int* warps, int* park, int* stages) {
+  switch (zone) {
+    case 0: bt_variant_info<0>(variant, warps, park, stages); break;
+    case 1: bt_variant_info<1>(variant, warps, park, stages); break;
+    case 2: bt_variant_info<2>(variant, warps, park, stages); break;
+    case 3: bt_variant_info<3>(variant, warps, park, stages); break;
+    default: *warps = *park = *stages = 0; break;
   }
 }
 

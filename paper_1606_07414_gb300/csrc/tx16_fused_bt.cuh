@@ -278,49 +278,93 @@ __device__ __forceinline__ void st_pair_cs(void* a, uint4 va, void* b, uint4 vb,
       : "memory");
 }
 
-// Warps per CTA: the class's setting for 8-bit samples, TX16_BT16_WARPS for
-// 16-bit samples (classes A..C; smaller CTAs fit more warps beside the wider
-// staging).
+// Alternative configurations of each class's work-list kernel, timed against
+// the default (variant 0, the settings above) by the plan autotuner: warps
+// per CTA, resident CTAs per SM, parked column pairs, input stages.
+template <int C, int VAR>
+struct BtAlt;
+template <>
+struct BtAlt<0, 1> {
+  static constexpr int kWarps = 1, kMinCtas = 16, kPark = 1, kStages = 1;
+};
+template <>
+struct BtAlt<0, 2> {
+  static constexpr int kWarps = 2, kMinCtas = 5, kPark = 1, kStages = 2;
+};
+template <>
+struct BtAlt<1, 1> {
+  static constexpr int kWarps = 4, kMinCtas = 4, kPark = 1, kStages = 1;
+};
+template <>
+struct BtAlt<1, 2> {
+  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 1, kStages = 2;
+};
+template <>
+struct BtAlt<2, 1> {
+  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 2, kStages = 1;
+};
+template <>
+struct BtAlt<2, 2> {
+  static constexpr int kWarps = 2, kMinCtas = 4, kPark = 2, kStages = 2;
+};
+template <>
+struct BtAlt<3, 1> {
+  static constexpr int kWarps = 1, kMinCtas = 11, kPark = 3, kStages = 1;
+};
+template <>
+struct BtAlt<3, 2> {
+  static constexpr int kWarps = 4, kMinCtas = 3, kPark = 2, kStages = 1;
+};
+constexpr int kBtVariants = 3;
+
+// Settings of class C, variant VAR, for SB-byte samples.  16-bit samples
+// (classes A..C, variant 0 only): TX16_BT16_WARPS warps per CTA,
+// TX16_BT16_MINCTAS CTAs, one stage, TX16_BT16_PARK_A parked pairs in class A
+// (measured on 3840x2160 10-bit frames: 4499 against 4401 Mblocks/s with one
+// parked) and TX16_BT16_PARK (at most the class's setting) in B and C.
 #ifndef TX16_BT16_WARPS
 #define TX16_BT16_WARPS 4
 #endif
-template <int C, int SB = 1>
-constexpr int bt_warps() { return SB == 1 ? BtLimits<C>::kWarps : TX16_BT16_WARPS; }
-// Input rows: per thread 16 rows of 16 * SB bytes per stage.
-template <int C, int SB = 1>
-constexpr int stage_bytes() { return 16 * 32 * bt_warps<C, SB>() * 16 * SB; }
-// input stages: TX16_BT_STAGES for 8-bit samples; one stage for 16-bit
-// samples (two stages of 32-byte rows would leave one CTA per SM)
-template <int C, int SB = 1>
-constexpr int stages() { return SB == 1 ? TX16_BT_STAGES : 1; }
-// Single-stage refill: bit 0 for 8-bit samples, bit 1 for 16-bit samples.
-// Set: the next tile's rows are fetched pair by pair during the inverse pass
-// ("rolling"); clear: all 16 after the tile.
-#ifndef TX16_BT_ROLLING
-#define TX16_BT_ROLLING 2
+#ifndef TX16_BT16_MINCTAS
+#define TX16_BT16_MINCTAS 2
 #endif
-template <int C, int SB = 1>
-constexpr bool rolling_refill() { return stages<C, SB>() == 1 && ((TX16_BT_ROLLING >> (SB - 1)) & 1) != 0; }
-// column pairs parked in shared memory: the class's setting for 8-bit
-// samples; for 16-bit samples none in class A (TX16_BT16_PARK_A; measured on
-// 3840x2160 10-bit frames: 4499 against 4401 Mblocks/s with one parked) and
-// TX16_BT16_PARK (at most the class's setting) in classes B and C
 #ifndef TX16_BT16_PARK
 #define TX16_BT16_PARK 1
 #endif
 #ifndef TX16_BT16_PARK_A
 #define TX16_BT16_PARK_A 0
 #endif
-template <int C, int SB = 1>
-constexpr int park_pairs() {
-  return SB == 1 ? BtLimits<C>::kPark
-                 : (C == 0 ? TX16_BT16_PARK_A
-                           : (BtLimits<C>::kPark < TX16_BT16_PARK ? BtLimits<C>::kPark : TX16_BT16_PARK));
-}
-template <int C, int SB = 1>
-constexpr int park_bytes() { return park_pairs<C, SB>() * 16 * 32 * bt_warps<C, SB>() * 8; }
-template <int C, int SB = 1>
-constexpr size_t dyn_smem() { return size_t(stages<C, SB>()) * size_t(stage_bytes<C, SB>()) + size_t(park_bytes<C, SB>()); }
+// Single-stage refill: bit 0 for 8-bit samples, bit 1 for 16-bit samples.
+// Set: the next tile's rows are fetched pair by pair during the inverse pass
+// ("rolling"); clear: all 16 after the tile.
+#ifndef TX16_BT_ROLLING
+#define TX16_BT_ROLLING 2
+#endif
+template <int C, int VAR>
+struct BtSel {
+  static constexpr int kWarps = BtAlt<C, VAR>::kWarps, kMinCtas = BtAlt<C, VAR>::kMinCtas,
+                       kPark = BtAlt<C, VAR>::kPark, kStages = BtAlt<C, VAR>::kStages;
+};
+template <int C>
+struct BtSel<C, 0> {
+  static constexpr int kWarps = BtLimits<C>::kWarps, kMinCtas = BtLimits<C>::kMinCtas, kPark = BtLimits<C>::kPark,
+                       kStages = TX16_BT_STAGES;
+};
+template <int C, int VAR, int SB>
+struct BtCfg {
+  static constexpr int kWarps = SB == 1 ? BtSel<C, VAR>::kWarps : TX16_BT16_WARPS;
+  static constexpr int kMinCtas = SB == 1 ? BtSel<C, VAR>::kMinCtas : TX16_BT16_MINCTAS;
+  static constexpr int kPark =
+      SB == 1 ? BtSel<C, VAR>::kPark
+              : (C == 0 ? TX16_BT16_PARK_A : (BtLimits<C>::kPark < TX16_BT16_PARK ? BtLimits<C>::kPark : TX16_BT16_PARK));
+  static constexpr int kStages = SB == 1 ? BtSel<C, VAR>::kStages : 1;
+  static constexpr bool kRolling = kStages == 1 && ((TX16_BT_ROLLING >> (SB - 1)) & 1) != 0;
+  // input rows: per thread 16 rows of 16 SB bytes per stage; parked pairs:
+  // 16 float2 per thread and pair
+  static constexpr int kStageBytes = 16 * 32 * kWarps * 16 * SB;
+  static constexpr int kParkBytes = kPark * 16 * 32 * kWarps * 8;
+  static constexpr size_t kSmem = size_t(kStages) * size_t(kStageBytes) + size_t(kParkBytes);
+};
 
 // f(integral_constant<int, i>) for i = 0 .. N-1 in order (compile-time indices)
 template <class F, int... I>
@@ -480,17 +524,18 @@ __device__ __forceinline__ void fill_consts_t(const ImgParam& I, PairConsts<U, N
   __syncwarp();
 }
 
-template <int C, bool DST, int SB, class Sched>
+template <int C, int VAR, bool DST, int SB, class Sched>
 __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, int nimg, int ntiles,
                                            unsigned long long* sse, Sched& sched) {
   static_assert(SB == 1 || SB == 2, "8- or 16-bit samples");
   using K = BtClass<C>;
   using N = RowNets<K::V>;
-  constexpr int kBtWarps = bt_warps<C, SB>();
+  using Cfg = BtCfg<C, VAR, SB>;
+  constexpr int kBtWarps = Cfg::kWarps;
   constexpr int kBtThreads = 32 * kBtWarps;
-  constexpr int kStageBytes = stage_bytes<C, SB>();
+  constexpr int kStageBytes = Cfg::kStageBytes;
   constexpr int kSlot = kBtThreads * 16;         // bytes of one staged slot
-  constexpr int kPark = park_pairs<C, SB>();     // column pairs parked in shared memory
+  constexpr int kPark = Cfg::kPark;              // column pairs parked in shared memory
   constexpr int kParkStride = kBtThreads * 8;    // bytes of one parked float2 slot
   constexpr int V = K::V;
   constexpr int U = K::U;
@@ -503,13 +548,13 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
   PairConsts<U, NP>& Q = consts[wib];
   int t = sched.first();
   if (t < 0) return;
-  constexpr int kStages = stages<C, SB>();
+  constexpr int kStages = Cfg::kStages;
   static_assert(kStages == 1 || kStages == 2, "one or two input stages");
   // bulk staging: per warp [row][lane][16 SB bytes] (a row of 32 blocks is
   // contiguous, one copy per run of blocks); cp.async staging: per CTA
   // [row][half][thread][16 bytes]
   constexpr bool kBulk = TX16_BT_BULK != 0;
-  constexpr bool kRolling = !kBulk && rolling_refill<C, SB>();
+  constexpr bool kRolling = !kBulk && Cfg::kRolling;
   constexpr int kWarpStage = 16 * 32 * 16 * SB;  // bytes of one warp's stage (bulk layout)
   constexpr int kRowStride = kBulk ? 32 * 16 * SB : SB * kSlot;
   constexpr int kHalfStride = kBulk ? 16 : kSlot;
@@ -810,33 +855,25 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
   if (sse) flush_sse(sse, imgs[k].out_index, acc);
 }
 
-// resident CTAs per SM the registers are budgeted for: the class's setting
-// for 8-bit samples, TX16_BT16_MINCTAS for 16-bit samples (wider staging,
-// more live values in the rounding)
-#ifndef TX16_BT16_MINCTAS
-#define TX16_BT16_MINCTAS 2
-#endif
-template <int C, int SB>
-constexpr int min_ctas() { return SB == 1 ? BtLimits<C>::kMinCtas : TX16_BT16_MINCTAS; }
-
 template <int MAXI, int C, bool DST, int SB>
-__global__ void __launch_bounds__(32 * bt_warps<C, SB>(), min_ctas<C, SB>())
+__global__ void __launch_bounds__(32 * BtCfg<C, 0, SB>::kWarps, BtCfg<C, 0, SB>::kMinCtas)
     fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
-  StaticWarps sched{int(blockIdx.x) * bt_warps<C, SB>() + int(threadIdx.x >> 5),
-                    int(gridDim.x) * bt_warps<C, SB>(), P.ntiles};
-  bt_tiles_t<C, DST, SB>(P.img, P.nimg, P.ntiles, P.sse, sched);
+  StaticWarps sched{int(blockIdx.x) * BtCfg<C, 0, SB>::kWarps + int(threadIdx.x >> 5),
+                    int(gridDim.x) * BtCfg<C, 0, SB>::kWarps, P.ntiles};
+  bt_tiles_t<C, 0, DST, SB>(P.img, P.nimg, P.ntiles, P.sse, sched);
 }
 
-template <int C, bool DST>
-__global__ void __launch_bounds__(32 * BtLimits<C>::kWarps, BtLimits<C>::kMinCtas)
+template <int C, int VAR, bool DST>
+__global__ void __launch_bounds__(32 * BtCfg<C, VAR, 1>::kWarps, BtCfg<C, VAR, 1>::kMinCtas)
     fused_bt_list_kernel(const ImgParam* __restrict__ imgs, int nimg, int ntiles, unsigned* counter, int chunk,
                          unsigned long long* sse) {
   DynamicWarps sched{counter, ntiles, chunk, 0, 0};
-  bt_tiles_t<C, DST, 1>(imgs, nimg, ntiles, sse, sched);
+  bt_tiles_t<C, VAR, DST, 1>(imgs, nimg, ntiles, sse, sched);
 }
 
 template <int MAXI, int C, bool DST, int SB>
 tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
+  using Cfg = BtCfg<C, 0, SB>;
   BatchParams<MAXI> P;
   P.nimg = n;
   P.sse = sse;
@@ -849,22 +886,21 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
     tiles += (imgs[i].nblk + kWarpTile - 1) / kWarpTile;
   }
   P.ntiles = tiles;
-  constexpr int kBtWarps = bt_warps<C, SB>();
-  constexpr int kBtThreads = 32 * kBtWarps;
-  constexpr size_t smem = dyn_smem<C, SB>();
+  constexpr int kBtThreads = 32 * Cfg::kWarps;
   static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
     if (cudaFuncSetAttribute(fused_bt_kernel<MAXI, C, DST, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem)) != cudaSuccess)
+                             int(Cfg::kSmem)) != cudaSuccess)
       return TX16_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_kernel<MAXI, C, DST, SB>, kBtThreads, smem) !=
-            cudaSuccess || o < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_kernel<MAXI, C, DST, SB>, kBtThreads,
+                                                      Cfg::kSmem) != cudaSuccess ||
+        o < 1)
       o = 1;
     occ = o;
   }
-  const int grid = std::max(1, std::min((tiles + kBtWarps - 1) / kBtWarps, occ * device_sm_count()));
-  fused_bt_kernel<MAXI, C, DST, SB><<<grid, kBtThreads, smem, stream>>>(P);
+  const int grid = std::max(1, std::min((tiles + Cfg::kWarps - 1) / Cfg::kWarps, occ * device_sm_count()));
+  fused_bt_kernel<MAXI, C, DST, SB><<<grid, kBtThreads, Cfg::kSmem, stream>>>(P);
   return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
 }
 
@@ -873,53 +909,48 @@ tx16_status launch_bt_dst(bool dst, const ImgParam* imgs, int n, unsigned long l
   return dst ? launch_bt<MAXI, C, true, SB>(imgs, n, sse, stream) : launch_bt<MAXI, C, false, SB>(imgs, n, sse, stream);
 }
 
-template <int C, bool DST>
-tx16_status launch_bt_list(const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter, int chunk,
-                           int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
-  constexpr int kThreadsZ = 32 * BtLimits<C>::kWarps;
-  constexpr size_t smem = dyn_smem<C, 1>();
+template <int C, int VAR, bool DST>
+int bt_list_max_ctas() {
+  using Cfg = BtCfg<C, VAR, 1>;
   static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
-    if (cudaFuncSetAttribute(fused_bt_list_kernel<C, DST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem)) != cudaSuccess)
-      return TX16_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_list_kernel<C, DST>, kThreadsZ, smem) !=
-            cudaSuccess || o < 1)
+    auto k = fused_bt_list_kernel<C, VAR, DST>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::kSmem)) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 32 * Cfg::kWarps, Cfg::kSmem) != cudaSuccess || o < 1)
       o = 1;
     occ = o;
   }
-  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ.load()) : occ.load();
-  const int grid = std::max(1, std::min((ntiles + BtLimits<C>::kWarps - 1) / BtLimits<C>::kWarps,
-                                        per_sm * device_sm_count()));
-  fused_bt_list_kernel<C, DST><<<grid, kThreadsZ, smem, stream>>>(d_imgs, nimg, ntiles, counter, chunk, sse);
+  return occ;
+}
+
+template <int C, int VAR, bool DST>
+tx16_status launch_bt_list(const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter, int chunk,
+                           int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
+  using Cfg = BtCfg<C, VAR, 1>;
+  const int occ = bt_list_max_ctas<C, VAR, DST>();
+  if (occ == 0) return TX16_ECUDA;
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+  const int grid = std::max(1, std::min((ntiles + Cfg::kWarps - 1) / Cfg::kWarps, per_sm * device_sm_count()));
+  fused_bt_list_kernel<C, VAR, DST><<<grid, 32 * Cfg::kWarps, Cfg::kSmem, stream>>>(d_imgs, nimg, ntiles, counter,
+                                                                                    chunk, sse);
   return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
 }
 
-template <int C>
-int bt_list_max_ctas(bool dst) {
-  constexpr size_t smem = dyn_smem<C, 1>();
-  int o = 0;
-  auto k = dst ? fused_bt_list_kernel<C, true> : fused_bt_list_kernel<C, false>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 32 * BtLimits<C>::kWarps, smem) != cudaSuccess || o < 1)
-    o = 1;
-  return o;
-}
-
-template <int C>
+template <int C, int VAR>
 tx16_status launch_bt_list_dst(bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter, int chunk,
                                int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
-  return dst ? launch_bt_list<C, true>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream)
-             : launch_bt_list<C, false>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+  return dst ? launch_bt_list<C, VAR, true>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream)
+             : launch_bt_list<C, VAR, false>(d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
 }
 
 }  // namespace
 
 // Entry points of one class (explicitly instantiated, one translation unit per
 // class: tx16_bt_c<class>.cu).
-// A batch whose descriptors travel in the kernel parameters; SB = 2 (9..12-bit
-// samples) for classes A..C only.
+// A batch whose descriptors travel in the kernel parameters (variant 0); SB =
+// 2 (9..12-bit samples) for classes A..C only.
 template <int C>
 tx16_status bt_batch(bool dst, int sb, const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
   if (sb == 1) {
@@ -932,15 +963,36 @@ tx16_status bt_batch(bool dst, int sb, const ImgParam* imgs, int n, unsigned lon
   }
   return TX16_EINVAL;
 }
-// A work list in device memory (tile0 in warp tiles), tiles claimed `chunk` at a time.
+// A work list in device memory (tile0 in warp tiles), tiles claimed `chunk` at
+// a time, by the kernel of variant `var` (0 .. kBtVariants - 1).
 template <int C>
-tx16_status bt_list(bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter, int chunk,
+tx16_status bt_list(int var, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter, int chunk,
                     int ctas_per_sm, unsigned long long* sse, cudaStream_t stream) {
-  return launch_bt_list_dst<C>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+  switch (var) {
+    case 0: return launch_bt_list_dst<C, 0>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 1: return launch_bt_list_dst<C, 1>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 2: return launch_bt_list_dst<C, 2>(dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    default: return TX16_EINVAL;
+  }
 }
+// resident CTAs per SM of variant `var` (0 if it cannot run)
 template <int C>
-int bt_list_ctas(bool dst) {
-  return bt_list_max_ctas<C>(dst);
+int bt_list_ctas(int var, bool dst) {
+  switch (var) {
+    case 0: return dst ? bt_list_max_ctas<C, 0, true>() : bt_list_max_ctas<C, 0, false>();
+    case 1: return dst ? bt_list_max_ctas<C, 1, true>() : bt_list_max_ctas<C, 1, false>();
+    case 2: return dst ? bt_list_max_ctas<C, 2, true>() : bt_list_max_ctas<C, 2, false>();
+    default: return 0;
+  }
+}
+// warps per CTA, parked column pairs and input stages of variant `var`
+template <int C>
+void bt_variant_info(int var, int* warps, int* park, int* stages) {
+  switch (var) {
+    case 0: *warps = BtSel<C, 0>::kWarps; *park = BtSel<C, 0>::kPark; *stages = BtSel<C, 0>::kStages; break;
+    case 1: *warps = BtSel<C, 1>::kWarps; *park = BtSel<C, 1>::kPark; *stages = BtSel<C, 1>::kStages; break;
+    default: *warps = BtSel<C, 2>::kWarps; *park = BtSel<C, 2>::kPark; *stages = BtSel<C, 2>::kStages; break;
+  }
 }
 
 }  // namespace tx16

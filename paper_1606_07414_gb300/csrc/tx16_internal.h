@@ -89,12 +89,17 @@ tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, uns
 // Its work-list form: descriptors in device memory with tile0 in warp tiles
 // of 32 blocks (bt_warp_tiles), relative to the list and ascending; warps
 // claim `chunk` tiles at a time from *counter (zeroed before the launch).
+// Each class has fused_bt_variants() compiled configurations (variant 0:
+// the default; the plan autotuner times the others).
 int bt_warp_tiles(int nblk);
 int bt_class_rmax(int zone);           // largest r of zonal class `zone` (0..5)
-int fused_bt_warps_per_cta(int zone);  // warps per CTA of the one-block-per-thread kernel
-tx16_status launch_fused_bt_list(int zone, bool dst, const ImgParam* d_imgs, int nimg, int ntiles, unsigned* counter,
-                                 int chunk, int ctas_per_sm, unsigned long long* sse, cudaStream_t stream);
-int fused_bt_list_max_ctas(int zone, bool dst);  // resident CTAs per SM
+int fused_bt_warps_per_cta(int zone);  // warps per CTA of the one-block-per-thread kernel (variant 0)
+int fused_bt_variants(int zone);       // compiled configurations of the work-list kernel (0: none)
+void fused_bt_variant_info(int zone, int variant, int* warps, int* park, int* stages);
+tx16_status launch_fused_bt_list(int zone, int variant, bool dst, const ImgParam* d_imgs, int nimg, int ntiles,
+                                 unsigned* counter, int chunk, int ctas_per_sm, unsigned long long* sse,
+                                 cudaStream_t stream);
+int fused_bt_list_max_ctas(int zone, int variant, bool dst);  // resident CTAs per SM
 // 9..12-bit planes (uint16 samples) with a quantiser of q >= 2^(bits-8)/256:
 // the one-block-per-thread kernel for zonal classes up to 8 kept columns and
 // no levels, the general kernel otherwise.

@@ -45,6 +45,7 @@ struct ClassRun {
   // its own table (tile0 in warp tiles of 32 blocks) and schedule
   bool bt;
   int bt_ntiles, bt_ctas_per_sm, bt_chunk;
+  int bt_variant;  // compiled configuration of that kernel (0: the default)
 };
 
 }  // namespace
@@ -81,8 +82,8 @@ tx16_status run_plan(tx16_plan* p, uint64_t* sse, int32_t* levels, cudaStream_t 
     const ClassRun& r = p->runs[i];
     tx16_status s;
     if (r.zone >= 0 && r.bt && levels == nullptr) {
-      s = launch_fused_bt_list(r.zone, p->has_dst, p->d_bt_table + r.first, r.count, r.bt_ntiles, p->d_counters + i,
-                               r.bt_chunk, r.bt_ctas_per_sm, s64, st);
+      s = launch_fused_bt_list(r.zone, r.bt_variant, p->has_dst, p->d_bt_table + r.first, r.count, r.bt_ntiles,
+                               p->d_counters + i, r.bt_chunk, r.bt_ctas_per_sm, s64, st);
     } else if (r.zone >= 0) {
       s = launch_fused_list(r.zone, levels != nullptr, p->has_dst, p->d_table + r.first, r.count, r.ntiles,
                             p->d_counters + i, r.chunk, r.ctas_per_sm, s64, levels, st);
@@ -130,7 +131,7 @@ tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_
   p->n = n;
   p->has_dst = out != nullptr;
   for (int c = -1; c <= 5; ++c) {
-    ClassRun r{c, int(p->table.size()), 0, 0, 0, 1, c >= 0 && fused_bt_supports(c, false), 0, 0, 1};
+    ClassRun r{c, int(p->table.size()), 0, 0, 0, 1, c >= 0 && fused_bt_supports(c, false), 0, 0, 1, 0};
     for (int i = 0; i < n; ++i) {
       if (cls[i] != c) continue;
       ImgParam q = params[i];
@@ -150,7 +151,7 @@ tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_
       r.chunk = std::max(1, std::min(16, r.ntiles / std::max(1, ctas * 8)));
     }
     if (r.bt) {
-      const int warps = fused_bt_list_max_ctas(c, p->has_dst) * device_sm_count() * fused_bt_warps_per_cta(c);
+      const int warps = fused_bt_list_max_ctas(c, 0, p->has_dst) * device_sm_count() * fused_bt_warps_per_cta(c);
       r.bt_chunk = std::max(1, std::min(16, r.bt_ntiles / std::max(1, warps * 8)));
     }
     p->runs.push_back(r);
@@ -189,7 +190,7 @@ tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels,
     // occupancy queries happen on first use of a kernel: do them before capture
     for (const ClassRun& r : plan->runs) {
       if (r.zone >= 0) fused_list_max_ctas(r.zone, levels != nullptr, plan->has_dst);
-      if (r.bt) fused_bt_list_max_ctas(r.zone, plan->has_dst);
+      if (r.bt) fused_bt_list_max_ctas(r.zone, r.bt_variant, plan->has_dst);
     }
     if (plan->graph != nullptr) {
       cudaGraphExecDestroy(plan->graph);
@@ -252,51 +253,65 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
     const int run_tiles = r.bt ? r.bt_ntiles : r.ntiles;
     bool hit = false;
     for (const std::string& c : cache) {
-      int ctas = 0, chunk = 0;
+      int ctas = 0, chunk = 0, var = 0;
       char k2[320];
-      if (std::sscanf(c.c_str(), "%319s %d %d", k2, &ctas, &chunk) == 3 && std::string(k2) == key) {
+      const int got = std::sscanf(c.c_str(), "%319s %d %d %d", k2, &ctas, &chunk, &var);
+      if (got >= 3 && std::string(k2) == key && (!r.bt || (var >= 0 && var < fused_bt_variants(r.zone)))) {
         run_ctas = ctas;
         run_chunk = chunk;
+        if (r.bt) r.bt_variant = got == 4 ? var : 0;
         hit = true;
       }
     }
     if (hit) continue;
-    const int maxc = r.bt ? fused_bt_list_max_ctas(r.zone, plan->has_dst)
-                          : fused_list_max_ctas(r.zone, false, plan->has_dst);
-    const int claimers_per_cta = r.bt ? 4 : 1;  // warps of a one-block-per-thread CTA claim separately
+    // candidates: each compiled configuration of the kernel (one block per
+    // thread: warps per CTA, parked column pairs, input stages), and for
+    // each its resident CTAs per SM (the most that fit and up to 4 fewer)
+    // and tiles per claim
     float best = 1e30f;
-    int best_ctas = run_ctas, best_chunk = run_chunk;
+    int best_ctas = run_ctas, best_chunk = run_chunk, best_var = r.bt ? r.bt_variant : 0;
+    const int nvar = r.bt ? fused_bt_variants(r.zone) : 1;
     const int chunks[] = {1, 2, 4, 8, 16};
-    for (int ctas = maxc; ctas >= 1 && ctas >= maxc - 4; --ctas) {
-      for (int chunk : chunks) {
-        if (chunk > std::max(1, run_tiles / (ctas * claimers_per_cta * device_sm_count()))) continue;
-        float ms = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
-          if (cudaMemsetAsync(plan->d_counters + i, 0, sizeof(unsigned), st) != cudaSuccess) return TX16_ECUDA;
-          cudaEventRecord(e0, st);
-          const tx16_status ls =
-              r.bt ? launch_fused_bt_list(r.zone, plan->has_dst, plan->d_bt_table + r.first, r.count, r.bt_ntiles,
-                                          plan->d_counters + i, chunk, ctas, nullptr, st)
-                   : launch_fused_list(r.zone, false, plan->has_dst, plan->d_table + r.first, r.count, r.ntiles,
-                                       plan->d_counters + i, chunk, ctas, nullptr, nullptr, st);
-          if (ls != TX16_OK) return TX16_ECUDA;
-          cudaEventRecord(e1, st);
-          if (cudaEventSynchronize(e1) != cudaSuccess) return TX16_ECUDA;
-          float t = 0.f;
-          cudaEventElapsedTime(&t, e0, e1);
-          if (rep > 0) ms += t;  // first repetition warms up
-        }
-        if (ms < best) {
-          best = ms;
-          best_ctas = ctas;
-          best_chunk = chunk;
+    for (int var = 0; var < nvar; ++var) {
+      const int maxc = r.bt ? fused_bt_list_max_ctas(r.zone, var, plan->has_dst)
+                            : fused_list_max_ctas(r.zone, false, plan->has_dst);
+      if (maxc <= 0) continue;
+      int warps = 1, park = 0, stages = 1;
+      if (r.bt) fused_bt_variant_info(r.zone, var, &warps, &park, &stages);
+      const int claimers_per_cta = r.bt ? warps : 1;  // warps of a one-block-per-thread CTA claim separately
+      for (int ctas = maxc; ctas >= 1 && ctas >= maxc - 4; --ctas) {
+        for (int chunk : chunks) {
+          if (chunk > std::max(1, run_tiles / (ctas * claimers_per_cta * device_sm_count()))) continue;
+          float ms = 0.f;
+          for (int rep = 0; rep < 3; ++rep) {
+            if (cudaMemsetAsync(plan->d_counters + i, 0, sizeof(unsigned), st) != cudaSuccess) return TX16_ECUDA;
+            cudaEventRecord(e0, st);
+            const tx16_status ls =
+                r.bt ? launch_fused_bt_list(r.zone, var, plan->has_dst, plan->d_bt_table + r.first, r.count,
+                                            r.bt_ntiles, plan->d_counters + i, chunk, ctas, nullptr, st)
+                     : launch_fused_list(r.zone, false, plan->has_dst, plan->d_table + r.first, r.count, r.ntiles,
+                                         plan->d_counters + i, chunk, ctas, nullptr, nullptr, st);
+            if (ls != TX16_OK) return TX16_ECUDA;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return TX16_ECUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t;  // first repetition warms up
+          }
+          if (ms < best) {
+            best = ms;
+            best_ctas = ctas;
+            best_chunk = chunk;
+            best_var = var;
+          }
         }
       }
     }
     run_ctas = best_ctas;
     run_chunk = best_chunk;
+    if (r.bt) r.bt_variant = best_var;
     char line[400];
-    std::snprintf(line, sizeof line, "%s %d %d\n", key, best_ctas, best_chunk);
+    std::snprintf(line, sizeof line, "%s %d %d %d\n", key, best_ctas, best_chunk, best_var);
     cache.emplace_back(line);
     changed = true;
   }
@@ -326,6 +341,42 @@ tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, 
     if (tiles) tiles[i] = r.bt ? r.bt_ntiles : r.ntiles;
     if (ctas_per_sm) ctas_per_sm[i] = r.bt ? r.bt_ctas_per_sm : r.ctas_per_sm;
     if (chunk) chunk[i] = r.bt ? r.bt_chunk : r.chunk;
+  }
+  return TX16_OK;
+}
+
+tx16_status tx16_plan_variant(const tx16_plan* plan, int32_t run, int32_t* variant, int32_t* warps_per_cta,
+                              int32_t* parked_pairs, int32_t* stages) {
+  if (plan == nullptr || run < 0 || run >= int32_t(plan->runs.size())) return TX16_EINVAL;
+  const ClassRun& r = plan->runs[run];
+  int w = 0, pk = 0, sg = 0;
+  if (r.bt) fused_bt_variant_info(r.zone, r.bt_variant, &w, &pk, &sg);
+  if (variant) *variant = r.bt ? r.bt_variant : -1;
+  if (warps_per_cta) *warps_per_cta = w;
+  if (parked_pairs) *parked_pairs = pk;
+  if (stages) *stages = sg;
+  return TX16_OK;
+}
+
+tx16_status tx16_plan_set_schedule(tx16_plan* plan, int32_t run, int32_t variant, int32_t ctas_per_sm,
+                                   int32_t chunk) {
+  if (plan == nullptr || run < 0 || run >= int32_t(plan->runs.size()) || ctas_per_sm < 0 || chunk < 1)
+    return TX16_EINVAL;
+  ClassRun& r = plan->runs[run];
+  if (r.zone < 0) return TX16_EINVAL;  // the general kernel has no schedule
+  if (r.bt) {
+    if (variant < 0 || variant >= fused_bt_variants(r.zone)) return TX16_EINVAL;
+    r.bt_variant = variant;
+    r.bt_ctas_per_sm = ctas_per_sm;
+    r.bt_chunk = chunk;
+  } else {
+    if (variant != 0) return TX16_EINVAL;
+    r.ctas_per_sm = ctas_per_sm;
+    r.chunk = chunk;
+  }
+  if (plan->graph != nullptr) {  // schedule changed: re-capture on next graph run
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
   }
   return TX16_OK;
 }

@@ -58,6 +58,9 @@ _SIGNATURES = {
     "tx16_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "tx16_plan_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    "tx16_plan_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32]),
     "tx16_plan_destroy": (None, [ctypes.c_void_p]),
     "tx16_zonal_sweep": (ctypes.c_int, [ctypes.POINTER(tx16_image), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
@@ -310,7 +313,18 @@ class Plan:
         m = 8
         z, t, c, k = [(ctypes.c_int32 * m)() for _ in range(4)]
         _check(lib.tx16_plan_info(self.handle, ctypes.byref(n), z, t, c, k, m), "tx16_plan_info")
-        return [{"zone": z[i], "tiles": t[i], "ctas_per_sm": c[i], "chunk": k[i]} for i in range(min(n.value, m))]
+        out = []
+        for i in range(min(n.value, m)):
+            v, w, p, s = [ctypes.c_int32() for _ in range(4)]
+            _check(lib.tx16_plan_variant(self.handle, i, ctypes.byref(v), ctypes.byref(w), ctypes.byref(p),
+                                         ctypes.byref(s)), "tx16_plan_variant")
+            out.append({"zone": z[i], "tiles": t[i], "ctas_per_sm": c[i], "chunk": k[i], "variant": v.value,
+                        "warps_per_cta": w.value, "parked_pairs": p.value, "stages": s.value})
+        return out
+
+    def set_schedule(self, run: int, variant: int, ctas_per_sm: int = 0, chunk: int = 1) -> None:
+        _check(load().tx16_plan_set_schedule(self.handle, int(run), int(variant), int(ctas_per_sm), int(chunk)),
+               "tx16_plan_set_schedule")
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -113,3 +113,57 @@ def test_plan_mixed_depths_and_tiny_steps(tx):
         assert np.array_equal(O.image_to_blocks(rec.astype(np.int64)), ref["recon"]), i
         assert int(sse[i].item()) == O.sse(im, rec), i
     plan.close()
+
+
+def test_every_compiled_configuration_gives_identical_results(tx):
+    """Each group of r <= 64 has several compiled configurations of the
+    one-block-per-thread kernel (warps per CTA, parked column pairs, input
+    stages).  Pinned one by one, with different CTAs per SM and tiles per
+    claim, every configuration writes the same samples and squared errors
+    (and the first run matches the oracle)."""
+    import torch
+
+    Hs, Ws = synth.uneven_sizes(31, 36, 16, 720)
+    rs = [4, 8, 16, 32, 64, 24, 48, 12]
+    qs = [16.0, None, 8.0, 32.0]
+    imgs = [synth.ar1_image(3100 + i, int(Hs[i]), int(Ws[i]), 0.85 + 0.02 * (i % 6), 8) for i in range(len(Hs))]
+    qp = [(qs[i % 4], rs[i % 8]) for i in range(len(imgs))]
+    ins = [to_dev(im) for im in imgs]
+    outs = [empty_like_img(*im.shape, 8) for im in imgs]
+    plan = tx.Plan(ins, outs, qp, bits=8)
+    info = plan.info()
+    tuned = [i for i, g in enumerate(info) if g["variant"] >= 0]
+    assert {info[i]["zone"] for i in tuned} == {0, 1, 2, 3}  # r <= 8, 16, 32, 64 all present
+    sse = torch.zeros(len(imgs), dtype=torch.int64, device="cuda")
+    ref_out, ref_sse = None, None
+    seen = set()
+    for var in range(3):
+        for ctas, chunk in ((0, 1), (1, 3)):
+            for i in tuned:
+                plan.set_schedule(i, var, ctas, chunk)
+            for o in outs:
+                o.zero_()
+            plan.run(sse=sse)
+            torch.cuda.synchronize()
+            for i in tuned:
+                g = plan.info()[i]
+                assert g["variant"] == var and g["ctas_per_sm"] == ctas and g["chunk"] == chunk
+                seen.add((g["zone"], var, g["warps_per_cta"], g["parked_pairs"], g["stages"]))
+            got = [o.clone() for o in outs]
+            if ref_out is None:
+                ref_out, ref_sse = got, sse.clone()
+                for im, o, (q, r) in zip(imgs, got, qp):
+                    ref = O.codec_image(im, q, r, 8, "fp32")
+                    assert np.array_equal(from_dev(o, 8), ref["recon"])
+            else:
+                for a, b in zip(ref_out, got):
+                    assert torch.equal(a, b)
+                assert torch.equal(ref_sse, sse)
+    # three distinct configurations per group, at least one with two stages
+    assert len(seen) == 12 and any(s[4] == 2 for s in seen)
+    with pytest.raises(tx.Tx16Error):
+        plan.set_schedule(tuned[0], 3, 0, 1)
+    plan.autotune(None)
+    for i in tuned:
+        assert 0 <= plan.info()[i]["variant"] < 3
+    plan.close()
