@@ -196,3 +196,22 @@ def test_build_refuses_flush_to_zero_flags(monkeypatch):
             build.extra_flags()
     monkeypatch.setenv("TX16_NVCC_FLAGS", "-DTX16_BT_MINCTAS_B=3 -ftz=false")
     assert build.extra_flags() == ["-DTX16_BT_MINCTAS_B=3", "-ftz=false"]
+
+
+def test_class_heights_are_the_zigzag_column_heights():
+    """The one-block-per-thread kernel prunes each column pair to the taller
+    column's height in Z_rmax of its class (compile-time tables in the kernel
+    source): they must be the oracle's zig-zag column heights, so that no
+    kept coefficient of any r <= r_max is dropped (Sec. 3.1 zonal scan)."""
+    src = open(os.path.join(ROOT, "paper_1606_07414_gb300", "csrc", "tx16_fused_bt.cuh")).read()
+    found = re.findall(r"struct BtClass<(\d)> \{\s*static constexpr int kRmax = (\d+), V = (\d+), U = (\d+);"
+                       r"\s*static constexpr int H\[\d+\] = \{([^}]*)\};", src)
+    assert len(found) == 6
+    for c, rmax, V, U, H in found:
+        rmax, V, U = int(rmax), int(V), int(U)
+        H = [int(x) for x in H.split(",")]
+        m = O.zonal_mask(rmax)
+        colh = [int(m[:, v].sum()) for v in range(16)]
+        assert V == max(v + 1 for v in range(16) if colh[v] > 0), c
+        assert U == max(colh), c
+        assert H == [max(colh[2 * p], colh[2 * p + 1]) for p in range(V // 2)], c
