@@ -626,7 +626,7 @@ def _serving(tx16, torch, np, args):
         ins = [torch.from_numpy(f.view(np.int16) if bits > 8 else f).pin_memory() for f in src]
         outs = [torch.empty_like(t).pin_memory() for t in ins]
         pools.append((H, W, bits, ins, outs))
-    srv = tx16.Server({"device_pool_mb": 16384, "streams": 3, "max_batch": 256})
+    srv = tx16.Server({"device_pool_mb": 16384, "streams": args.serve_streams, "max_batch": 256})
     rates = [int(x) for x in args.serve_rates.split(",")]
     # untimed warm-up: every request kind, q and r through both forms once
     # (first launches of each kernel variant load their modules)
@@ -927,8 +927,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-rates", default="1000,5000,20000,50000")
+    ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--serve-seconds", type=float, default=0.5)
+    ap.add_argument("--serve-streams", type=int, default=6, help="stream slots of the server")
+    ap.add_argument("--serve-only", action="store_true", help="the serving section alone (one short JSON line)")
     ap.add_argument("--quick", action="store_true", help="headline number only")
     ap.add_argument("--e2e-chunk", type=int, default=16,
                     help="frames per chunk of the host-buffer pipeline (a divisor of the frame count)")
@@ -943,6 +945,14 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_only:
+        import numpy as np
+        import torch
+
+        from paper_1606_07414_gb300 import tx16
+
+        tx16.load()
+        print(json.dumps({"serving": _serving(tx16, torch, np, args), "streams": args.serve_streams}), flush=True)
     elif args.ssim_only:
         run_ssim_only(args)
     elif args.frames10_only:

@@ -339,15 +339,23 @@ typedef struct tx16_server tx16_server;
  *   "device_pool_mb"  device arena for request planes (default: a quarter of
  *                     the free HBM, at most 4096); fails with TX16_ENOMEM
  *                     when it exceeds the free HBM
- *   "streams"         groups in flight (default 3, 1..16)
+ *   "streams"         groups in flight (default 6, 1..16)
  *   "max_batch"       requests per group (default 256)
  *   "max_queue"       queued requests before submit returns TX16_EBUSY
- *   "spin_us"         polling window, 0..1e6 (default 300): after its last
- *                     progress the worker polls for submissions and finished
- *                     groups this long before it blocks, and tx16_serve_wait
- *                     polls this long before it blocks; 0 blocks at once
- *                     (no host core kept busy, longer hand-offs at low load)
- * The server uses the device current at creation. */
+ *   "spin_us"         worker polling window, 0..1e6 (default 300): the
+ *                     worker polls for submissions and finished groups while
+ *                     a group is in flight and for this long after its last
+ *                     progress, then blocks; 0 blocks at once when nothing
+ *                     is in flight (no host core kept busy when idle, longer
+ *                     hand-offs at low load)
+ *   "wait_spin_us"    tx16_serve_wait polling window, 0..1e6 (default 2000):
+ *                     the waiter polls this long, itself retiring the
+ *                     request's group when its work has finished, before it
+ *                     blocks; 0 blocks at once
+ * A request that arrives while nothing is queued or in flight is admitted and
+ * launched by tx16_serve_submit on the caller's thread; otherwise the worker
+ * admits it and the group's stream slot has its own thread issuing the
+ * copies and the launch.  The server uses the device current at creation. */
 tx16_status tx16_serve_create(const char* json_cfg, tx16_server** server);
 
 /* Queue one request: host_pixels (w x h samples, uint8 for bits = 8, uint16

@@ -2,25 +2,31 @@
 // quantiser, coded by the fused batch kernels with continuous batching.
 //
 //  submit   validates the request, stamps its arrival time and queues it.
+//           If the server is idle (nothing queued or in flight), it admits
+//           the request and puts it on a slot itself: a lone request skips
+//           the hand-off to the worker.
 //  worker   (one host thread) repeatedly
 //             - admits queued requests, in arrival order, while the device
 //               arena has room for their input and output planes and a batch
 //               slot is free ("admission by free HBM");
-//             - puts each admitted group on a free slot's stream: host->device
-//               copies of the inputs, ONE tx16_codec_batch launch over the
-//               group, device->host copies of the reconstructions and SSEs,
-//               then an event;
+//             - hands each admitted group to its slot's issuer thread, which
+//               puts it on the slot's stream: host->device copies of the
+//               inputs, ONE tx16_codec_batch launch over the group,
+//               device->host copies of the reconstructions and SSEs, then an
+//               event -- the slots' issuers run in parallel, so the CUDA calls
+//               of one group do not hold up the admission of the next;
 //             - retires slots whose event has fired: PSNR, latency, frees the
 //               requests' arena space, wakes their waiters.
-//           With nothing to do it polls (submissions, slot events) for up to
-//           spin_us after its last progress, then blocks until a submit or a
-//           slot's host callback wakes it: at low load the hand-offs between
-//           threads, not the GPU, set the latency.
+//           While a group is in flight it polls (submissions, slot events),
+//           so a finished group is retired at once; with nothing in flight it
+//           polls for up to spin_us after its last progress, then blocks until
+//           a submit or a slot's host callback wakes it.
 //           Groups on different slots overlap on the GPU (copies of one with
 //           the kernel of another), and requests that arrive while others are
 //           in flight join the next group: the batch is never closed.
-//  wait     polls for up to spin_us, then blocks (bounded) until the request
-//           is done.
+//  wait     polls for up to wait_spin_us -- retiring the request's group
+//           itself if its event has fired, so completion needs no hand-off
+//           either -- then blocks (bounded) until the request is done.
 //
 // All device memory (the arena, per-slot SSE arrays) is allocated once at
 // creation; requests never allocate.  Host buffers are the caller's: the input
@@ -115,6 +121,7 @@ struct Request {
   char* d_in = nullptr;
   char* d_out = nullptr;
   std::atomic<bool> done{false};
+  std::atomic<struct Slot*> slot{nullptr};  // the group's slot while in flight
   tx16_status status = TX16_OK;
   double psnr = 0.0;
   double latency_us = 0.0;
@@ -126,7 +133,11 @@ struct Slot {
   uint64_t* d_sse = nullptr;
   uint64_t* h_sse = nullptr;  // pinned
   std::vector<Request*> reqs;
-  bool busy = false;  // written by the worker thread only
+  bool busy = false;            // a group is admitted (under the server's lock)
+  bool issue_pending = false;   // the issuer has a group to launch (under the lock)
+  std::atomic<bool> launched{false};  // the group's work and event are on the stream
+  std::condition_variable cv_issue;
+  std::thread issuer;
   struct tx16_server* server = nullptr;
 };
 
@@ -137,7 +148,7 @@ struct tx16_server {
   int max_batch = 256;
   size_t max_queue = 1 << 20;
   Arena arena;
-  std::vector<Slot> slots;
+  std::deque<Slot> slots;  // built once at creation (slots hold threads and atomics)
   std::mutex mu;
   std::condition_variable cv_work;  // worker: new requests / stop
   std::condition_variable cv_done;  // waiters
@@ -145,9 +156,11 @@ struct tx16_server {
   std::map<uint64_t, Request*> live;  // ticket -> request (until waited)
   uint64_t next_ticket = 1;
   bool stop = false;
+  bool stop_issuers = false;  // set after the worker has drained everything
   bool paused = false;  // admission held (tx16_serve_pause)
   std::atomic<uint64_t> pokes{0};  // bumped by submit, pause, stop and slot callbacks
-  double spin_us = 300;            // polling window of the worker and of waiters
+  double spin_us = 300;            // polling window of the worker
+  double wait_spin_us = 2000;      // polling window of waiters (they retire finished groups themselves)
   std::thread worker;
   // statistics
   std::vector<double> lat;  // reservoir of latencies (us)
@@ -280,11 +293,74 @@ void retire(tx16_server* s, Slot& slot, tx16_status st) {
     s->arena.free(r->d_in);
     s->arena.free(r->d_out);
     r->d_in = r->d_out = nullptr;
+    r->slot.store(nullptr, std::memory_order_relaxed);
     r->done.store(true, std::memory_order_release);
   }
   s->t_last = t;
   slot.reqs.clear();
+  slot.launched.store(false, std::memory_order_relaxed);
   slot.busy = false;
+}
+
+// Admit queued requests into a free slot, in arrival order, while the arena
+// has room (the caller holds the lock).  Returns false if none fits.
+bool admit(tx16_server* s, Slot& slot) {
+  while (!s->queue.empty() && int(slot.reqs.size()) < s->max_batch) {
+    Request* r = s->queue.front();
+    r->d_in = s->arena.alloc(r->bytes);
+    r->d_out = r->d_in ? s->arena.alloc(r->bytes) : nullptr;
+    if (r->d_out == nullptr) {  // no room now: wait for a group to retire
+      s->arena.free(r->d_in);
+      r->d_in = nullptr;
+      break;
+    }
+    s->queue.pop_front();
+    slot.reqs.push_back(r);
+  }
+  if (slot.reqs.empty()) return false;
+  slot.busy = true;
+  slot.launched.store(false, std::memory_order_relaxed);
+  for (Request* r : slot.reqs) r->slot.store(&slot, std::memory_order_release);
+  return true;
+}
+
+// Put the admitted group of `slot` on its stream, without the lock (lk is
+// held on entry and on return).  On an error the group is retired with it.
+void issue(tx16_server* s, Slot& slot, std::unique_lock<std::mutex>& lk) {
+  lk.unlock();
+  const tx16_status st = launch_group(slot);
+  if (st != TX16_OK) cudaStreamSynchronize(slot.stream);
+  lk.lock();
+  if (st != TX16_OK) {
+    retire(s, slot, st);
+    s->cv_done.notify_all();
+  } else {
+    slot.launched.store(true, std::memory_order_release);
+  }
+  s->pokes.fetch_add(1, std::memory_order_release);
+  s->cv_work.notify_one();
+}
+
+// A slot whose group is on the stream and whose event has fired (no lock
+// needed for the query): the error of the group's work, if any, in *st.
+bool slot_finished(Slot& slot, tx16_status* st) {
+  if (!slot.launched.load(std::memory_order_acquire)) return false;
+  const cudaError_t q = cudaEventQuery(slot.event);
+  if (q == cudaErrorNotReady) return false;
+  *st = q == cudaSuccess ? TX16_OK : TX16_ECUDA;
+  return true;
+}
+
+// The issuer thread of one slot: launches the groups the worker admits to it.
+void issuer_main(tx16_server* s, Slot* slot) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    slot->cv_issue.wait(lk, [&] { return slot->issue_pending || s->stop_issuers; });
+    if (!slot->issue_pending) break;
+    slot->issue_pending = false;
+    issue(s, *slot, lk);
+  }
 }
 
 // Poll, without the lock, until a submission or callback arrives, a slot in
@@ -292,8 +368,9 @@ void retire(tx16_server* s, Slot& slot, tx16_status st) {
 void poll_for_work(tx16_server* s, uint64_t seen, Clock::time_point until) {
   while (Clock::now() < until) {
     if (s->pokes.load(std::memory_order_acquire) != seen) return;
+    tx16_status st;
     for (Slot& slot : s->slots)
-      if (slot.busy && cudaEventQuery(slot.event) != cudaErrorNotReady) return;
+      if (slot.busy && slot_finished(slot, &st)) return;
   }
 }
 
@@ -308,39 +385,18 @@ void worker_main(tx16_server* s) {
     // is reported by the query)
     bool progressed = false;
     for (Slot& slot : s->slots) {
-      if (!slot.busy) continue;
-      const cudaError_t q = cudaEventQuery(slot.event);
-      if (q == cudaErrorNotReady) continue;
-      retire(s, slot, q == cudaSuccess ? TX16_OK : TX16_ECUDA);
+      tx16_status st;
+      if (!slot.busy || !slot_finished(slot, &st)) continue;
+      retire(s, slot, st);
       progressed = true;
     }
     if (progressed) s->cv_done.notify_all();
-    // admit and launch: one group per free slot
+    // admit: one group per free slot, launched by the slot's issuer
     for (Slot& slot : s->slots) {
       if (slot.busy || s->queue.empty() || s->paused) continue;
-      while (!s->queue.empty() && int(slot.reqs.size()) < s->max_batch) {
-        Request* r = s->queue.front();
-        r->d_in = s->arena.alloc(r->bytes);
-        r->d_out = r->d_in ? s->arena.alloc(r->bytes) : nullptr;
-        if (r->d_out == nullptr) {  // no room now: wait for a group to retire
-          s->arena.free(r->d_in);
-          r->d_in = nullptr;
-          break;
-        }
-        s->queue.pop_front();
-        slot.reqs.push_back(r);
-      }
-      if (slot.reqs.empty()) break;
-      slot.busy = true;
-      // issue copies and the launch without holding the lock (submit stays cheap)
-      lk.unlock();
-      const tx16_status st = launch_group(slot);
-      if (st != TX16_OK) cudaStreamSynchronize(slot.stream);
-      lk.lock();
-      if (st != TX16_OK) {
-        retire(s, slot, st);
-        s->cv_done.notify_all();
-      }
+      if (!admit(s, slot)) break;
+      slot.issue_pending = true;
+      slot.cv_issue.notify_one();
       progressed = true;
     }
     const bool inflight = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot& x) { return x.busy; });
@@ -348,9 +404,11 @@ void worker_main(tx16_server* s) {
     const Clock::time_point now = Clock::now();
     if (progressed) {
       last_progress = now;
-    } else if (now < last_progress + spin) {
+    } else if (inflight || now < last_progress + spin) {
+      // poll while a group is in flight (its completion is then seen at once,
+      // not through the callback thread) and for the window after progress
       lk.unlock();
-      poll_for_work(s, seen, last_progress + spin);
+      poll_for_work(s, seen, inflight ? now + spin : last_progress + spin);
       lk.lock();
     } else if (s->pokes.load(std::memory_order_acquire) == seen) {
       // sleep until a callback, a submit, a resume or stop (bounded: re-check)
@@ -377,13 +435,14 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
   }
   const double pool_mb = cfg.count("device_pool_mb") ? cfg["device_pool_mb"]
                                                       : std::min(4096.0, double(free_b) / 4.0 / (1 << 20));
-  const int nslots = cfg.count("streams") ? int(cfg["streams"]) : 3;
+  const int nslots = cfg.count("streams") ? int(cfg["streams"]) : 6;
   s->max_batch = cfg.count("max_batch") ? int(cfg["max_batch"]) : 256;
   s->max_queue = cfg.count("max_queue") ? size_t(cfg["max_queue"]) : size_t(1) << 20;
   s->spin_us = cfg.count("spin_us") ? cfg["spin_us"] : 300.0;
+  s->wait_spin_us = cfg.count("wait_spin_us") ? cfg["wait_spin_us"] : 2000.0;
   const size_t pool = size_t(pool_mb * (1 << 20));
   if (pool < 4096 || nslots < 1 || nslots > 16 || s->max_batch < 1 || s->max_batch > 4096 || s->max_queue < 1 ||
-      !(s->spin_us >= 0 && s->spin_us <= 1e6)) {
+      !(s->spin_us >= 0 && s->spin_us <= 1e6) || !(s->wait_spin_us >= 0 && s->wait_spin_us <= 1e6)) {
     delete s;
     return TX16_EINVAL;
   }
@@ -391,7 +450,7 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
     delete s;
     return TX16_ENOMEM;
   }
-  s->slots.resize(nslots);
+  for (int i = 0; i < nslots; ++i) s->slots.emplace_back();
   for (Slot& slot : s->slots) {
     slot.server = s;
     if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -402,6 +461,7 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
       return TX16_ENOMEM;
     }
   }
+  for (Slot& slot : s->slots) slot.issuer = std::thread(issuer_main, s, &slot);
   s->worker = std::thread(worker_main, s);
   *out = s;
   return TX16_OK;
@@ -447,6 +507,14 @@ tx16_status tx16_serve_submit(tx16_server* s, const void* host_pixels, int32_t w
     s->pokes.fetch_add(1, std::memory_order_release);
   }
   s->cv_work.notify_one();
+  // An idle server: admit and launch the request here, on the caller's
+  // thread, instead of waking the worker for it.
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool idle = !s->paused && !s->stop && s->queue.size() == 1 && s->queue.front() == r &&
+                      std::none_of(s->slots.begin(), s->slots.end(), [](const Slot& x) { return x.busy; });
+    if (idle && admit(s, s->slots.front())) issue(s, s->slots.front(), lk);
+  }
   return TX16_OK;
 }
 
@@ -459,11 +527,25 @@ tx16_status tx16_serve_wait(tx16_server* s, uint64_t ticket, int32_t timeout_ms,
   Request* r = it->second;  // only its waiter frees it, so it outlives the unlocked poll
   const Clock::time_point t0 = Clock::now();
   const auto deadline = t0 + std::chrono::milliseconds(std::max(0, timeout_ms));
-  if (!r->done.load(std::memory_order_acquire) && s->spin_us > 0) {
+  if (!r->done.load(std::memory_order_acquire) && s->wait_spin_us > 0) {
     const auto until = std::min(deadline, t0 + std::chrono::duration_cast<Clock::duration>(
-                                                   std::chrono::duration<double, std::micro>(s->spin_us)));
+                                                   std::chrono::duration<double, std::micro>(s->wait_spin_us)));
     lk.unlock();
     while (!r->done.load(std::memory_order_acquire) && Clock::now() < until) {
+      // retire the request's group here once its event has fired
+      Slot* slot = r->slot.load(std::memory_order_acquire);
+      tx16_status st;
+      if (slot != nullptr && slot_finished(*slot, &st)) {
+        lk.lock();
+        if (!r->done.load(std::memory_order_acquire) && r->slot.load(std::memory_order_acquire) == slot &&
+            slot->busy && slot_finished(*slot, &st)) {
+          retire(s, *slot, st);
+          s->cv_done.notify_all();
+          s->pokes.fetch_add(1, std::memory_order_release);  // the worker may admit into the freed slot
+          s->cv_work.notify_one();
+        }
+        lk.unlock();
+      }
     }
     lk.lock();
   }
@@ -534,6 +616,14 @@ void tx16_serve_destroy(tx16_server* s) {
   }
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_issuers = true;
+  }
+  for (Slot& slot : s->slots) {
+    slot.cv_issue.notify_all();
+    if (slot.issuer.joinable()) slot.issuer.join();
+  }
   for (Slot& slot : s->slots) {
     if (slot.stream) cudaStreamSynchronize(slot.stream);
     if (slot.event) cudaEventDestroy(slot.event);

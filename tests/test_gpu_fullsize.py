@@ -3,11 +3,13 @@ benchmark times (one call over the whole batch), on sampled outputs the
 oracle computes block by block, plus properties checked on every output.
 
   * 256 frames of 1920 x 1088 uint8 (the video model: one AR(1) field, rho
-    0.95, cropped along a 2-pixel random walk), q = 16 and r in {4, 16, 32,
-    256}: one tx16_codec_batch call (the kernel of each zonal class as timed),
-    3000 random blocks and every tile-boundary block of the first and last
-    frames against the oracle's binary32 decision path, bit-exact; every
-    frame's squared error against the GPU's own reconstruction, exact.
+    0.95, cropped along a 2-pixel random walk), the bench's sweep points (q in
+    {8, 16, 32}, r in {4, 16, 32, 64, 128, 256}): one tx16_codec_batch call
+    (the kernel of each zonal class as timed), 3000 random blocks and every
+    tile-boundary block of the first and last frames against the oracle's
+    binary32 decision path, bit-exact; every frame's squared error against the
+    GPU's own reconstruction, exact; the PSNR of two full frames within
+    1e-3 dB of the float64 definition.
   * 64 images of 2048 x 2048 uint8, forward only: 4000 random blocks and the
     first and last block of every image against the direct int64 product,
     bit-exact.  The forward path is data-independent arithmetic, so uniform
@@ -47,12 +49,17 @@ def _blocks(plane, picks, nbx):
     return np.stack([plane[(b // nbx) * 16:(b // nbx) * 16 + 16, (b % nbx) * 16:(b % nbx) * 16 + 16] for b in picks])
 
 
-@pytest.mark.parametrize("r", [16, 4, 32, 256])
-def test_headline_workload_full_size(tx, frames, r):
+@pytest.mark.parametrize("q,r", [(16.0, 16), (16.0, 4), (16.0, 32), (16.0, 256), (8.0, 16), (32.0, 16),
+                                 (16.0, 64), (8.0, 64), (32.0, 128)])
+def test_headline_workload_full_size(tx, frames, q, r):
+    """One call over the 256 frames of the bench's sweep points (every zonal
+    class, q in {8, 16, 32}); sampled blocks bit-exact against the oracle's
+    binary32 decision path, every frame's squared error exact, and the PSNR
+    of the first and last full frames within 1e-3 dB of the float64
+    definition (the paper's arithmetic, Sec. 3.1)."""
     import torch
 
     n, H, W = frames.shape
-    q = 16.0
     d_in = torch.from_numpy(frames).cuda()
     d_out = torch.zeros_like(d_in)
     sse = torch.full((n,), -1, dtype=torch.int64, device="cuda")
@@ -75,6 +82,10 @@ def test_headline_workload_full_size(tx, frames, r):
     got = np.concatenate([_blocks(rec[i], sorted(p), nbx) for i, p in sorted(picks.items())])
     ref = oracle_blocks(X.astype(np.int64), q, r, 8)
     assert np.array_equal(got, ref["recon"])
+    psnr = tx.tx16_psnr([int(s[0]), int(s[n - 1])], [tx.image(d_in[0]), tx.image(d_in[n - 1])])
+    for got_db, i in zip(psnr, (0, n - 1)):
+        want = O.codec_image(frames[i], q, r, 8, "fp64")["psnr"]
+        assert abs(got_db - want) <= 1e-3, (i, got_db, want)
 
 
 def test_forward_full_size(tx):
