@@ -4,14 +4,18 @@
 // the padded blocks are coded as usual, and only the image's own pixels are
 // written and counted in the squared error.
 //
-// Each image is split on the host into its interior of whole blocks, which
-// the ordinary codec kernels handle (a fused kernel where the samples and the
-// step suit it, the general kernel otherwise), and at most two edge strips --
-// the last, partial block column (full height) and the last, partial block
-// row (interior width) -- which the kernel below codes with the replication
-// done in its loads: a row below the image reads the last row instead, and
-// samples right of the image take the value of the last column.  Both
-// launches add into the image's SSE slot.
+// Each image is split on the host.  Where the one-block-per-thread kernel
+// takes the image's samples and zone, its columns of whole blocks are coded
+// over the full height by that kernel, which repeats the last row into a
+// partial last block row in its loads and writes and counts only the image's
+// rows.  Otherwise its interior of whole blocks goes to the ordinary codec
+// kernels (a fused kernel where the samples and the step suit it, the general
+// kernel otherwise) and the last, partial block row (interior width) to the
+// strip kernel below.  The last, partial block column (full height) always
+// goes to the strip kernel, which does the replication in its loads: a row
+// below the image reads the last row instead, and samples right of the image
+// take the value of the last column.  All launches add into the image's SSE
+// slot.
 //
 // The strip kernel has the general kernel's mapping (16 threads per block,
 // int32 forward, binary32 or exact inverse).  Colour images are coded plane
@@ -215,6 +219,7 @@ extern "C" tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_imag
   // interior of whole blocks (width and height rounded down to 16) per image,
   // or nblk = 0 when there is none; edge strips as AnyParam
   std::vector<ImgParam> inner(n);
+  std::vector<ImgParam> ragged;  // whole images of ragged height for the one-block-per-thread kernel
   std::vector<AnyParam> strips;
   strips.reserve(2 * size_t(n));
   for (int i = 0; i < n; ++i) {
@@ -235,7 +240,20 @@ extern "C" tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_imag
       return r;
     };
     std::memset(&inner[i], 0, sizeof(ImgParam));
-    if (W16 > 0 && H16 > 0) {
+    bool whole_height = false;  // columns [0, W16) over the full height coded as one ragged image
+    if (W16 > 0 && H16 < H) {
+      const int Hp = (H + 15) / 16 * 16;
+      tx16_image a = sub(in[i], 0, 0, W16, Hp), b;
+      if (out != nullptr) b = sub(out[i], 0, 0, W16, Hp);
+      ImgParam p = make_param(a, out ? &b : nullptr, qp[i], 0);
+      if (fused_bt_ragged_supports(p)) {
+        p.flags |= (Hp - H) << kBtMissingShift;
+        p.out_index = i;
+        ragged.push_back(p);
+        whole_height = true;
+      }
+    }
+    if (W16 > 0 && H16 > 0 && !whole_height) {
       const tx16_image a = sub(in[i], 0, 0, W16, H16);
       tx16_image b;
       if (out != nullptr) b = sub(out[i], 0, 0, W16, H16);
@@ -257,7 +275,7 @@ extern "C" tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_imag
       strips.push_back(A);
     };
     if (W16 < W) add_strip(W16, 0, W - W16, H);   // last block column, full height
-    if (H16 < H && W16 > 0) add_strip(0, H16, W16, H - H16);  // last block row, interior width
+    if (H16 < H && W16 > 0 && !whole_height) add_strip(0, H16, W16, H - H16);  // last block row, interior width
   }
   if (n == 0) return TX16_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -275,6 +293,11 @@ extern "C" tx16_status tx16_codec_any_size(const tx16_image* in, const tx16_imag
     const tx16_status r = launch_codec_runs(inner.data() + s, e - s, s64 ? s64 + s : nullptr, nullptr, st);
     if (r != TX16_OK) return r;
     s = e;
+  }
+  // whole images of ragged height
+  if (!ragged.empty()) {
+    const tx16_status r = launch_fused_bt_ragged(ragged.data(), int(ragged.size()), s64, st);
+    if (r != TX16_OK) return r;
   }
   // edge strips: runs of equal sample size, at most kAnyMaxImg per launch
   const int m = int(strips.size());

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "tx16_fused_bt.cuh"
 #include "tx16_internal.h"
@@ -14,6 +15,14 @@ extern template tx16_status bt_batch<0>(bool, int, const ImgParam*, int, unsigne
 extern template tx16_status bt_batch<1>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 extern template tx16_status bt_batch<2>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 extern template tx16_status bt_batch<3>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_ragged<0>(bool, int, const ImgParam*, int, unsigned long long*,
+                                                cudaStream_t);
+extern template tx16_status bt_batch_ragged<1>(bool, int, const ImgParam*, int, unsigned long long*,
+                                                cudaStream_t);
+extern template tx16_status bt_batch_ragged<2>(bool, int, const ImgParam*, int, unsigned long long*,
+                                                cudaStream_t);
+extern template tx16_status bt_batch_ragged<3>(bool, int, const ImgParam*, int, unsigned long long*,
+                                                cudaStream_t);
 extern template tx16_status bt_list<0>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
                                        unsigned long long*, cudaStream_t);
 extern template tx16_status bt_list<1>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
@@ -111,6 +120,38 @@ tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, uns
     case 3: return bt_batch<3>(dst, 1, imgs, n, sse, stream);
     default: return TX16_EINVAL;
   }
+}
+
+tx16_status launch_fused_bt_ragged(const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
+  // runs of equal sample size and zonal class, at most kMaxImg per launch
+  std::vector<ImgParam> run;
+  for (int sb = 1; sb <= 2; ++sb) {
+    for (int zone = 0; zone <= 3; ++zone) {
+      run.clear();
+      for (int i = 0; i < n; ++i)
+        if (sample_bytes(imgs[i].flags & 0xff) == sb && fused_zone_class(&imgs[i], 1) == zone) run.push_back(imgs[i]);
+      for (size_t s = 0; s < run.size(); s += kMaxImg) {
+        const int m = int(std::min<size_t>(kMaxImg, run.size() - s));
+        const bool dst = run[s].dst != nullptr;
+        tx16_status st;
+        switch (zone) {
+          case 0: st = bt_batch_ragged<0>(dst, sb, run.data() + s, m, sse, stream); break;
+          case 1: st = bt_batch_ragged<1>(dst, sb, run.data() + s, m, sse, stream); break;
+          case 2: st = bt_batch_ragged<2>(dst, sb, run.data() + s, m, sse, stream); break;
+          default: st = bt_batch_ragged<3>(dst, sb, run.data() + s, m, sse, stream); break;
+        }
+        if (st != TX16_OK) return st;
+      }
+    }
+  }
+  return TX16_OK;
+}
+
+bool fused_bt_ragged_supports(const ImgParam& p) {
+  const int bits = p.flags & 0xff;
+  const int zone = fused_zone_class(&p, 1);
+  if (bits == 8) return fused_eligible(p) && fused_bt_supports(zone, false);
+  return fused_bt16_eligible(p) && zone <= 2;
 }
 
 bool fused_bt16_eligible(const ImgParam& p) {

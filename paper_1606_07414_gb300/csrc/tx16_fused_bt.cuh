@@ -278,6 +278,17 @@ __device__ __forceinline__ void st_pair_cs(void* a, uint4 va, void* b, uint4 vb,
       : "memory");
 }
 
+// As st_pair_cs with a predicate per row.
+__device__ __forceinline__ void st_pair_cs2(void* a, uint4 va, bool pa, void* b, uint4 vb, bool pb) {
+  asm volatile(
+      "{\n\t.reg .pred q, r;\n\tsetp.ne.b32 q, %10, 0;\n\tsetp.ne.b32 r, %11, 0;\n\t"
+      "@q st.global.cs.v4.u32 [%0], {%2, %3, %4, %5};\n\t"
+      "@r st.global.cs.v4.u32 [%1], {%6, %7, %8, %9};\n\t}" ::"l"(a),
+      "l"(b), "r"(va.x), "r"(va.y), "r"(va.z), "r"(va.w), "r"(vb.x), "r"(vb.y), "r"(vb.z), "r"(vb.w), "r"(int(pa)),
+      "r"(int(pb))
+      : "memory");
+}
+
 // Alternative configurations of each class's work-list kernel, timed against
 // the default (variant 0, the settings above) by the plan autotuner: warps
 // per CTA, resident CTAs per SM, parked column pairs, input stages.
@@ -524,7 +535,13 @@ __device__ __forceinline__ void fill_consts_t(const ImgParam& I, PairConsts<U, N
   __syncwarp();
 }
 
-template <int C, int VAR, bool DST, int SB, class Sched>
+// RAGGED: images whose height is not a multiple of 16 (tx16_codec_any_size):
+// the descriptor covers the padded block rows, flags bits from
+// kBtMissingShift hold the rows missing from the last block row; rows below
+// the image read the last row (edge replication), and only the image's rows
+// are stored and counted.
+
+template <int C, int VAR, bool DST, int SB, bool RAGGED, class Sched>
 __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, int nimg, int ntiles,
                                            unsigned long long* sse, Sched& sched) {
   static_assert(SB == 1 || SB == 2, "8- or 16-bit samples");
@@ -555,6 +572,7 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
   // [row][half][thread][16 bytes]
   constexpr bool kBulk = TX16_BT_BULK != 0;
   constexpr bool kRolling = !kBulk && Cfg::kRolling;
+  static_assert(!(kBulk && RAGGED), "the bulk-copy staging reads whole blocks: no ragged images");
   constexpr int kWarpStage = 16 * 32 * 16 * SB;  // bytes of one warp's stage (bulk layout)
   constexpr int kRowStride = kBulk ? 32 * 16 * SB : SB * kSlot;
   constexpr int kHalfStride = kBulk ? 16 : kSlot;
@@ -610,18 +628,24 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
     const uint8_t* g;
     int64_t pitch;
     int bytes;
+    int last;  // last row of the block inside the image (RAGGED), else 15
+  };
+  // last row of block blk of image I inside the image
+  auto last_row = [&](const ImgParam& I, int blk) {
+    return (RAGGED && blk >= I.nblk - I.nbx) ? 15 - ((I.flags >> kBtMissingShift) & 15) : 15;
   };
   auto row_src = [&](int kk, int tt) {
     const ImgParam& I = imgs[kk];
     const int blk = (tt - I.tile0) * kWarpTile + lane;
     const uint8_t* src = static_cast<const uint8_t*>(I.src);
-    if (blk >= I.nblk) return RowSrc{src, 0, 0};
+    if (blk >= I.nblk) return RowSrc{src, 0, 0, 15};
     const int2 c = block_coords(I.div_magic, I.nbx, blk);
-    return RowSrc{src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16 * SB, I.src_pitch, 16};
+    return RowSrc{src + int64_t(c.x) * 16 * I.src_pitch + c.y * 16 * SB, I.src_pitch, 16, last_row(I, blk)};
   };
   auto fetch_row = [&](const RowSrc& r, uint8_t* s, int i) {
+    const int64_t row = RAGGED ? min(i, r.last) : i;  // rows below the image repeat its last row
 #pragma unroll
-    for (int h = 0; h < SB; ++h) cp_async16(s + (i * SB + h) * kSlot, r.g + int64_t(i) * r.pitch + 16 * h, r.bytes);
+    for (int h = 0; h < SB; ++h) cp_async16(s + (i * SB + h) * kSlot, r.g + row * r.pitch + 16 * h, r.bytes);
   };
   // all 16 rows of this thread's block of tile tt (image kk) into stage st, one group
   auto prefetch = [&](int kk, int tt, int st) {
@@ -683,6 +707,7 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
     const int blk = (t - I.tile0) * kWarpTile + lane;
     const bool valid = blk < I.nblk;
     const int2 c = valid ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
+    const int last = last_row(I, blk);  // 15 unless RAGGED and in the last block row
     const uint8_t* rows = stage_rows(stage);  // row 0 of this thread's block
     const int64_t dpitch = DST ? I.dst_pitch : 0;
     uint8_t* const dblk = DST ? static_cast<uint8_t*>(I.dst) + int64_t(c.x) * 16 * dpitch + c.y * 16 * SB : nullptr;
@@ -788,20 +813,27 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
           xa[q] = pack4_sat_u8(na[4 * q], na[4 * q + 1], na[4 * q + 2], na[4 * q + 3]);
           xb[q] = pack4_sat_u8(nb[4 * q], nb[4 * q + 1], nb[4 * q + 2], nb[4 * q + 3]);
         }
-        if (DST)
+        if (DST && !RAGGED)
           st_pair_cs(dblk + i * dpitch, make_uint4(xa[0], xa[1], xa[2], xa[3]), dblk + (15 - i) * dpitch,
                      make_uint4(xb[0], xb[1], xb[2], xb[3]), valid);
+        if (DST && RAGGED)
+          st_pair_cs2(dblk + i * dpitch, make_uint4(xa[0], xa[1], xa[2], xa[3]), valid && i <= last,
+                      dblk + (15 - i) * dpitch, make_uint4(xb[0], xb[1], xb[2], xb[3]), valid && 15 - i <= last);
         // SSE = sum |x - y|^2 by bytes (vabsdiff4, then dp4a); the error of a
-        // block past the image's end is dropped below
+        // block past the image's end is dropped below, and of rows below the
+        // image here
         const uint4 ra = *reinterpret_cast<const uint4*>(rows + i * kRowStride);
         const uint4 rb = *reinterpret_cast<const uint4*>(rows + (15 - i) * kRowStride);
         const unsigned ia[4] = {ra.x, ra.y, ra.z, ra.w}, ib[4] = {rb.x, rb.y, rb.z, rb.w};
+        unsigned sa = 0, sb = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const unsigned da = __vabsdiffu4(ia[q], xa[q]), db = __vabsdiffu4(ib[q], xb[q]);
-          s1 = __dp4a(da, da, s1);
-          s1 = __dp4a(db, db, s1);
+          sa = __dp4a(da, da, sa);
+          sb = __dp4a(db, db, sb);
         }
+        s1 += (!RAGGED || i <= last) ? sa : 0u;
+        s1 += (!RAGGED || 15 - i <= last) ? sb : 0u;
       } else {
         const unsigned peak2 = ((1u << (imgs[k].flags & 0xff)) - 1u) * 0x10001u;
         unsigned ya[8], yb[8];
@@ -821,20 +853,25 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
         if (DST) {
           uint8_t* da_ = dblk + i * dpitch;
           uint8_t* db_ = dblk + (15 - i) * dpitch;
+          const bool pa = valid && (!RAGGED || i <= last), pb = valid && (!RAGGED || 15 - i <= last);
           st_pair_cs(da_, make_uint4(ya[0], ya[1], ya[2], ya[3]), da_ + 16, make_uint4(ya[4], ya[5], ya[6], ya[7]),
-                     valid);
+                     pa);
           st_pair_cs(db_, make_uint4(yb[0], yb[1], yb[2], yb[3]), db_ + 16, make_uint4(yb[4], yb[5], yb[6], yb[7]),
-                     valid);
+                     pb);
         }
         unsigned wa[8], wb[8];
         load_row_at<2>(rows + i * kRowStride, kHalfStride, wa);
         load_row_at<2>(rows + (15 - i) * kRowStride, kHalfStride, wb);
+        unsigned sa = 0, sb = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int d0 = int(wa[q] & 0xffffu) - int(ya[q] & 0xffffu), d1 = int(wa[q] >> 16) - int(ya[q] >> 16);
           const int d2 = int(wb[q] & 0xffffu) - int(yb[q] & 0xffffu), d3 = int(wb[q] >> 16) - int(yb[q] >> 16);
-          s1 += unsigned(d0 * d0) + unsigned(d1 * d1) + unsigned(d2 * d2) + unsigned(d3 * d3);
+          sa += unsigned(d0 * d0) + unsigned(d1 * d1);
+          sb += unsigned(d2 * d2) + unsigned(d3 * d3);
         }
+        s1 += (!RAGGED || i <= last) ? sa : 0u;
+        s1 += (!RAGGED || 15 - i <= last) ? sb : 0u;
       }
       // rows i and 15 - i of the stage are used: refill them for the next tile
       if (kRolling && tn >= 0) {
@@ -855,12 +892,12 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
   if (sse) flush_sse(sse, imgs[k].out_index, acc);
 }
 
-template <int MAXI, int C, bool DST, int SB>
+template <int MAXI, int C, bool DST, int SB, bool RAGGED = false>
 __global__ void __launch_bounds__(32 * BtCfg<C, 0, SB>::kWarps, BtCfg<C, 0, SB>::kMinCtas)
     fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
   StaticWarps sched{int(blockIdx.x) * BtCfg<C, 0, SB>::kWarps + int(threadIdx.x >> 5),
                     int(gridDim.x) * BtCfg<C, 0, SB>::kWarps, P.ntiles};
-  bt_tiles_t<C, 0, DST, SB>(P.img, P.nimg, P.ntiles, P.sse, sched);
+  bt_tiles_t<C, 0, DST, SB, RAGGED>(P.img, P.nimg, P.ntiles, P.sse, sched);
 }
 
 template <int C, int VAR, bool DST>
@@ -868,11 +905,15 @@ __global__ void __launch_bounds__(32 * BtCfg<C, VAR, 1>::kWarps, BtCfg<C, VAR, 1
     fused_bt_list_kernel(const ImgParam* __restrict__ imgs, int nimg, int ntiles, unsigned* counter, int chunk,
                          unsigned long long* sse) {
   DynamicWarps sched{counter, ntiles, chunk, 0, 0};
-  bt_tiles_t<C, VAR, DST, 1>(imgs, nimg, ntiles, sse, sched);
+  bt_tiles_t<C, VAR, DST, 1, false>(imgs, nimg, ntiles, sse, sched);
 }
 
-template <int MAXI, int C, bool DST, int SB>
-tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
+// keep_index: the descriptors' out_index are already the SSE slots (RAGGED
+// launches over a subset of a call's images); otherwise image i of the launch
+// adds into sse[i].
+template <int MAXI, int C, bool DST, int SB, bool RAGGED = false>
+tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream,
+                      bool keep_index = false) {
   using Cfg = BtCfg<C, 0, SB>;
   BatchParams<MAXI> P;
   P.nimg = n;
@@ -882,7 +923,7 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
   for (int i = 0; i < n; ++i) {
     P.img[i] = imgs[i];
     P.img[i].tile0 = tiles;
-    P.img[i].out_index = i;
+    if (!keep_index) P.img[i].out_index = i;
     tiles += (imgs[i].nblk + kWarpTile - 1) / kWarpTile;
   }
   P.ntiles = tiles;
@@ -890,17 +931,17 @@ tx16_status launch_bt(const ImgParam* imgs, int n, unsigned long long* sse, cuda
   static std::atomic<int> occ{0};  // resident CTAs per SM, looked up once
   if (occ == 0) {
     int o = 0;
-    if (cudaFuncSetAttribute(fused_bt_kernel<MAXI, C, DST, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(fused_bt_kernel<MAXI, C, DST, SB, RAGGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(Cfg::kSmem)) != cudaSuccess)
       return TX16_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_kernel<MAXI, C, DST, SB>, kBtThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_bt_kernel<MAXI, C, DST, SB, RAGGED>, kBtThreads,
                                                       Cfg::kSmem) != cudaSuccess ||
         o < 1)
       o = 1;
     occ = o;
   }
   const int grid = std::max(1, std::min((tiles + Cfg::kWarps - 1) / Cfg::kWarps, occ * device_sm_count()));
-  fused_bt_kernel<MAXI, C, DST, SB><<<grid, kBtThreads, Cfg::kSmem, stream>>>(P);
+  fused_bt_kernel<MAXI, C, DST, SB, RAGGED><<<grid, kBtThreads, Cfg::kSmem, stream>>>(P);
   return cudaGetLastError() == cudaSuccess ? TX16_OK : TX16_ECUDA;
 }
 
@@ -961,6 +1002,19 @@ tx16_status bt_batch(bool dst, int sb, const ImgParam* imgs, int n, unsigned lon
     if (n <= 8) return launch_bt_dst<8, C, 2>(dst, imgs, n, sse, stream);
     return launch_bt_dst<kMaxImg, C, 2>(dst, imgs, n, sse, stream);
   }
+  return TX16_EINVAL;
+}
+// Images of ragged height (see kBtMissingShift), out_index = SSE slot of sse,
+// at most kMaxImg.
+template <int C>
+tx16_status bt_batch_ragged(bool dst, int sb, const ImgParam* imgs, int n, unsigned long long* sse,
+                            cudaStream_t stream) {
+  if (sb == 1)
+    return dst ? launch_bt<kMaxImg, C, true, 1, true>(imgs, n, sse, stream, true)
+               : launch_bt<kMaxImg, C, false, 1, true>(imgs, n, sse, stream, true);
+  if constexpr (C <= 2)
+    return dst ? launch_bt<kMaxImg, C, true, 2, true>(imgs, n, sse, stream, true)
+               : launch_bt<kMaxImg, C, false, 2, true>(imgs, n, sse, stream, true);
   return TX16_EINVAL;
 }
 // A work list in device memory (tile0 in warp tiles), tiles claimed `chunk` at

@@ -100,6 +100,14 @@ tx16_status launch_fused_bt_list(int zone, int variant, bool dst, const ImgParam
                                  unsigned* counter, int chunk, int ctas_per_sm, unsigned long long* sse,
                                  cudaStream_t stream);
 int fused_bt_list_max_ctas(int zone, int variant, bool dst);  // resident CTAs per SM
+// Images whose height is not a multiple of 16 (tx16_codec_any_size), coded
+// whole by the one-block-per-thread kernel: the descriptor covers the padded
+// block rows, flags bits 12..15 hold the rows missing from the last block row
+// (kBtMissingShift); rows below the image repeat its last row, and only the
+// image's rows are written and counted in sse[out_index].
+constexpr int kBtMissingShift = 12;
+bool fused_bt_ragged_supports(const ImgParam& p);
+tx16_status launch_fused_bt_ragged(const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream);
 // 9..12-bit planes (uint16 samples) with a quantiser of q >= 2^(bits-8)/256:
 // the one-block-per-thread kernel for zonal classes up to 8 kept columns and
 // no levels, the general kernel otherwise.
