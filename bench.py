@@ -492,6 +492,9 @@ def _extras(args, lib, tx16, torch, np, ins, outs, d_in, d_out, h_in, d_sse, spt
     out["mixed_tiling"] = {"workload": f"{FRAMES} frames {W}x{H} uint8, q={args.q:g}, r16={args.r}, "
                                        f"r8={max(1, args.r // 4)}, tiling chosen per 16x16 region by squared error",
                            "Mregions_s": round(blocks / (ms_m * 1e-3) / 1e6, 1), "ms": round(ms_m, 4),
+                           # 256 bytes in, 256 out and one split-map byte per region
+                           "GB_s": round(blocks * 513 / (ms_m * 1e-3) / 1e9, 1),
+                           "frac": round(blocks * 513 / (ms_m * 1e-3) / 1e9 / peak, 4),
                            "split_fraction": round(float(split.float().mean().item()), 4),
                            "mean_psnr_db": round(psnr_m, 4)}
 
@@ -882,6 +885,41 @@ def run_ssim_only(args):
                       "mean_ssim": round(float(ms_t.mean().item()), 6)}), flush=True)
 
 
+def run_mixed_only(args):
+    """Mixed 8/16 tiling of --frames frames (q, r16 = r, r8 = r / 4), --steps
+    timed launches after --warmup; prints one short JSON line (not the bench
+    line)."""
+    import torch
+
+    from paper_1606_07414_gb300 import synth, tx16
+
+    lib = tx16.load()
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    d_in = torch.from_numpy(synth.video_frames(SEED, FRAMES, H, W, rho=0.95)).cuda()
+    d_out = torch.empty_like(d_in)
+    ins = (tx16.tx16_image * FRAMES)(*[tx16.image(d_in[i]) for i in range(FRAMES)])
+    outs = (tx16.tx16_image * FRAMES)(*[tx16.image(d_out[i]) for i in range(FRAMES)])
+    r8 = max(1, args.r // 4)
+    mqp = (tx16.tx16_mixed_qparams * FRAMES)(*[tx16.tx16_mixed_qparams(args.q, args.r, r8, 0)] * FRAMES)
+    regions = FRAMES * (H // 16) * (W // 16)
+    split = torch.zeros(regions, dtype=torch.uint8, device="cuda")
+    sse = torch.zeros(FRAMES, dtype=torch.int64, device="cuda")
+
+    def mixed():
+        st = lib.tx16_codec_mixed(ins, outs, FRAMES, ctypes.cast(mqp, ctypes.c_void_p),
+                                  ctypes.c_void_p(split.data_ptr()), ctypes.c_void_p(sse.data_ptr()), sptr)
+        if st != 0:
+            raise tx16.Tx16Error(st, "tx16_codec_mixed")
+    for _ in range(args.warmup):
+        mixed()
+    ms = _events_time(mixed, args.steps, stream)
+    gbs = regions * 513 / (ms * 1e-3) / 1e9
+    print(json.dumps({"mixed_ms": round(ms, 4), "frames": FRAMES, "r16": args.r, "r8": r8,
+                      "Mregions_s": round(regions / (ms * 1e-3) / 1e6, 1), "GB_s": round(gbs, 1),
+                      "split_fraction": round(float(split.float().mean().item()), 4)}))
+
+
 def run_frames10_only(args):
     """The fused 16-bit codec on --frames 3840 x 2160 10-bit frames, --steps
     timed launches after --warmup; prints one short JSON line (not the bench
@@ -938,6 +976,8 @@ def main():
     ap.add_argument("--frames", type=int, default=FRAMES, help="smaller cases for profiling")
     ap.add_argument("--ssim-only", action="store_true",
                     help="time tx16_ssim alone on --frames frames and their reconstruction (profiling)")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="the mixed 8/16 tiling section alone (one short JSON line)")
     ap.add_argument("--frames10-only", action="store_true",
                     help="time the fused 16-bit codec alone on --frames 10-bit 3840x2160 frames (profiling)")
     args = ap.parse_args()
@@ -958,6 +998,8 @@ def main():
         run_ssim_only(args)
     elif args.frames10_only:
         run_frames10_only(args)
+    elif args.mixed_only:
+        run_mixed_only(args)
     else:
         run_gpu(args)
 

@@ -387,6 +387,150 @@ def emit_transposing(w, T, rnd):
     w("")
 
 
+# --- the 8-point approximation T8 (Sec. 2.1): the first halves of M2, M3, M4 --
+# (those stages are block diagonal across the split of their 16 inputs into
+# 0..7 and 8..15), with output k of T8 the first-half output that P2 sends to
+# row 2k of T
+G8 = [G2[2 * k] for k in range(8)]
+
+
+def t8_forward(net, x):
+    e = net.m4(net.m3(net.m2(list(x) + [ZERO] * 8)))
+    return [e[g] for g in G8]
+
+
+def t8_inverse(net, y):
+    e = [ZERO] * 16
+    for k in range(8):
+        e[G8[k]] = y[k]
+    return net.m2(net.m3(net.m4(e)))[:8]
+
+
+def emit_t8(w, T, rnd):
+    """Networks of T8 on float2 pairs for the mixed 8/16 tiling codec, which
+    holds a 16x16 region per thread with rows (i, 15 - i) in the lanes: lane x
+    walks the upper 8x8 blocks top-down, lane y the lower ones bottom-up.  The
+    column networks take the eight row pairs in order; the first stage of T8
+    (M2) pairs rows k and 7 - k of a block, which both lanes see, and lane y
+    then carries the odd-frequency half negated (rows 3 - k and 4 + k come in
+    swapped order).  The quantiser is odd-symmetric and the inverse column
+    network undoes the same swap in its last stage, so lane y's output pair m
+    is row 7 - m of the lower block with its true value: outputs come back in
+    the (i, 15 - i) pairing."""
+    T8 = [[T[2 * k][j] for j in range(8)] for k in range(8)]
+    # T8 is the even rows of T on the sums x_j + x_(15-j)
+    for k in range(8):
+        assert all(T[2 * k][j] == T[2 * k][15 - j] for j in range(8))
+    G = [[sum(T8[a][j] * T8[b][j] for j in range(8)) for b in range(8)] for a in range(8)]
+    assert all(G[a][b] == 0 for a in range(8) for b in range(8) if a != b), "T8 T8^t is not diagonal"
+    fsign = None
+    for V in range(1, 9):  # forward row pass, outputs v < V (signed)
+        net = Net(cse=True)
+        x = [net.leaf(i) for i in range(8)]
+        y = t8_forward(net, x)[:V]
+        lines, outs, adds = emit_nodes(net, y, [f"X[{i}]" for i in range(8)])
+        for _ in range(20):
+            xs = [rnd.randint(0, 255) for _ in range(8)]
+            check(net, y, xs, [sum(T8[k][m] * xs[m] for m in range(8)) for k in range(V)])
+        signs = [o[1] for o in outs] + [0] * (16 - V)
+        if V == 8:
+            fsign = signs[:8]
+        w(f"// T8 on one half row of both lanes, outputs v < {V}: R[v] = sign[v] * (T8 x)[v];")
+        w(f"// {adds} pair additions")
+        w(f"struct FwdRow8T{V} {{")
+        w(sign_fn(signs))
+        w(f"  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[{V}]) {{")
+        for ln in lines:
+            w("    " + ln)
+        for v in range(V):
+            w(f"    R[{v}] = {outs[v][0]};")
+        w("  }")
+        w("};")
+        w("")
+    for H in range(1, 9):  # forward column pass over the 8 row pairs, outputs u < H (signed)
+        net = Net(cse=True)
+        a = [net.leaf(i) for i in range(8)]
+        y = t8_forward(net, a)[:H]
+        lines, outs, adds = emit_nodes(net, y, [f"a[{i}]" for i in range(8)])
+        for _ in range(20):
+            xs = [rnd.randint(-4096, 4096) for _ in range(8)]
+            check(net, y, xs, [sum(T8[k][m] * xs[m] for m in range(8)) for k in range(H)])
+        signs = [o[1] for o in outs] + [0] * (16 - H)
+        assert signs[:H] == fsign[:H]  # the same network: the same output signs
+        w(f"// T8 down a column of the eight row pairs, outputs u < {H}: n[u] = sign[u] * (T8 a)[u]")
+        w(f"// per lane (lane y: odd u negated, see the row-pair note); {adds} pair additions")
+        w(f"struct FwdCol8M{H} {{")
+        w(sign_fn(signs))
+        w(f"  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[{H}]) {{")
+        for ln in lines:
+            w("    " + ln)
+        for u in range(H):
+            w(f"    n[{u}] = {outs[u][0]};")
+        w("  }")
+        w("};")
+        w("")
+    for H in range(1, 9):  # inverse column pass, inputs u < H (true values), outputs true
+        net = Net()
+        ins = [net.leaf(i) if i < H else ZERO for i in range(8)]
+        z = t8_inverse(net, ins)
+        lines, outs, adds = emit_nodes(net, z, [f"w[{i}]" for i in range(8)])
+        assert all(o is not None and o[1] == 1 for o in outs), "inverse column outputs must be true values"
+        for _ in range(20):
+            ws = [rnd.randint(-5000, 5000) if i < H else 0 for i in range(8)]
+            check(net, z, ws, [sum(T8[m][k] * ws[m] for m in range(8)) for k in range(8)])
+        w(f"// T8^t down a column, inputs u < {H}: z[m] = (T8^t w)[m] per lane, true values; "
+          f"{adds} pair additions")
+        w(f"struct InvCol8T{H} {{")
+        w(f"  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {{")
+        for ln in lines:
+            w("    " + ln)
+        for m in range(8):
+            w(f"    z[{m}] = {outs[m][0]};")
+        w("  }")
+        w("};")
+        w("")
+    for V in range(1, 9):  # inverse row pass, inputs v < V (true values), outputs signed
+        net = Net()
+        ins = [net.leaf(i) if i < V else ZERO for i in range(8)]
+        z = t8_inverse(net, ins)
+        lines, outs, adds = emit_nodes(net, z, [f"w[{i}]" for i in range(8)])
+        assert all(o is not None for o in outs)
+        for _ in range(20):
+            ws = [rnd.randint(-5000, 5000) if i < V else 0 for i in range(8)]
+            check(net, z, ws, [sum(T8[m][k] * ws[m] for m in range(8)) for k in range(8)])
+        signs = [o[1] for o in outs] + [0] * 8
+        w(f"// T8^t on a half row, inputs v < {V}: z[j] = sign[j] * (T8^t w)[j]; {adds} pair additions")
+        w(f"struct InvRow8T{V} {{")
+        w(sign_fn(signs))
+        w(f"  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {{")
+        for ln in lines:
+            w("    " + ln)
+        for j in range(8):
+            w(f"    z[{j}] = {outs[j][0]};")
+        w("  }")
+        w("};")
+        w("")
+    w("// the T8 networks of the mixed tiling codec: a column keeping rows u < H,")
+    w("// a half row keeping columns v < V")
+    w("template <int H>")
+    w("struct Col8Nets;")
+    for H in range(1, 9):
+        w("template <>")
+        w(f"struct Col8Nets<{H}> {{")
+        w(f"  using FC = FwdCol8M{H};")
+        w(f"  using IC = InvCol8T{H};")
+        w("};")
+    w("template <int V>")
+    w("struct Row8Nets;")
+    for V in range(1, 9):
+        w("template <>")
+        w(f"struct Row8Nets<{V}> {{")
+        w(f"  using FR = FwdRow8T{V};")
+        w(f"  using IR = InvRow8T{V};")
+        w("};")
+    w("")
+
+
 ZONES = [(3, 4), (5, 6), (7, 8), (11, 10), (16, 16)]  # (rows U, columns V) kept
 
 
@@ -519,6 +663,7 @@ def main():
         w("};")
         w("")
     emit_transposing(w, T, rnd)
+    emit_t8(w, T, rnd)
     w(f"// sign of each output of the (unpruned) forward network: row-pass outputs")
     w(f"// are stored unsigned; the column thread folds this sign into its scale.")
     w(f"constexpr unsigned kFwdNegMask = 0x{sum(1 << i for i, x in enumerate(fwd_sign) if x < 0):04x}u;")

@@ -388,15 +388,34 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // Tile schedules of one warp (every call is warp-uniform).  StaticWarps: warp
-// w takes tiles w, w + W, w + 2W, ... (W warps in the grid).  DynamicWarps:
-// the warp claims chunks of tiles from a counter of the work list, the next
-// chunk one chunk ahead, so that the next tile is known while this one runs.
+// w takes tiles w, w + W, w + 2W, ... (W warps in the grid).  ChunkWarps:
+// warp w takes a contiguous run of tiles.  DynamicWarps: the warp claims
+// chunks of tiles from a counter of the work list, the next chunk one chunk
+// ahead, so that the next tile is known while this one runs.  A batch launch
+// takes ChunkWarps (TX16_BT_CHUNKED 1): 10386-10484 against 10180-10188
+// Mblocks/s on 1920x1088 frames at r = 16 with StaticWarps, which changes
+// image, and so refills the quantiser table, at nearly every tile.
+#ifndef TX16_BT_CHUNKED
+#define TX16_BT_CHUNKED 1
+#endif
 struct StaticWarps {
   int t0, step, ntiles;
   __device__ __forceinline__ int first() const { return t0 < ntiles ? t0 : -1; }
   __device__ __forceinline__ int next(int t) const { return t + step < ntiles ? t + step : -1; }
 };
 
+// Warp w of W takes the contiguous tiles [w n / W, (w + 1) n / W): a warp
+// changes image (and refills its quantiser tables) about once per launch,
+// where taking tiles w, w + W, ... changes image at nearly every tile once
+// the images have fewer tiles than the grid has warps (7362 against 6480
+// Mregions/s on 1920x1088 frames).
+struct ChunkWarps {
+  int t0, t1;
+  __device__ ChunkWarps(int w, int nw, int ntiles)
+      : t0(int(int64_t(w) * ntiles / nw)), t1(int(int64_t(w + 1) * ntiles / nw)) {}
+  __device__ __forceinline__ int first() const { return t0 < t1 ? t0 : -1; }
+  __device__ __forceinline__ int next(int t) const { return t + 1 < t1 ? t + 1 : -1; }
+};
 struct DynamicWarps {
   unsigned* counter;
   int ntiles, chunk, cur_end, next_start;
@@ -895,9 +914,15 @@ __device__ __forceinline__ void bt_tiles_t(const ImgParam* __restrict__ imgs, in
 template <int MAXI, int C, bool DST, int SB, bool RAGGED = false>
 __global__ void __launch_bounds__(32 * BtCfg<C, 0, SB>::kWarps, BtCfg<C, 0, SB>::kMinCtas)
     fused_bt_kernel(const __grid_constant__ BatchParams<MAXI> P) {
-  StaticWarps sched{int(blockIdx.x) * BtCfg<C, 0, SB>::kWarps + int(threadIdx.x >> 5),
-                    int(gridDim.x) * BtCfg<C, 0, SB>::kWarps, P.ntiles};
-  bt_tiles_t<C, 0, DST, SB, RAGGED>(P.img, P.nimg, P.ntiles, P.sse, sched);
+  const int w = int(blockIdx.x) * BtCfg<C, 0, SB>::kWarps + int(threadIdx.x >> 5);
+  const int nw = int(gridDim.x) * BtCfg<C, 0, SB>::kWarps;
+  if (TX16_BT_CHUNKED) {
+    ChunkWarps sched(w, nw, P.ntiles);
+    bt_tiles_t<C, 0, DST, SB, RAGGED>(P.img, P.nimg, P.ntiles, P.sse, sched);
+  } else {
+    StaticWarps sched{w, nw, P.ntiles};
+    bt_tiles_t<C, 0, DST, SB, RAGGED>(P.img, P.nimg, P.ntiles, P.sse, sched);
+  }
 }
 
 template <int C, int VAR, bool DST>

@@ -115,6 +115,28 @@ bool fused_bt16_eligible(const ImgParam& p);
 tx16_status launch_fused_u16(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                              cudaStream_t stream);
 
+// Mixed 8/16 tiling (tx16_mixed.cu): per image, the 16x16 quantiser and
+// region grid (p; blk0 = first region in the split map, out_index = SSE
+// slot), the 8x8 quantiser (S8 merged: f8 = fl32(2^(-3+k/2) / q), g8 =
+// fl32(q 2^(-3+k/2))), the kept rows of each 8x8 column and the tiling mode
+// (0 automatic, 1 all 16x16, 2 all 8x8).
+struct MixedParam {
+  ImgParam p;
+  float f8[5];
+  float g8[5];
+  uint8_t colh8[8];
+  int32_t mode;
+};
+constexpr int kMixMaxImg = 160;  // images per launch (kernel-parameter limit)
+// The one-region-per-thread kernel (tx16_mixed_bt.cu): 8-bit samples with a
+// quantiser of q >= kFusedMinQ, an output plane, 16x16 zones of r <= 64 and
+// 8x8 zones of r8 <= 16.  mixed_bt_pair: the compiled class pair that covers
+// the image (0..4), or -1; one launch takes images of one pair.
+constexpr int kMixBtPairs = 5;
+int mixed_bt_pair(const MixedParam& m);
+tx16_status launch_mixed_bt(int pair, const MixedParam* imgs, int n, unsigned long long* sse, uint8_t* split,
+                            cudaStream_t stream);
+
 // Launchers (tx16_codec.cu).  `imgs` points at `n` ImgParam already filled in
 // (except tile0, set here), all with the same sample size.
 tx16_status launch_blocks(Op op, int sample_bytes, ImgParam* imgs, int n,

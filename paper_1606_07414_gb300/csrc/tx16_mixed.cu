@@ -31,22 +31,13 @@ ImgParam make_param(const tx16_image& in, const tx16_image* out, const tx16_qpar
 
 namespace {
 
-struct MixedParam {
-  ImgParam p;       // 16x16 quantiser (r16), samples, region grid; blk0 = first region in the split map
-  float f8[5];      // fl32(2^(-3+k/2) / q)
-  float g8[5];      // fl32(q 2^(-3+k/2))
-  uint8_t colh8[8];  // kept rows of column v of an 8x8 block (zig-zag, r8)
-  int32_t mode;     // 0 automatic, 1 all 16x16, 2 all 8x8
-};
-
 template <int MAXI>
 struct MixedBatch {
   int32_t nimg, ntiles;
-  unsigned long long* sse;
+  unsigned long long* sse;  // indexed by out_index
   uint8_t* split;
   MixedParam img[MAXI];
 };
-constexpr int kMixMaxImg = 160;
 static_assert(sizeof(MixedBatch<kMixMaxImg>) < 32000, "kernel parameters too large");
 
 __device__ __forceinline__ int c8(int u) { return (u & 1) ? 2 : ((u & 2) ? 1 : 0); }  // 0,2,1,2,0,2,1,2
@@ -73,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) mixed_kernel(const __grid_constant__
   for (int t = t0; t < t1; ++t) {
     while (k + 1 < P.nimg && P.img[k + 1].p.tile0 <= t) ++k;  // uniform
     if (k != acc_img) {
-      if (P.sse) flush_sse_rows(P.sse, acc_img, acc);
+      if (P.sse) flush_sse_rows(P.sse, P.img[acc_img].p.out_index, acc);
       acc = 0;
       acc_img = k;
     }
@@ -250,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) mixed_kernel(const __grid_constant__
       acc += split ? e8 : e16;
     }
   }
-  if (P.sse) flush_sse_rows(P.sse, acc_img, acc);
+  if (P.sse) flush_sse_rows(P.sse, P.img[acc_img].p.out_index, acc);
 }
 
 template <typename Smp>
@@ -323,6 +314,7 @@ extern "C" tx16_status tx16_codec_mixed(const tx16_image* in, const tx16_image* 
       return TX16_EINVAL;
     const tx16_qparams q16{m.q, m.r16};
     M[i].p = make_param(in[i], out ? &out[i] : nullptr, q16, blk0);
+    M[i].p.out_index = i;
     blk0 += M[i].p.nblk;
     const double r2 = std::sqrt(2.0);
     for (int k = 0; k < 5; ++k) {
@@ -337,12 +329,27 @@ extern "C" tx16_status tx16_codec_mixed(const tx16_image* in, const tx16_image* 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (sse != nullptr && cudaMemsetAsync(sse, 0, sizeof(uint64_t) * size_t(n), st) != cudaSuccess) return TX16_ECUDA;
   unsigned long long* s64 = reinterpret_cast<unsigned long long*>(sse);
+  // the one-region-per-thread kernel by class pair; the rest on the kernel
+  // above, by runs of equal sample size
+  std::vector<MixedParam> fast[kMixBtPairs], rest;
+  for (int i = 0; i < n; ++i) {
+    const int pair = mixed_bt_pair(M[i]);
+    (pair >= 0 ? fast[pair] : rest).push_back(M[i]);
+  }
+  for (int c = 0; c < kMixBtPairs; ++c)
+    for (size_t s = 0; s < fast[c].size(); s += kMixMaxImg) {
+      const int m = int(std::min<size_t>(kMixMaxImg, fast[c].size() - s));
+      const tx16_status r = launch_mixed_bt(c, fast[c].data() + s, m, s64, split, st);
+      if (r != TX16_OK) return r;
+    }
+  const int nr = int(rest.size());
   int s = 0;
-  while (s < n) {
+  while (s < nr) {
+    const bool u8 = (rest[s].p.flags & 0xff) == 8;
     int e = s + 1;
-    while (e < n && e - s < kMixMaxImg && (in[e].bits == 8) == (in[s].bits == 8)) ++e;
-    const tx16_status r = in[s].bits == 8 ? launch_mixed<uint8_t>(M.data() + s, e - s, s64 ? s64 + s : nullptr, split, st)
-                                          : launch_mixed<uint16_t>(M.data() + s, e - s, s64 ? s64 + s : nullptr, split, st);
+    while (e < nr && e - s < kMixMaxImg && ((rest[e].p.flags & 0xff) == 8) == u8) ++e;
+    const tx16_status r = u8 ? launch_mixed<uint8_t>(rest.data() + s, e - s, s64, split, st)
+                             : launch_mixed<uint16_t>(rest.data() + s, e - s, s64, split, st);
     if (r != TX16_OK) return r;
     s = e;
   }

@@ -3063,6 +3063,805 @@ struct ColNets<16> {
   using IC = InvColT16;
 };
 
+// T8 on one half row of both lanes, outputs v < 1: R[v] = sign[v] * (T8 x)[v];
+// 7 pair additions
+struct FwdRow8T1 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfffeu, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[1]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    R[0] = t20;
+  }
+};
+
+// T8 on one half row of both lanes, outputs v < 2: R[v] = sign[v] * (T8 x)[v];
+// 8 pair additions
+struct FwdRow8T2 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfffcu, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[2]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t15 = sub2(X[0], X[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    R[0] = t20;
+    R[1] = t15;
+  }
+};
+
+// T8 on one half row of both lanes, outputs v < 3: R[v] = sign[v] * (T8 x)[v];
+// 9 pair additions
+struct FwdRow8T3 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfff8u, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[3]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t15 = sub2(X[0], X[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    R[0] = t20;
+    R[1] = t15;
+    R[2] = t19;
+  }
+};
+
+// T8 on one half row of both lanes, outputs v < 4: R[v] = sign[v] * (T8 x)[v];
+// 10 pair additions
+struct FwdRow8T4 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0008u, 0xfff0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[4]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t11 = sub2(X[2], X[5]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t15 = sub2(X[0], X[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    R[0] = t20;
+    R[1] = t15;
+    R[2] = t19;
+    R[3] = t11;
+  }
+};
+
+// T8 on one half row of both lanes, outputs v < 5: R[v] = sign[v] * (T8 x)[v];
+// 11 pair additions
+struct FwdRow8T5 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0008u, 0xffe0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[5]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t11 = sub2(X[2], X[5]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t15 = sub2(X[0], X[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    R[0] = t20;
+    R[1] = t15;
+    R[2] = t19;
+    R[3] = t11;
+    R[4] = t21;
+  }
+};
+
+// T8 on one half row of both lanes, outputs v < 6: R[v] = sign[v] * (T8 x)[v];
+// 12 pair additions
+struct FwdRow8T6 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0028u, 0xffc0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[6]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t11 = sub2(X[2], X[5]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t13 = sub2(X[1], X[6]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t15 = sub2(X[0], X[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    R[0] = t20;
+    R[1] = t15;
+    R[2] = t19;
+    R[3] = t11;
+    R[4] = t21;
+    R[5] = t13;
+  }
+};
+
+// T8 on one half row of both lanes, outputs v < 7: R[v] = sign[v] * (T8 x)[v];
+// 13 pair additions
+struct FwdRow8T7 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0068u, 0xff80u, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[7]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t11 = sub2(X[2], X[5]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t13 = sub2(X[1], X[6]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t15 = sub2(X[0], X[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t18 = sub2(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    R[0] = t20;
+    R[1] = t15;
+    R[2] = t19;
+    R[3] = t11;
+    R[4] = t21;
+    R[5] = t13;
+    R[6] = t18;
+  }
+};
+
+// T8 on one half row of both lanes, outputs v < 8: R[v] = sign[v] * (T8 x)[v];
+// 14 pair additions
+struct FwdRow8T8 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x00e8u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&X)[8], float2 (&R)[8]) {
+    const float2 t8 = __fadd2_rn(X[0], X[7]);
+    const float2 t9 = sub2(X[3], X[4]);
+    const float2 t10 = __fadd2_rn(X[1], X[6]);
+    const float2 t11 = sub2(X[2], X[5]);
+    const float2 t12 = __fadd2_rn(X[2], X[5]);
+    const float2 t13 = sub2(X[1], X[6]);
+    const float2 t14 = __fadd2_rn(X[3], X[4]);
+    const float2 t15 = sub2(X[0], X[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t18 = sub2(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    R[0] = t20;
+    R[1] = t15;
+    R[2] = t19;
+    R[3] = t11;
+    R[4] = t21;
+    R[5] = t13;
+    R[6] = t18;
+    R[7] = t9;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 1: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 7 pair additions
+struct FwdCol8M1 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfffeu, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[1]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    n[0] = t20;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 2: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 8 pair additions
+struct FwdCol8M2 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfffcu, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[2]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t15 = sub2(a[0], a[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    n[0] = t20;
+    n[1] = t15;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 3: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 9 pair additions
+struct FwdCol8M3 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xfff8u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[3]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t15 = sub2(a[0], a[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    n[0] = t20;
+    n[1] = t15;
+    n[2] = t19;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 4: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 10 pair additions
+struct FwdCol8M4 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0008u, 0xfff0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[4]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t11 = sub2(a[2], a[5]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t15 = sub2(a[0], a[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    n[0] = t20;
+    n[1] = t15;
+    n[2] = t19;
+    n[3] = t11;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 5: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 11 pair additions
+struct FwdCol8M5 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0008u, 0xffe0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[5]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t11 = sub2(a[2], a[5]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t15 = sub2(a[0], a[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    n[0] = t20;
+    n[1] = t15;
+    n[2] = t19;
+    n[3] = t11;
+    n[4] = t21;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 6: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 12 pair additions
+struct FwdCol8M6 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0028u, 0xffc0u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[6]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t11 = sub2(a[2], a[5]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t13 = sub2(a[1], a[6]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t15 = sub2(a[0], a[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    n[0] = t20;
+    n[1] = t15;
+    n[2] = t19;
+    n[3] = t11;
+    n[4] = t21;
+    n[5] = t13;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 7: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 13 pair additions
+struct FwdCol8M7 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0068u, 0xff80u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[7]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t11 = sub2(a[2], a[5]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t13 = sub2(a[1], a[6]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t15 = sub2(a[0], a[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t18 = sub2(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    n[0] = t20;
+    n[1] = t15;
+    n[2] = t19;
+    n[3] = t11;
+    n[4] = t21;
+    n[5] = t13;
+    n[6] = t18;
+  }
+};
+
+// T8 down a column of the eight row pairs, outputs u < 8: n[u] = sign[u] * (T8 a)[u]
+// per lane (lane y: odd u negated, see the row-pair note); 14 pair additions
+struct FwdCol8M8 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x00e8u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&a)[8], float2 (&n)[8]) {
+    const float2 t8 = __fadd2_rn(a[0], a[7]);
+    const float2 t9 = sub2(a[3], a[4]);
+    const float2 t10 = __fadd2_rn(a[1], a[6]);
+    const float2 t11 = sub2(a[2], a[5]);
+    const float2 t12 = __fadd2_rn(a[2], a[5]);
+    const float2 t13 = sub2(a[1], a[6]);
+    const float2 t14 = __fadd2_rn(a[3], a[4]);
+    const float2 t15 = sub2(a[0], a[7]);
+    const float2 t16 = __fadd2_rn(t8, t14);
+    const float2 t17 = __fadd2_rn(t10, t12);
+    const float2 t18 = sub2(t10, t12);
+    const float2 t19 = sub2(t8, t14);
+    const float2 t20 = __fadd2_rn(t16, t17);
+    const float2 t21 = sub2(t16, t17);
+    n[0] = t20;
+    n[1] = t15;
+    n[2] = t19;
+    n[3] = t11;
+    n[4] = t21;
+    n[5] = t13;
+    n[6] = t18;
+    n[7] = t9;
+  }
+};
+
+// T8^t down a column, inputs u < 1: z[m] = (T8^t w)[m] per lane, true values; 0 pair additions
+struct InvCol8T1 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    z[0] = w[0];
+    z[1] = w[0];
+    z[2] = w[0];
+    z[3] = w[0];
+    z[4] = w[0];
+    z[5] = w[0];
+    z[6] = w[0];
+    z[7] = w[0];
+  }
+};
+
+// T8^t down a column, inputs u < 2: z[m] = (T8^t w)[m] per lane, true values; 2 pair additions
+struct InvCol8T2 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t2 = __fadd2_rn(w[0], w[1]);
+    const float2 t3 = sub2(w[0], w[1]);
+    z[0] = t2;
+    z[1] = w[0];
+    z[2] = w[0];
+    z[3] = w[0];
+    z[4] = w[0];
+    z[5] = w[0];
+    z[6] = w[0];
+    z[7] = t3;
+  }
+};
+
+// T8^t down a column, inputs u < 3: z[m] = (T8^t w)[m] per lane, true values; 4 pair additions
+struct InvCol8T3 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t3 = __fadd2_rn(w[0], w[2]);
+    const float2 t4 = sub2(w[0], w[2]);
+    const float2 t5 = __fadd2_rn(t3, w[1]);
+    const float2 t6 = sub2(t3, w[1]);
+    z[0] = t5;
+    z[1] = w[0];
+    z[2] = w[0];
+    z[3] = t4;
+    z[4] = t4;
+    z[5] = w[0];
+    z[6] = w[0];
+    z[7] = t6;
+  }
+};
+
+// T8^t down a column, inputs u < 4: z[m] = (T8^t w)[m] per lane, true values; 6 pair additions
+struct InvCol8T4 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t4 = __fadd2_rn(w[0], w[2]);
+    const float2 t5 = sub2(w[0], w[2]);
+    const float2 t6 = __fadd2_rn(t4, w[1]);
+    const float2 t7 = __fadd2_rn(w[0], w[3]);
+    const float2 t8 = sub2(w[0], w[3]);
+    const float2 t9 = sub2(t4, w[1]);
+    z[0] = t6;
+    z[1] = w[0];
+    z[2] = t8;
+    z[3] = t5;
+    z[4] = t5;
+    z[5] = t7;
+    z[6] = w[0];
+    z[7] = t9;
+  }
+};
+
+// T8^t down a column, inputs u < 5: z[m] = (T8^t w)[m] per lane, true values; 8 pair additions
+struct InvCol8T5 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t5 = __fadd2_rn(w[0], w[4]);
+    const float2 t6 = sub2(w[0], w[4]);
+    const float2 t7 = __fadd2_rn(t5, w[2]);
+    const float2 t8 = sub2(t5, w[2]);
+    const float2 t9 = __fadd2_rn(t7, w[1]);
+    const float2 t10 = __fadd2_rn(t6, w[3]);
+    const float2 t11 = sub2(t6, w[3]);
+    const float2 t12 = sub2(t7, w[1]);
+    z[0] = t9;
+    z[1] = t6;
+    z[2] = t11;
+    z[3] = t8;
+    z[4] = t8;
+    z[5] = t10;
+    z[6] = t6;
+    z[7] = t12;
+  }
+};
+
+// T8^t down a column, inputs u < 6: z[m] = (T8^t w)[m] per lane, true values; 10 pair additions
+struct InvCol8T6 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t6 = __fadd2_rn(w[0], w[4]);
+    const float2 t7 = sub2(w[0], w[4]);
+    const float2 t8 = __fadd2_rn(t6, w[2]);
+    const float2 t9 = sub2(t6, w[2]);
+    const float2 t10 = __fadd2_rn(t8, w[1]);
+    const float2 t11 = sub2(t7, w[5]);
+    const float2 t12 = __fadd2_rn(t7, w[3]);
+    const float2 t13 = sub2(t7, w[3]);
+    const float2 t14 = __fadd2_rn(t7, w[5]);
+    const float2 t15 = sub2(t8, w[1]);
+    z[0] = t10;
+    z[1] = t11;
+    z[2] = t13;
+    z[3] = t9;
+    z[4] = t9;
+    z[5] = t12;
+    z[6] = t14;
+    z[7] = t15;
+  }
+};
+
+// T8^t down a column, inputs u < 7: z[m] = (T8^t w)[m] per lane, true values; 12 pair additions
+struct InvCol8T7 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t7 = __fadd2_rn(w[0], w[4]);
+    const float2 t8 = sub2(w[0], w[4]);
+    const float2 t9 = __fadd2_rn(t7, w[2]);
+    const float2 t10 = sub2(t8, w[6]);
+    const float2 t11 = __fadd2_rn(t8, w[6]);
+    const float2 t12 = sub2(t7, w[2]);
+    const float2 t13 = __fadd2_rn(t9, w[1]);
+    const float2 t14 = sub2(t10, w[5]);
+    const float2 t15 = __fadd2_rn(t11, w[3]);
+    const float2 t16 = sub2(t11, w[3]);
+    const float2 t17 = __fadd2_rn(t10, w[5]);
+    const float2 t18 = sub2(t9, w[1]);
+    z[0] = t13;
+    z[1] = t14;
+    z[2] = t16;
+    z[3] = t12;
+    z[4] = t12;
+    z[5] = t15;
+    z[6] = t17;
+    z[7] = t18;
+  }
+};
+
+// T8^t down a column, inputs u < 8: z[m] = (T8^t w)[m] per lane, true values; 14 pair additions
+struct InvCol8T8 {
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t8 = __fadd2_rn(w[0], w[4]);
+    const float2 t9 = sub2(w[0], w[4]);
+    const float2 t10 = __fadd2_rn(t8, w[2]);
+    const float2 t11 = sub2(t9, w[6]);
+    const float2 t12 = __fadd2_rn(t9, w[6]);
+    const float2 t13 = sub2(t8, w[2]);
+    const float2 t14 = __fadd2_rn(t10, w[1]);
+    const float2 t15 = __fadd2_rn(t13, w[7]);
+    const float2 t16 = sub2(t11, w[5]);
+    const float2 t17 = __fadd2_rn(t12, w[3]);
+    const float2 t18 = sub2(t12, w[3]);
+    const float2 t19 = __fadd2_rn(t11, w[5]);
+    const float2 t20 = sub2(t13, w[7]);
+    const float2 t21 = sub2(t10, w[1]);
+    z[0] = t14;
+    z[1] = t16;
+    z[2] = t18;
+    z[3] = t20;
+    z[4] = t15;
+    z[5] = t17;
+    z[6] = t19;
+    z[7] = t21;
+  }
+};
+
+// T8^t on a half row, inputs v < 1: z[j] = sign[j] * (T8^t w)[j]; 0 pair additions
+struct InvRow8T1 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    z[0] = w[0];
+    z[1] = w[0];
+    z[2] = w[0];
+    z[3] = w[0];
+    z[4] = w[0];
+    z[5] = w[0];
+    z[6] = w[0];
+    z[7] = w[0];
+  }
+};
+
+// T8^t on a half row, inputs v < 2: z[j] = sign[j] * (T8^t w)[j]; 2 pair additions
+struct InvRow8T2 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t2 = __fadd2_rn(w[0], w[1]);
+    const float2 t3 = sub2(w[0], w[1]);
+    z[0] = t2;
+    z[1] = w[0];
+    z[2] = w[0];
+    z[3] = w[0];
+    z[4] = w[0];
+    z[5] = w[0];
+    z[6] = w[0];
+    z[7] = t3;
+  }
+};
+
+// T8^t on a half row, inputs v < 3: z[j] = sign[j] * (T8^t w)[j]; 4 pair additions
+struct InvRow8T3 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t3 = __fadd2_rn(w[0], w[2]);
+    const float2 t4 = sub2(w[0], w[2]);
+    const float2 t5 = __fadd2_rn(t3, w[1]);
+    const float2 t6 = sub2(t3, w[1]);
+    z[0] = t5;
+    z[1] = w[0];
+    z[2] = w[0];
+    z[3] = t4;
+    z[4] = t4;
+    z[5] = w[0];
+    z[6] = w[0];
+    z[7] = t6;
+  }
+};
+
+// T8^t on a half row, inputs v < 4: z[j] = sign[j] * (T8^t w)[j]; 6 pair additions
+struct InvRow8T4 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t4 = __fadd2_rn(w[0], w[2]);
+    const float2 t5 = sub2(w[0], w[2]);
+    const float2 t6 = __fadd2_rn(t4, w[1]);
+    const float2 t7 = __fadd2_rn(w[0], w[3]);
+    const float2 t8 = sub2(w[0], w[3]);
+    const float2 t9 = sub2(t4, w[1]);
+    z[0] = t6;
+    z[1] = w[0];
+    z[2] = t8;
+    z[3] = t5;
+    z[4] = t5;
+    z[5] = t7;
+    z[6] = w[0];
+    z[7] = t9;
+  }
+};
+
+// T8^t on a half row, inputs v < 5: z[j] = sign[j] * (T8^t w)[j]; 8 pair additions
+struct InvRow8T5 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t5 = __fadd2_rn(w[0], w[4]);
+    const float2 t6 = sub2(w[0], w[4]);
+    const float2 t7 = __fadd2_rn(t5, w[2]);
+    const float2 t8 = sub2(t5, w[2]);
+    const float2 t9 = __fadd2_rn(t7, w[1]);
+    const float2 t10 = __fadd2_rn(t6, w[3]);
+    const float2 t11 = sub2(t6, w[3]);
+    const float2 t12 = sub2(t7, w[1]);
+    z[0] = t9;
+    z[1] = t6;
+    z[2] = t11;
+    z[3] = t8;
+    z[4] = t8;
+    z[5] = t10;
+    z[6] = t6;
+    z[7] = t12;
+  }
+};
+
+// T8^t on a half row, inputs v < 6: z[j] = sign[j] * (T8^t w)[j]; 10 pair additions
+struct InvRow8T6 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t6 = __fadd2_rn(w[0], w[4]);
+    const float2 t7 = sub2(w[0], w[4]);
+    const float2 t8 = __fadd2_rn(t6, w[2]);
+    const float2 t9 = sub2(t6, w[2]);
+    const float2 t10 = __fadd2_rn(t8, w[1]);
+    const float2 t11 = sub2(t7, w[5]);
+    const float2 t12 = __fadd2_rn(t7, w[3]);
+    const float2 t13 = sub2(t7, w[3]);
+    const float2 t14 = __fadd2_rn(t7, w[5]);
+    const float2 t15 = sub2(t8, w[1]);
+    z[0] = t10;
+    z[1] = t11;
+    z[2] = t13;
+    z[3] = t9;
+    z[4] = t9;
+    z[5] = t12;
+    z[6] = t14;
+    z[7] = t15;
+  }
+};
+
+// T8^t on a half row, inputs v < 7: z[j] = sign[j] * (T8^t w)[j]; 12 pair additions
+struct InvRow8T7 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t7 = __fadd2_rn(w[0], w[4]);
+    const float2 t8 = sub2(w[0], w[4]);
+    const float2 t9 = __fadd2_rn(t7, w[2]);
+    const float2 t10 = sub2(t8, w[6]);
+    const float2 t11 = __fadd2_rn(t8, w[6]);
+    const float2 t12 = sub2(t7, w[2]);
+    const float2 t13 = __fadd2_rn(t9, w[1]);
+    const float2 t14 = sub2(t10, w[5]);
+    const float2 t15 = __fadd2_rn(t11, w[3]);
+    const float2 t16 = sub2(t11, w[3]);
+    const float2 t17 = __fadd2_rn(t10, w[5]);
+    const float2 t18 = sub2(t9, w[1]);
+    z[0] = t13;
+    z[1] = t14;
+    z[2] = t16;
+    z[3] = t12;
+    z[4] = t12;
+    z[5] = t15;
+    z[6] = t17;
+    z[7] = t18;
+  }
+};
+
+// T8^t on a half row, inputs v < 8: z[j] = sign[j] * (T8^t w)[j]; 14 pair additions
+struct InvRow8T8 {
+  __host__ __device__ static constexpr int sign(int i) { return sign_of(0x0000u, 0xff00u, i); }
+  __device__ static __forceinline__ void run(const float2 (&w)[8], float2 (&z)[8]) {
+    const float2 t8 = __fadd2_rn(w[0], w[4]);
+    const float2 t9 = sub2(w[0], w[4]);
+    const float2 t10 = __fadd2_rn(t8, w[2]);
+    const float2 t11 = sub2(t9, w[6]);
+    const float2 t12 = __fadd2_rn(t9, w[6]);
+    const float2 t13 = sub2(t8, w[2]);
+    const float2 t14 = __fadd2_rn(t10, w[1]);
+    const float2 t15 = __fadd2_rn(t13, w[7]);
+    const float2 t16 = sub2(t11, w[5]);
+    const float2 t17 = __fadd2_rn(t12, w[3]);
+    const float2 t18 = sub2(t12, w[3]);
+    const float2 t19 = __fadd2_rn(t11, w[5]);
+    const float2 t20 = sub2(t13, w[7]);
+    const float2 t21 = sub2(t10, w[1]);
+    z[0] = t14;
+    z[1] = t16;
+    z[2] = t18;
+    z[3] = t20;
+    z[4] = t15;
+    z[5] = t17;
+    z[6] = t19;
+    z[7] = t21;
+  }
+};
+
+// the T8 networks of the mixed tiling codec: a column keeping rows u < H,
+// a half row keeping columns v < V
+template <int H>
+struct Col8Nets;
+template <>
+struct Col8Nets<1> {
+  using FC = FwdCol8M1;
+  using IC = InvCol8T1;
+};
+template <>
+struct Col8Nets<2> {
+  using FC = FwdCol8M2;
+  using IC = InvCol8T2;
+};
+template <>
+struct Col8Nets<3> {
+  using FC = FwdCol8M3;
+  using IC = InvCol8T3;
+};
+template <>
+struct Col8Nets<4> {
+  using FC = FwdCol8M4;
+  using IC = InvCol8T4;
+};
+template <>
+struct Col8Nets<5> {
+  using FC = FwdCol8M5;
+  using IC = InvCol8T5;
+};
+template <>
+struct Col8Nets<6> {
+  using FC = FwdCol8M6;
+  using IC = InvCol8T6;
+};
+template <>
+struct Col8Nets<7> {
+  using FC = FwdCol8M7;
+  using IC = InvCol8T7;
+};
+template <>
+struct Col8Nets<8> {
+  using FC = FwdCol8M8;
+  using IC = InvCol8T8;
+};
+template <int V>
+struct Row8Nets;
+template <>
+struct Row8Nets<1> {
+  using FR = FwdRow8T1;
+  using IR = InvRow8T1;
+};
+template <>
+struct Row8Nets<2> {
+  using FR = FwdRow8T2;
+  using IR = InvRow8T2;
+};
+template <>
+struct Row8Nets<3> {
+  using FR = FwdRow8T3;
+  using IR = InvRow8T3;
+};
+template <>
+struct Row8Nets<4> {
+  using FR = FwdRow8T4;
+  using IR = InvRow8T4;
+};
+template <>
+struct Row8Nets<5> {
+  using FR = FwdRow8T5;
+  using IR = InvRow8T5;
+};
+template <>
+struct Row8Nets<6> {
+  using FR = FwdRow8T6;
+  using IR = InvRow8T6;
+};
+template <>
+struct Row8Nets<7> {
+  using FR = FwdRow8T7;
+  using IR = InvRow8T7;
+};
+template <>
+struct Row8Nets<8> {
+  using FR = FwdRow8T8;
+  using IR = InvRow8T8;
+};
+
 // sign of each output of the (unpruned) forward network: row-pass outputs
 // are stored unsigned; the column thread folds this sign into its scale.
 constexpr unsigned kFwdNegMask = 0xdc48u;

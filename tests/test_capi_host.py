@@ -215,3 +215,25 @@ def test_class_heights_are_the_zigzag_column_heights():
         assert V == max(v + 1 for v in range(16) if colh[v] > 0), c
         assert U == max(colh), c
         assert H == [max(colh[2 * p], colh[2 * p + 1]) for p in range(V // 2)], c
+
+
+def test_mixed_8x8_class_heights_are_the_zigzag_column_heights():
+    """The mixed-tiling kernel prunes each 8x8 column to its height in the
+    8x8 zig-zag zone Z_rmax of its class; the dispatcher's copy of the tables
+    must agree, and both must be the oracle's 8x8 zig-zag column heights."""
+    src = open(os.path.join(ROOT, "paper_1606_07414_gb300", "csrc", "tx16_mixed_bt.cuh")).read()
+    found = re.findall(r"struct Mix8Class<(\d)> \{\s*static constexpr int kRmax = (\d+), V = (\d+), U = (\d+);"
+                       r"\s*static constexpr int H\[\d+\] = \{([^}]*)\};", src)
+    assert len(found) == 2
+    disp = open(os.path.join(ROOT, "paper_1606_07414_gb300", "csrc", "tx16_mixed_bt.cu")).read()
+    table = re.search(r"static const uint8_t H\[2\]\[8\] = \{(.*?)\};", disp, re.S).group(1)
+    rows = [[int(x) for x in r.split(",")] for r in re.findall(r"\{([^{}]*)\}", table)]
+    for c, rmax, V, U, H in found:
+        rmax, V, U = int(rmax), int(V), int(U)
+        H = [int(x) for x in H.split(",")]
+        m = O.zonal_mask(rmax, 8)
+        colh = [int(m[:, v].sum()) for v in range(8)]
+        assert V == max(v + 1 for v in range(8) if colh[v] > 0), c
+        assert U == max(colh), c
+        assert H == colh[:V], c
+        assert rows[int(c)] == colh, c

@@ -64,6 +64,76 @@ def test_mixed_bitexact(tx, q, r16, r8, mode):
         assert 0 < int(split.sum()) < split.size or q is None or r16 == 4  # both tilings occur
 
 
+# One case per compiled class pair of the one-region-per-thread kernel
+# (16x16 class, 8x8 class): (A, 0), (B, 0), (B, 1), (C, 1), (D, 1); the image
+# is 5 x 17 regions, so the last warp tile of 32 regions is ragged.
+PAIR_CASES = [(12.0, 8, 4, "auto"), (16.0, 13, 3, "auto"), (10.0, 12, 16, "auto"), (7.0, 32, 9, "auto"),
+              (8.0, 50, 12, "auto"), (1.0 / 256, 16, 4, "auto"), (200.0, 64, 16, "auto"), (9.0, 30, 10, "8")]
+
+
+@pytest.mark.parametrize("q,r16,r8,mode", PAIR_CASES)
+def test_mixed_pairs_bitexact(tx, q, r16, r8, mode):
+    img = synth.ar1_image(900 + r16 * 3 + r8, 80, 272, 0.93, 8)
+    recs, split, sse = _run(tx, [img], [(q, r16, r8, mode)], [8])
+    want = _oracle(img, q, r16, r8, 8, mode)
+    assert np.array_equal(recs[0], want["recon"])
+    assert np.array_equal(split.astype(bool), want["split"].ravel())
+    assert int(sse[0]) == want["sse"]
+
+
+def test_mixed_batch_across_kernels(tx):
+    """One call whose images go to different class pairs of the
+    one-region-per-thread kernel and to the general kernel (no quantiser,
+    r16 > 64, 10-bit), interleaved: each image's split-map range and SSE slot
+    must be its own."""
+    qps = [(16.0, 16, 4, "auto"), (None, 16, 4, "auto"), (7.0, 32, 9, "auto"), (5.0, 100, 8, "auto"),
+           (12.0, 8, 2, "auto"), (3.0, 20, 40, "auto"), (16.0, 16, 4, "16"), (8.0, 64, 16, "auto")]
+    shapes = [(48, 64), (32, 96), (64, 48), (16, 32), (80, 16), (32, 32), (48, 48), (16, 16)]
+    bits = [8, 8, 8, 8, 8, 10, 8, 8]
+    imgs = [synth.ar1_image(950 + i, h, w, 0.9, b) for i, ((h, w), b) in enumerate(zip(shapes, bits))]
+    recs, split, sse = _run(tx, imgs, qps, bits)
+    k = 0
+    for i, (im, (q, r16, r8, mode), b) in enumerate(zip(imgs, qps, bits)):
+        want = _oracle(im, q, r16, r8, b, mode)
+        n = want["split"].size
+        assert np.array_equal(recs[i], want["recon"]), i
+        assert np.array_equal(split[k:k + n].astype(bool), want["split"].ravel()), i
+        assert int(sse[i]) == want["sse"], i
+        k += n
+
+
+def test_mixed_more_images_than_one_launch(tx):
+    """170 images of one class pair: more than one launch's worth of image
+    descriptors."""
+    n = 170
+    imgs = [synth.ar1_image(2000 + i, 16 * (1 + i % 3), 32, 0.9, 8) for i in range(n)]
+    qps = [(8.0 + (i % 5), 16, 4, "auto") for i in range(n)]
+    recs, split, sse = _run(tx, imgs, qps, [8] * n)
+    k = 0
+    for i, (im, (q, r16, r8, mode)) in enumerate(zip(imgs, qps)):
+        want = _oracle(im, q, r16, r8, 8, mode)
+        m = want["split"].size
+        assert np.array_equal(recs[i], want["recon"]), i
+        assert np.array_equal(split[k:k + m].astype(bool), want["split"].ravel()), i
+        assert int(sse[i]) == want["sse"], i
+        k += m
+
+
+def test_mixed_without_output_plane(tx):
+    """No output plane: the split map and SSE alone (general kernel)."""
+    import torch
+
+    img = synth.ar1_image(960, 64, 96, 0.93, 8)
+    d = to_dev(img)
+    split = torch.full((24,), 7, dtype=torch.uint8, device="cuda")
+    sse = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_mixed([tx.image(d)], None, [(16.0, 16, 4, "auto")], split=split, sse=sse)
+    torch.cuda.synchronize()
+    want = _oracle(img, 16.0, 16, 4, 8, "auto")
+    assert np.array_equal(split.cpu().numpy().astype(bool), want["split"].ravel())
+    assert int(sse.cpu().numpy()[0]) == want["sse"]
+
+
 def test_mixed_lossless_and_flat(tx):
     """r16 = 256, r8 = 64, no quantiser: lossless whichever tiling; a flat
     image ties everywhere and stays 16x16."""
