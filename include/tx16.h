@@ -286,8 +286,8 @@ tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels,
 
 /* Time the schedule candidates of each group on the plan's own data and keep
  * the fastest.  The schedule tuned is that of the kernel a run without levels
- * uses.  For the groups of r <= 64 (one 16x16 block per thread, warps claiming
- * 32-block tiles) the candidates are the kernel's compiled configurations
+ * uses.  For the groups coded one 16x16 block per thread (8-bit samples in
+ * the fused quantiser range; warps claiming 32-block tiles) the candidates are the kernel's compiled configurations
  * (warps per CTA, column pairs parked in shared memory, input stages: see
  * tx16_plan_variant) and, for each, the resident CTAs per SM and the tiles
  * per claim; for the others, the CTAs per SM and tiles per claim.
@@ -303,7 +303,8 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
 tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, int32_t* tiles,
                            int32_t* ctas_per_sm, int32_t* chunk, int32_t max_runs);
 
-/* The compiled configuration group `run` uses (groups of r <= 64): its index
+/* The compiled configuration group `run` uses (groups coded one block per
+ * thread): its index
  * (-1 for a group without configurations), warps per CTA, column pairs parked
  * in shared memory and input stages.  Any output may be NULL.  TX16_EINVAL
  * for a run index out of range. */

@@ -413,8 +413,7 @@ template <int MAXI>
 tx16_status launch_fused_modes(int zone, const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                                cudaStream_t stream) {
   const bool dst = imgs[0].dst != nullptr;
-  // up to 8 kept columns and no level output: one block per thread in
-  // registers -- unless the batch has fewer 32-block warp tiles than the GPU
+  // no level output: one block per thread in registers -- unless the batch has fewer 32-block warp tiles than the GPU
   // has SMs: then each warp would code a single tile, a whole block per
   // thread in series, and the pair kernel (16 blocks over 128 threads) ends
   // sooner

@@ -39,14 +39,29 @@ extern template int bt_list_ctas<2>(int, bool);
 extern template void bt_variant_info<2>(int, int*, int*, int*);
 extern template int bt_list_ctas<3>(int, bool);
 extern template void bt_variant_info<3>(int, int*, int*, int*);
+extern template tx16_status bt_batch<4>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_ragged<4>(bool, int, const ImgParam*, int, unsigned long long*,
+                                                cudaStream_t);
+extern template tx16_status bt_list<4>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
+                                       unsigned long long*, cudaStream_t);
+extern template int bt_list_ctas<4>(int, bool);
+extern template void bt_variant_info<4>(int, int*, int*, int*);
+extern template tx16_status bt_batch<5>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_ragged<5>(bool, int, const ImgParam*, int, unsigned long long*,
+                                                cudaStream_t);
+extern template tx16_status bt_list<5>(int, bool, const ImgParam*, int, int, unsigned*, int, int,
+                                       unsigned long long*, cudaStream_t);
+extern template int bt_list_ctas<5>(int, bool);
+extern template void bt_variant_info<5>(int, int*, int*, int*);
 
 // Zonal classes routed to this kernel for 8-bit samples (bit c for class c;
-// compile-time tunable): A..D.  Classes E and F (r > 64) measured slower here
-// than on the two-blocks-per-pair kernel (r = 128: 3929 against about 4100
-// Mblocks/s, r = 256: 3474 against 4142): one block per thread leaves them 8
-// or 9 warps per SM with four column pairs parked.  9..12-bit samples: A..C.
+// compile-time tunable): all six.  With each warp on a contiguous run of
+// tiles, classes E and F run faster here than on the two-blocks-per-pair
+// kernel (r = 128: 5539 against 4163 Mblocks/s, r = 256: 4359 against 4142);
+// with tiles w, w + W, ... they had measured slower (3929 and 3474).
+// 9..12-bit samples: A..C.
 #ifndef TX16_BT_ZONE_MASK
-#define TX16_BT_ZONE_MASK 0x0f
+#define TX16_BT_ZONE_MASK 0x3f
 #endif
 
 bool fused_bt_supports(int zone, bool levels) {
@@ -85,6 +100,8 @@ tx16_status launch_fused_bt_list(int zone, int variant, bool dst, const ImgParam
     case 1: return bt_list<1>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
     case 2: return bt_list<2>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
     case 3: return bt_list<3>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 4: return bt_list<4>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
+    case 5: return bt_list<5>(variant, dst, d_imgs, nimg, ntiles, counter, chunk, ctas_per_sm, sse, stream);
     default: return TX16_EINVAL;
   }
 }
@@ -95,6 +112,8 @@ int fused_bt_list_max_ctas(int zone, int variant, bool dst) {
     case 1: return bt_list_ctas<1>(variant, dst);
     case 2: return bt_list_ctas<2>(variant, dst);
     case 3: return bt_list_ctas<3>(variant, dst);
+    case 4: return bt_list_ctas<4>(variant, dst);
+    case 5: return bt_list_ctas<5>(variant, dst);
     default: return 0;
   }
 }
@@ -107,6 +126,8 @@ void fused_bt_variant_info(int zone, int variant, int* warps, int* park, int* st
     case 1: bt_variant_info<1>(variant, warps, park, stages); break;
     case 2: bt_variant_info<2>(variant, warps, park, stages); break;
     case 3: bt_variant_info<3>(variant, warps, park, stages); break;
+    case 4: bt_variant_info<4>(variant, warps, park, stages); break;
+    case 5: bt_variant_info<5>(variant, warps, park, stages); break;
     default: *warps = *park = *stages = 0; break;
   }
 }
@@ -118,6 +139,8 @@ tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, uns
     case 1: return bt_batch<1>(dst, 1, imgs, n, sse, stream);
     case 2: return bt_batch<2>(dst, 1, imgs, n, sse, stream);
     case 3: return bt_batch<3>(dst, 1, imgs, n, sse, stream);
+    case 4: return bt_batch<4>(dst, 1, imgs, n, sse, stream);
+    case 5: return bt_batch<5>(dst, 1, imgs, n, sse, stream);
     default: return TX16_EINVAL;
   }
 }
@@ -126,7 +149,7 @@ tx16_status launch_fused_bt_ragged(const ImgParam* imgs, int n, unsigned long lo
   // runs of equal sample size and zonal class, at most kMaxImg per launch
   std::vector<ImgParam> run;
   for (int sb = 1; sb <= 2; ++sb) {
-    for (int zone = 0; zone <= 3; ++zone) {
+    for (int zone = 0; zone < kBtClasses; ++zone) {
       run.clear();
       for (int i = 0; i < n; ++i)
         if (sample_bytes(imgs[i].flags & 0xff) == sb && fused_zone_class(&imgs[i], 1) == zone) run.push_back(imgs[i]);
@@ -138,7 +161,9 @@ tx16_status launch_fused_bt_ragged(const ImgParam* imgs, int n, unsigned long lo
           case 0: st = bt_batch_ragged<0>(dst, sb, run.data() + s, m, sse, stream); break;
           case 1: st = bt_batch_ragged<1>(dst, sb, run.data() + s, m, sse, stream); break;
           case 2: st = bt_batch_ragged<2>(dst, sb, run.data() + s, m, sse, stream); break;
-          default: st = bt_batch_ragged<3>(dst, sb, run.data() + s, m, sse, stream); break;
+          case 3: st = bt_batch_ragged<3>(dst, sb, run.data() + s, m, sse, stream); break;
+          case 4: st = bt_batch_ragged<4>(dst, sb, run.data() + s, m, sse, stream); break;
+          default: st = bt_batch_ragged<5>(dst, sb, run.data() + s, m, sse, stream); break;
         }
         if (st != TX16_OK) return st;
       }

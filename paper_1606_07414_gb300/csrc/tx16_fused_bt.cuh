@@ -130,7 +130,10 @@ struct RowNets<16> {
 // 1920x1088 frames with one input stage (the next tile is fetched once the
 // current rows are used; other warps cover the latency): A 4-warp CTAs x 4,
 // one pair parked; B 1-warp CTAs x 16 (128 registers), one pair parked; C
-// 4-warp CTAs x 3, two pairs parked.
+// 4-warp CTAs x 3, two pairs parked; D 1-warp CTAs x 12, two parked; E
+// 1-warp CTAs x 8 (255 registers), two parked (5539 Mblocks/s at r = 128,
+// against 5357 with three parked and 5381 with 2-warp CTAs); F 1-warp CTAs x
+// 8, one parked (4359 at r = 256, against 4229 with two and 4027 with three).
 #ifndef TX16_BT_WARPS_A
 #define TX16_BT_WARPS_A 4
 #endif
@@ -171,19 +174,19 @@ struct RowNets<16> {
 #define TX16_BT_WARPS_E 1
 #endif
 #ifndef TX16_BT_MINCTAS_E
-#define TX16_BT_MINCTAS_E 9
+#define TX16_BT_MINCTAS_E 8
 #endif
 #ifndef TX16_BT_PARK_E
-#define TX16_BT_PARK_E 4
+#define TX16_BT_PARK_E 2
 #endif
 #ifndef TX16_BT_WARPS_F
 #define TX16_BT_WARPS_F 1
 #endif
 #ifndef TX16_BT_MINCTAS_F
-#define TX16_BT_MINCTAS_F 9
+#define TX16_BT_MINCTAS_F 8
 #endif
 #ifndef TX16_BT_PARK_F
-#define TX16_BT_PARK_F 4
+#define TX16_BT_PARK_F 1
 #endif
 #ifndef TX16_BT_STAGES
 #define TX16_BT_STAGES 1
@@ -325,6 +328,22 @@ struct BtAlt<3, 1> {
 template <>
 struct BtAlt<3, 2> {
   static constexpr int kWarps = 4, kMinCtas = 3, kPark = 2, kStages = 1;
+};
+template <>
+struct BtAlt<4, 1> {
+  static constexpr int kWarps = 1, kMinCtas = 8, kPark = 1, kStages = 1;
+};
+template <>
+struct BtAlt<4, 2> {
+  static constexpr int kWarps = 2, kMinCtas = 4, kPark = 3, kStages = 1;
+};
+template <>
+struct BtAlt<5, 1> {
+  static constexpr int kWarps = 1, kMinCtas = 8, kPark = 2, kStages = 1;
+};
+template <>
+struct BtAlt<5, 2> {
+  static constexpr int kWarps = 2, kMinCtas = 4, kPark = 3, kStages = 1;
 };
 constexpr int kBtVariants = 3;
 
