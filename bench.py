@@ -630,7 +630,10 @@ def _serving(tx16, torch, np, args):
         ins = [torch.from_numpy(f.view(np.int16) if bits > 8 else f).pin_memory() for f in src]
         outs = [torch.empty_like(t).pin_memory() for t in ins]
         pools.append((H, W, bits, ins, outs))
-    srv = tx16.Server({"device_pool_mb": 16384, "streams": args.serve_streams, "max_batch": 256})
+    cfg = {"device_pool_mb": 16384, "streams": args.serve_streams, "max_batch": 256}
+    if args.serve_band_mb is not None:
+        cfg["band_mb"] = args.serve_band_mb
+    srv = tx16.Server(cfg)
     rates = [int(x) for x in args.serve_rates.split(",")]
     # untimed warm-up: every request kind, q and r through both forms once
     # (first launches of each kernel variant load their modules)
@@ -970,6 +973,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--serve-streams", type=int, default=6, help="stream slots of the server")
     ap.add_argument("--serve-only", action="store_true", help="the serving section alone (one short JSON line)")
+    ap.add_argument("--serve-band-mb", type=float, default=None,
+                    help="server band size in MB (planes above it are copied and coded in bands; 0: never)")
     ap.add_argument("--quick", action="store_true", help="headline number only")
     ap.add_argument("--e2e-chunk", type=int, default=16,
                     help="frames per chunk of the host-buffer pipeline (a divisor of the frame count)")

@@ -353,6 +353,12 @@ typedef struct tx16_server tx16_server;
  *                     the waiter polls this long, itself retiring the
  *                     request's group when its work has finished, before it
  *                     blocks; 0 blocks at once
+ *   "band_mb"         a group of at most 16 requests holding a plane larger
+ *                     than this (default 4; 0: never) is copied in, coded and
+ *                     copied out in up to 8 bands of whole block rows, the
+ *                     copies out of coded bands overlapping the copies in of
+ *                     the next ones (lower latency at light load; larger
+ *                     groups take one launch)
  * A request that arrives while nothing is queued or in flight is admitted and
  * launched by tx16_serve_submit on the caller's thread; otherwise the worker
  * admits it and the group's stream slot has its own thread issuing the

@@ -10,11 +10,18 @@
 //               arena has room for their input and output planes and a batch
 //               slot is free ("admission by free HBM");
 //             - hands each admitted group to its slot's issuer thread, which
-//               puts it on the slot's stream: host->device copies of the
+//               puts it on the slot's streams: host->device copies of the
 //               inputs, ONE tx16_codec_batch launch over the group,
 //               device->host copies of the reconstructions and SSEs, then an
 //               event -- the slots' issuers run in parallel, so the CUDA calls
-//               of one group do not hold up the admission of the next;
+//               of one group do not hold up the admission of the next.
+//               A group of at most 16 requests with a plane larger than
+//               band_mb goes in bands of whole block rows on three streams:
+//               all copies in, one after another; each band's launch once its
+//               copies are in; each band's copies out once it is coded -- so
+//               that copies out overlap copies in (the two directions have
+//               their own copy engines: 16.6 MB each way took 142 us
+//               overlapped against 190 us one after the other);
 //             - retires slots whose event has fired: PSNR, latency, frees the
 //               requests' arena space, wakes their waiters.
 //           While a group is in flight it polls (submissions, slot events),
@@ -122,16 +129,25 @@ struct Request {
   char* d_out = nullptr;
   std::atomic<bool> done{false};
   std::atomic<struct Slot*> slot{nullptr};  // the group's slot while in flight
+  int nbands = 1;   // bands of its group's launch (set when launched)
+  int sse_pos = 0;  // its index in each band's launch
   tx16_status status = TX16_OK;
   double psnr = 0.0;
   double latency_us = 0.0;
 };
 
+constexpr int kMaxBands = 8;
+constexpr int kBandMaxGroup = 16;  // groups of more requests are not cut into bands
+
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;      // a group in one band: everything; in bands: the launches
+  cudaStream_t in_stream = nullptr;   // copies in of a group in bands
+  cudaStream_t out_stream = nullptr;  // copies out of a group in bands
   cudaEvent_t event = nullptr;
-  uint64_t* d_sse = nullptr;
-  uint64_t* h_sse = nullptr;  // pinned
+  cudaEvent_t in_ev[kMaxBands] = {};    // band b copied in
+  cudaEvent_t band_ev[kMaxBands] = {};  // band b coded
+  uint64_t* d_sse = nullptr;  // [band][request], kMaxBands x max_batch
+  uint64_t* h_sse = nullptr;  // pinned, the same
   std::vector<Request*> reqs;
   bool busy = false;            // a group is admitted (under the server's lock)
   bool issue_pending = false;   // the issuer has a group to launch (under the lock)
@@ -161,6 +177,7 @@ struct tx16_server {
   std::atomic<uint64_t> pokes{0};  // bumped by submit, pause, stop and slot callbacks
   double spin_us = 300;            // polling window of the worker
   double wait_spin_us = 2000;      // polling window of waiters (they retire finished groups themselves)
+  size_t band_bytes = size_t(4) << 20;  // planes above this go in bands (0: never)
   std::thread worker;
   // statistics
   std::vector<double> lat;  // reservoir of latencies (us)
@@ -246,33 +263,91 @@ void CUDART_CB slot_done(void* arg) {
   s->cv_work.notify_one();
 }
 
-// Put one admitted group on a slot: copies in, one batched launch, copies out.
+// Put one admitted group on a slot: copies in, one batched launch, copies out
+// -- in bands when a plane is larger than band_bytes.  A request of k bands is
+// cut into k runs of whole block rows; band b's launch codes band b of every
+// request that has one.  The requests are taken in decreasing band count, so
+// that those of band b are a prefix of the group and keep their index
+// (sse_pos) in every band's launch.
 tx16_status launch_group(Slot& slot) {
   TX16_TRACE("tx16 serve: launch group");
+  tx16_server* s = slot.server;
   const int n = int(slot.reqs.size());
+  std::vector<Request*> order(slot.reqs);
+  int nbmax = 1;
+  // bands shorten a small group's latency; a large group (a busy server) is
+  // throughput-bound and takes one launch
+  const bool may_band = s->band_bytes > 0 && n <= kBandMaxGroup;
+  for (Request* r : order) {
+    const int brows = r->h / 16;
+    int k = 1;
+    if (may_band) k = int(std::min<size_t>(kMaxBands, (r->bytes + s->band_bytes - 1) / s->band_bytes));
+    k = std::max(1, std::min(k, brows));
+    const int rows = (brows + k - 1) / k * 16;  // rows per band
+    r->nbands = (r->h + rows - 1) / rows;
+    nbmax = std::max(nbmax, r->nbands);
+  }
+  std::stable_sort(order.begin(), order.end(), [](const Request* a, const Request* b) { return a->nbands > b->nbands; });
+  for (int i = 0; i < n; ++i) order[i]->sse_pos = i;
+  const bool banded = nbmax > 1;
+  cudaStream_t s_in = banded ? slot.in_stream : slot.stream;
+  cudaStream_t s_out = banded ? slot.out_stream : slot.stream;
+  // rows [y0, y0 + hb) of request r in band b, as a byte range of its plane
+  auto band = [](const Request* r, int b, size_t& off, size_t& len, int& hb) {
+    const int64_t pitch = int64_t(r->w) * (r->bits == 8 ? 1 : 2);
+    const int rows = (r->h / 16 + r->nbands - 1) / r->nbands * 16;
+    const int y0 = b * rows;
+    hb = std::min(rows, r->h - y0);
+    off = size_t(y0) * size_t(pitch);
+    len = size_t(hb) * size_t(pitch);
+  };
+  for (int b = 0; b < nbmax; ++b) {  // copies in
+    for (int i = 0; i < n && order[i]->nbands > b; ++i) {
+      Request* r = order[i];
+      size_t off, len;
+      int hb;
+      band(r, b, off, len, hb);
+      if (cudaMemcpyAsync(r->d_in + off, static_cast<const char*>(r->host_in) + off, len, cudaMemcpyHostToDevice,
+                          s_in) != cudaSuccess)
+        return TX16_ECUDA;
+    }
+    if (banded && cudaEventRecord(slot.in_ev[b], s_in) != cudaSuccess) return TX16_ECUDA;
+  }
   std::vector<tx16_image> in(n), out(n);
   std::vector<tx16_qparams> qp(n);
-  for (int i = 0; i < n; ++i) {
-    Request* r = slot.reqs[i];
-    const int64_t pitch = int64_t(r->w) * (r->bits == 8 ? 1 : 2);
-    if (cudaMemcpyAsync(r->d_in, r->host_in, r->bytes, cudaMemcpyHostToDevice, slot.stream) != cudaSuccess)
+  for (int b = 0; b < nbmax; ++b) {  // launches, copies out
+    int m = 0;
+    for (; m < n && order[m]->nbands > b; ++m) {
+      Request* r = order[m];
+      size_t off, len;
+      int hb;
+      band(r, b, off, len, hb);
+      const int64_t pitch = int64_t(r->w) * (r->bits == 8 ? 1 : 2);
+      in[m] = tx16_image{r->d_in + off, r->w, hb, pitch, r->bits};
+      out[m] = tx16_image{r->d_out + off, r->w, hb, pitch, r->bits};
+      qp[m] = r->qp;
+    }
+    if (banded && cudaStreamWaitEvent(slot.stream, slot.in_ev[b], 0) != cudaSuccess) return TX16_ECUDA;
+    const tx16_status st = tx16_codec_batch(in.data(), out.data(), m, qp.data(), slot.d_sse + size_t(b) * s->max_batch,
+                                            nullptr, slot.stream);
+    if (st != TX16_OK) return st;
+    if (banded && (cudaEventRecord(slot.band_ev[b], slot.stream) != cudaSuccess ||
+                   cudaStreamWaitEvent(s_out, slot.band_ev[b], 0) != cudaSuccess))
       return TX16_ECUDA;
-    in[i] = tx16_image{r->d_in, r->w, r->h, pitch, r->bits};
-    out[i] = tx16_image{r->d_out, r->w, r->h, pitch, r->bits};
-    qp[i] = r->qp;
+    for (int i = 0; i < m; ++i) {
+      Request* r = order[i];
+      if (r->host_out == nullptr) continue;
+      size_t off, len;
+      int hb;
+      band(r, b, off, len, hb);
+      if (cudaMemcpyAsync(static_cast<char*>(r->host_out) + off, r->d_out + off, len, cudaMemcpyDeviceToHost, s_out) !=
+          cudaSuccess)
+        return TX16_ECUDA;
+    }
   }
-  const tx16_status st = tx16_codec_batch(in.data(), out.data(), n, qp.data(), slot.d_sse, nullptr, slot.stream);
-  if (st != TX16_OK) return st;
-  for (int i = 0; i < n; ++i) {
-    Request* r = slot.reqs[i];
-    if (r->host_out != nullptr &&
-        cudaMemcpyAsync(r->host_out, r->d_out, r->bytes, cudaMemcpyDeviceToHost, slot.stream) != cudaSuccess)
-      return TX16_ECUDA;
-  }
-  if (cudaMemcpyAsync(slot.h_sse, slot.d_sse, sizeof(uint64_t) * size_t(n), cudaMemcpyDeviceToHost, slot.stream) !=
-          cudaSuccess ||
-      cudaEventRecord(slot.event, slot.stream) != cudaSuccess ||
-      cudaLaunchHostFunc(slot.stream, slot_done, &slot) != cudaSuccess)
+  const size_t nsse = size_t(nbmax - 1) * size_t(s->max_batch) + size_t(n);
+  if (cudaMemcpyAsync(slot.h_sse, slot.d_sse, sizeof(uint64_t) * nsse, cudaMemcpyDeviceToHost, s_out) != cudaSuccess ||
+      cudaEventRecord(slot.event, s_out) != cudaSuccess || cudaLaunchHostFunc(s_out, slot_done, &slot) != cudaSuccess)
     return TX16_ECUDA;
   return TX16_OK;
 }
@@ -285,7 +360,9 @@ void retire(tx16_server* s, Slot& slot, tx16_status st) {
     r->status = st;
     if (st == TX16_OK) {
       tx16_image d{r->d_in, r->w, r->h, int64_t(r->w) * (r->bits == 8 ? 1 : 2), r->bits};
-      tx16_psnr(&slot.h_sse[i], &d, 1, &r->psnr);
+      uint64_t e = 0;
+      for (int b = 0; b < r->nbands; ++b) e += slot.h_sse[size_t(b) * size_t(s->max_batch) + size_t(r->sse_pos)];
+      tx16_psnr(&e, &d, 1, &r->psnr);
       s->blocks_done += double(r->blocks);
     }
     r->latency_us = now_us(r->t_submit, t);
@@ -329,7 +406,11 @@ bool admit(tx16_server* s, Slot& slot) {
 void issue(tx16_server* s, Slot& slot, std::unique_lock<std::mutex>& lk) {
   lk.unlock();
   const tx16_status st = launch_group(slot);
-  if (st != TX16_OK) cudaStreamSynchronize(slot.stream);
+  if (st != TX16_OK) {
+    cudaStreamSynchronize(slot.in_stream);
+    cudaStreamSynchronize(slot.stream);
+    cudaStreamSynchronize(slot.out_stream);
+  }
   lk.lock();
   if (st != TX16_OK) {
     retire(s, slot, st);
@@ -440,6 +521,12 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
   s->max_queue = cfg.count("max_queue") ? size_t(cfg["max_queue"]) : size_t(1) << 20;
   s->spin_us = cfg.count("spin_us") ? cfg["spin_us"] : 300.0;
   s->wait_spin_us = cfg.count("wait_spin_us") ? cfg["wait_spin_us"] : 2000.0;
+  const double band_mb = cfg.count("band_mb") ? cfg["band_mb"] : 4.0;
+  if (!(band_mb >= 0 && band_mb <= 65536)) {
+    delete s;
+    return TX16_EINVAL;
+  }
+  s->band_bytes = size_t(band_mb * (1 << 20));
   const size_t pool = size_t(pool_mb * (1 << 20));
   if (pool < 4096 || nslots < 1 || nslots > 16 || s->max_batch < 1 || s->max_batch > 4096 || s->max_queue < 1 ||
       !(s->spin_us >= 0 && s->spin_us <= 1e6) || !(s->wait_spin_us >= 0 && s->wait_spin_us <= 1e6)) {
@@ -453,10 +540,16 @@ tx16_status tx16_serve_create(const char* json_cfg, tx16_server** out) {
   for (int i = 0; i < nslots; ++i) s->slots.emplace_back();
   for (Slot& slot : s->slots) {
     slot.server = s;
-    if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&slot.event, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc(&slot.d_sse, sizeof(uint64_t) * size_t(s->max_batch)) != cudaSuccess ||
-        cudaMallocHost(&slot.h_sse, sizeof(uint64_t) * size_t(s->max_batch)) != cudaSuccess) {
+    bool ok = cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&slot.in_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&slot.out_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&slot.event, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc(&slot.d_sse, sizeof(uint64_t) * kMaxBands * size_t(s->max_batch)) == cudaSuccess &&
+              cudaMallocHost(&slot.h_sse, sizeof(uint64_t) * kMaxBands * size_t(s->max_batch)) == cudaSuccess;
+    for (int b = 0; ok && b < kMaxBands; ++b)
+      ok = cudaEventCreateWithFlags(&slot.in_ev[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&slot.band_ev[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
       tx16_serve_destroy(s);
       return TX16_ENOMEM;
     }
@@ -626,8 +719,16 @@ void tx16_serve_destroy(tx16_server* s) {
   }
   for (Slot& slot : s->slots) {
     if (slot.stream) cudaStreamSynchronize(slot.stream);
+    if (slot.in_stream) cudaStreamSynchronize(slot.in_stream);
+    if (slot.out_stream) cudaStreamSynchronize(slot.out_stream);
     if (slot.event) cudaEventDestroy(slot.event);
+    for (int b = 0; b < kMaxBands; ++b) {
+      if (slot.in_ev[b]) cudaEventDestroy(slot.in_ev[b]);
+      if (slot.band_ev[b]) cudaEventDestroy(slot.band_ev[b]);
+    }
     if (slot.stream) cudaStreamDestroy(slot.stream);
+    if (slot.in_stream) cudaStreamDestroy(slot.in_stream);
+    if (slot.out_stream) cudaStreamDestroy(slot.out_stream);
     if (slot.d_sse) cudaFree(slot.d_sse);
     if (slot.h_sse) cudaFreeHost(slot.h_sse);
   }

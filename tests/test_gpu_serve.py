@@ -139,3 +139,31 @@ def test_bad_polling_window_is_rejected(tx):
         with pytest.raises(tx.Tx16Error) as e:
             tx.Server({"spin_us": bad})
         assert e.value.status == tx.TX16_EINVAL
+
+
+@pytest.mark.parametrize("band_mb", [0.0, 0.01, 0.05])
+def test_bands_do_not_change_results(tx, band_mb):
+    """Planes above band_mb are copied in, coded and copied out in bands of
+    whole block rows (up to 8; the band count of a group differs from request
+    to request): samples and PSNR stay those of the oracle, the per-band
+    squared errors summing to the plane's."""
+    srv = tx.Server({"device_pool_mb": 128, "streams": 3, "max_batch": 16, "band_mb": band_mb})
+    reqs = _mix(31, 60)
+    outs, tickets = [], []
+    for img, bits, q, r in reqs:
+        o = np.zeros_like(img)
+        outs.append(o)
+        tickets.append(srv.submit(img, q, r, out=o, bits=bits))
+    for (img, bits, q, r), o, t in zip(reqs, outs, tickets):
+        p, lat = srv.wait(t)
+        ref = O.codec_image(img, q, r, bits, "fp32" if q else "fp64")
+        assert np.array_equal(o, ref["recon"])
+        assert (p == ref["psnr"]) if not np.isfinite(ref["psnr"]) else p == pytest.approx(ref["psnr"], abs=1e-9)
+    srv.close()
+
+
+def test_bad_band_size_is_rejected(tx):
+    for bad in (-1, 1e9, float("nan")):
+        with pytest.raises(tx.Tx16Error) as e:
+            tx.Server({"band_mb": bad})
+        assert e.value.status == tx.TX16_EINVAL
