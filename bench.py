@@ -654,7 +654,7 @@ def _serving(tx16, torch, np, args):
     out = {"workload": "Poisson arrivals; 60% 256x256 u8, 30% 1920x1088 u8, 10% 3840x2160 10-bit; "
                        "q in {8,16,32}, r in {4,16,64,256}; pinned host buffers", "rates": []}
     for rate in rates:
-        n = max(200, min(int(rate * args.serve_seconds), 60000))
+        n = max(1000, min(int(rate * args.serve_seconds), 60000))  # p99 from at least 1000 requests
         u = synth.uniforms(SEED + rate, 4 * n)
         gaps = -np.log(u[:n]) / rate
         kind = np.where(u[n:2 * n] < 0.6, 0, np.where(u[n:2 * n] < 0.9, 1, 2))
@@ -685,7 +685,7 @@ def _serving(tx16, torch, np, args):
                             "p999_us": round(st["p999_us"], 1), "Mblocks_s": round(st["mblocks_per_s"], 1),
                             "req_per_s": round(achieved, 1)}}
         # the plain form: each request coded alone (copy in, one launch, copy out) as it arrives
-        m = min(n, max(200, int(rate * 0.5)))
+        m = min(n, max(1000, int(rate * 0.5)))
         lat = []
         t0 = time.perf_counter()
         due = t0

@@ -126,31 +126,41 @@ struct RowNets<16> {
 
 // Per class (compile-time tunable): warps per CTA, resident CTAs per SM the
 // registers are budgeted for (the limit per thread is 65536 / (32 * warps *
-// CTAs)), column pairs parked in shared memory, input stages.  Measured on
-// 1920x1088 frames with one input stage (the next tile is fetched once the
-// current rows are used; other warps cover the latency): A 4-warp CTAs x 4,
-// one pair parked; B 1-warp CTAs x 16 (128 registers), one pair parked; C
-// 4-warp CTAs x 3, two pairs parked; D 1-warp CTAs x 12, two parked; E
-// 1-warp CTAs x 8 (255 registers), two parked (5539 Mblocks/s at r = 128,
-// against 5357 with three parked and 5381 with 2-warp CTAs); F 1-warp CTAs x
-// 8, one parked (4359 at r = 256, against 4229 with two and 4027 with three).
+// CTAs): at most 8 warps per SM allow 255 registers, 9..12 allow 168, 13..16
+// allow 128), column pairs parked in shared memory, input stages.  Measured
+// on 1920x1088 frames with one input stage (the next tile's rows are fetched
+// as the current ones are used; other warps cover the latency) and each warp
+// on a contiguous run of tiles (Mblocks/s):
+//   A  4-warp CTAs x 3, none parked: 11318 (1-warp x 12: 10901; 4 x 4 with
+//      one parked, 16 warps at 128 registers: 10482)
+//   B  4-warp CTAs x 3, none parked: 11152 (3 x 4: 11128; 1 x 12: 10983;
+//      6 x 2: 10249; 1 x 16 with one parked: 10431)
+//   C  4-warp CTAs x 3, one parked: 9729 (none: 9608; two: 9440; 1 x 12 with
+//      one: 9683)
+//   D  1-warp CTAs x 12, one parked: 7522 (two: 7354; 1 x 8 none, 255
+//      registers: 6882)
+//   E  1-warp CTAs x 8 (255 registers), two parked: 5539 (three 5357, one
+//      5524; 2-warp x 4: 5381)
+//   F  1-warp CTAs x 8, one parked: 4359 (two 4229, three 4027)
+// Fewer warps with nothing parked beat 16 warps with a pair parked once the
+// warps stopped refilling their tables at every tile.
 #ifndef TX16_BT_WARPS_A
 #define TX16_BT_WARPS_A 4
 #endif
 #ifndef TX16_BT_MINCTAS_A
-#define TX16_BT_MINCTAS_A 4
+#define TX16_BT_MINCTAS_A 3
 #endif
 #ifndef TX16_BT_PARK_A
-#define TX16_BT_PARK_A 1
+#define TX16_BT_PARK_A 0
 #endif
 #ifndef TX16_BT_WARPS_B
-#define TX16_BT_WARPS_B 1
+#define TX16_BT_WARPS_B 4
 #endif
 #ifndef TX16_BT_MINCTAS_B
-#define TX16_BT_MINCTAS_B 16
+#define TX16_BT_MINCTAS_B 3
 #endif
 #ifndef TX16_BT_PARK_B
-#define TX16_BT_PARK_B 1
+#define TX16_BT_PARK_B 0
 #endif
 #ifndef TX16_BT_WARPS_C
 #define TX16_BT_WARPS_C 4
@@ -159,7 +169,7 @@ struct RowNets<16> {
 #define TX16_BT_MINCTAS_C 3
 #endif
 #ifndef TX16_BT_PARK_C
-#define TX16_BT_PARK_C 2
+#define TX16_BT_PARK_C 1
 #endif
 #ifndef TX16_BT_WARPS_D
 #define TX16_BT_WARPS_D 1
@@ -168,7 +178,7 @@ struct RowNets<16> {
 #define TX16_BT_MINCTAS_D 12
 #endif
 #ifndef TX16_BT_PARK_D
-#define TX16_BT_PARK_D 2
+#define TX16_BT_PARK_D 1
 #endif
 #ifndef TX16_BT_WARPS_E
 #define TX16_BT_WARPS_E 1
@@ -299,7 +309,7 @@ template <int C, int VAR>
 struct BtAlt;
 template <>
 struct BtAlt<0, 1> {
-  static constexpr int kWarps = 1, kMinCtas = 16, kPark = 1, kStages = 1;
+  static constexpr int kWarps = 4, kMinCtas = 4, kPark = 1, kStages = 1;
 };
 template <>
 struct BtAlt<0, 2> {
@@ -307,23 +317,23 @@ struct BtAlt<0, 2> {
 };
 template <>
 struct BtAlt<1, 1> {
-  static constexpr int kWarps = 4, kMinCtas = 4, kPark = 1, kStages = 1;
+  static constexpr int kWarps = 1, kMinCtas = 16, kPark = 1, kStages = 1;
 };
 template <>
 struct BtAlt<1, 2> {
-  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 1, kStages = 2;
+  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 0, kStages = 1;
 };
 template <>
 struct BtAlt<2, 1> {
-  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 2, kStages = 1;
+  static constexpr int kWarps = 4, kMinCtas = 3, kPark = 2, kStages = 1;
 };
 template <>
 struct BtAlt<2, 2> {
-  static constexpr int kWarps = 2, kMinCtas = 4, kPark = 2, kStages = 2;
+  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 1, kStages = 1;
 };
 template <>
 struct BtAlt<3, 1> {
-  static constexpr int kWarps = 1, kMinCtas = 11, kPark = 3, kStages = 1;
+  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 2, kStages = 1;
 };
 template <>
 struct BtAlt<3, 2> {
@@ -351,7 +361,7 @@ constexpr int kBtVariants = 3;
 // (classes A..C, variant 0 only): TX16_BT16_WARPS warps per CTA,
 // TX16_BT16_MINCTAS CTAs, one stage, TX16_BT16_PARK_A parked pairs in class A
 // (measured on 3840x2160 10-bit frames: 4499 against 4401 Mblocks/s with one
-// parked) and TX16_BT16_PARK (at most the class's setting) in B and C.
+// parked) and TX16_BT16_PARK in B and C.
 #ifndef TX16_BT16_WARPS
 #define TX16_BT16_WARPS 4
 #endif
@@ -386,7 +396,7 @@ struct BtCfg {
   static constexpr int kMinCtas = SB == 1 ? BtSel<C, VAR>::kMinCtas : TX16_BT16_MINCTAS;
   static constexpr int kPark =
       SB == 1 ? BtSel<C, VAR>::kPark
-              : (C == 0 ? TX16_BT16_PARK_A : (BtLimits<C>::kPark < TX16_BT16_PARK ? BtLimits<C>::kPark : TX16_BT16_PARK));
+              : (C == 0 ? TX16_BT16_PARK_A : TX16_BT16_PARK);
   static constexpr int kStages = SB == 1 ? BtSel<C, VAR>::kStages : 1;
   static constexpr bool kRolling = kStages == 1 && ((TX16_BT_ROLLING >> (SB - 1)) & 1) != 0;
   // input rows: per thread 16 rows of 16 SB bytes per stage; parked pairs:

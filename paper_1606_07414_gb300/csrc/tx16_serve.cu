@@ -9,9 +9,10 @@
 //             - admits queued requests, in arrival order, while the device
 //               arena has room for their input and output planes and a batch
 //               slot is free ("admission by free HBM");
-//             - hands each admitted group to its slot's issuer thread, which
-//               puts it on the slot's streams: host->device copies of the
-//               inputs, ONE tx16_codec_batch launch over the group,
+//             - hands each admitted group to its slot's issuer thread (or,
+//               when nothing else is queued or being issued, issues it
+//               itself), which puts it on the slot's streams: host->device
+//               copies of the inputs, ONE tx16_codec_batch launch over the group,
 //               device->host copies of the reconstructions and SSEs, then an
 //               event -- the slots' issuers run in parallel, so the CUDA calls
 //               of one group do not hold up the admission of the next.
@@ -174,6 +175,7 @@ struct tx16_server {
   bool stop = false;
   bool stop_issuers = false;  // set after the worker has drained everything
   bool paused = false;  // admission held (tx16_serve_pause)
+  int issuing = 0;      // groups being put on their streams (under the lock)
   std::atomic<uint64_t> pokes{0};  // bumped by submit, pause, stop and slot callbacks
   double spin_us = 300;            // polling window of the worker
   double wait_spin_us = 2000;      // polling window of waiters (they retire finished groups themselves)
@@ -404,6 +406,7 @@ bool admit(tx16_server* s, Slot& slot) {
 // Put the admitted group of `slot` on its stream, without the lock (lk is
 // held on entry and on return).  On an error the group is retired with it.
 void issue(tx16_server* s, Slot& slot, std::unique_lock<std::mutex>& lk) {
+  ++s->issuing;
   lk.unlock();
   const tx16_status st = launch_group(slot);
   if (st != TX16_OK) {
@@ -412,6 +415,7 @@ void issue(tx16_server* s, Slot& slot, std::unique_lock<std::mutex>& lk) {
     cudaStreamSynchronize(slot.out_stream);
   }
   lk.lock();
+  --s->issuing;
   if (st != TX16_OK) {
     retire(s, slot, st);
     s->cv_done.notify_all();
@@ -472,13 +476,20 @@ void worker_main(tx16_server* s) {
       progressed = true;
     }
     if (progressed) s->cv_done.notify_all();
-    // admit: one group per free slot, launched by the slot's issuer
+    // admit: one group per free slot, launched by the slot's issuer -- or
+    // by the worker itself when nothing else is queued or being issued (light
+    // load: no hand-off, whose wake-up can cost a sleeping core tens of us)
     for (Slot& slot : s->slots) {
       if (slot.busy || s->queue.empty() || s->paused) continue;
       if (!admit(s, slot)) break;
-      slot.issue_pending = true;
-      slot.cv_issue.notify_one();
       progressed = true;
+      const bool handing = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot& x) { return x.issue_pending; });
+      if (s->queue.empty() && s->issuing == 0 && !handing) {
+        issue(s, slot, lk);
+      } else {
+        slot.issue_pending = true;
+        slot.cv_issue.notify_one();
+      }
     }
     const bool inflight = std::any_of(s->slots.begin(), s->slots.end(), [](const Slot& x) { return x.busy; });
     if (s->stop && s->queue.empty() && !inflight) break;
