@@ -286,11 +286,13 @@ tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels,
 
 /* Time the schedule candidates of each group on the plan's own data and keep
  * the fastest.  The schedule tuned is that of the kernel a run without levels
- * uses.  For the groups coded one 16x16 block per thread (8-bit samples in
- * the fused quantiser range; warps claiming 32-block tiles) the candidates are the kernel's compiled configurations
- * (warps per CTA, column pairs parked in shared memory, input stages: see
- * tx16_plan_variant) and, for each, the resident CTAs per SM and the tiles
- * per claim; for the others, the CTAs per SM and tiles per claim.
+ * uses.  For the fused groups (8-bit samples in the fused quantiser range) the
+ * candidates are both mappings of blocks to lanes -- one 16x16 block per
+ * thread (warps claiming 32-block tiles) in each of its compiled
+ * configurations (warps per CTA, column pairs parked in shared memory, input
+ * stages: see tx16_plan_variant), and the pair kernel (two blocks per pair of
+ * binary32 lanes, CTAs claiming 16-block tiles) -- and, for each, the resident
+ * CTAs per SM and the tiles per claim.
  * cache_path: a text file of tuned schedules keyed by device, group and size
  * class (read and extended), or NULL.  Synchronous on `stream`; writes the
  * outputs. */
@@ -303,18 +305,18 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
 tx16_status tx16_plan_info(const tx16_plan* plan, int32_t* runs, int32_t* zone, int32_t* tiles,
                            int32_t* ctas_per_sm, int32_t* chunk, int32_t max_runs);
 
-/* The compiled configuration group `run` uses (groups coded one block per
- * thread): its index
- * (-1 for a group without configurations), warps per CTA, column pairs parked
- * in shared memory and input stages.  Any output may be NULL.  TX16_EINVAL
- * for a run index out of range. */
+/* The mapping and configuration group `run` uses: the configuration index of
+ * the one-block-per-thread kernel, or -1 for the pair kernel (and for the
+ * general kernel's group), with its warps per CTA, column pairs parked in
+ * shared memory and input stages (0 for -1).  Any output may be NULL.
+ * TX16_EINVAL for a run index out of range. */
 tx16_status tx16_plan_variant(const tx16_plan* plan, int32_t run, int32_t* variant, int32_t* warps_per_cta,
                               int32_t* parked_pairs, int32_t* stages);
 
-/* Pin the schedule of group `run`: configuration index (0 for groups without
- * configurations), resident CTAs per SM (0 = all that fit) and tiles per
- * claim (>= 1).  Results do not depend on the schedule.  TX16_EINVAL for a
- * run of the general kernel or out-of-range values. */
+/* Pin the schedule of group `run`: configuration index (as tx16_plan_variant
+ * reports it: -1 selects the pair kernel), resident CTAs per SM (0 = all that
+ * fit) and tiles per claim (>= 1).  Results do not depend on the schedule.
+ * TX16_EINVAL for a run of the general kernel or out-of-range values. */
 tx16_status tx16_plan_set_schedule(tx16_plan* plan, int32_t run, int32_t variant, int32_t ctas_per_sm,
                                    int32_t chunk);
 

@@ -360,16 +360,18 @@ constexpr int kBtVariants = 3;
 // Settings of class C, variant VAR, for SB-byte samples.  16-bit samples
 // (classes A..C, variant 0 only): TX16_BT16_WARPS warps per CTA,
 // TX16_BT16_MINCTAS CTAs, one stage, TX16_BT16_PARK_A parked pairs in class A
-// (measured on 3840x2160 10-bit frames: 4499 against 4401 Mblocks/s with one
-// parked) and TX16_BT16_PARK in B and C.
+// and TX16_BT16_PARK in B and C.  Measured on 3840x2160 10-bit frames at
+// r = 16 (Mblocks/s): 4-warp CTAs x 3, none parked, 4389; x 2 with one
+// parked 4306; x 3 with one parked 4310; 1-warp CTAs x 8, none parked, 4347;
+// class A (r = 4) with none parked 4499 against 4401 with one.
 #ifndef TX16_BT16_WARPS
 #define TX16_BT16_WARPS 4
 #endif
 #ifndef TX16_BT16_MINCTAS
-#define TX16_BT16_MINCTAS 2
+#define TX16_BT16_MINCTAS 3
 #endif
 #ifndef TX16_BT16_PARK
-#define TX16_BT16_PARK 1
+#define TX16_BT16_PARK 0
 #endif
 #ifndef TX16_BT16_PARK_A
 #define TX16_BT16_PARK_A 0

@@ -41,11 +41,12 @@ struct ClassRun {
   int ntiles;      // tiles of the run (16 blocks, pair kernel)
   int ctas_per_sm; // 0: as many as fit
   int chunk;       // tiles per claim
-  // classes the one-block-per-thread kernel takes when no levels are asked:
-  // its own table (tile0 in warp tiles of 32 blocks) and schedule
-  bool bt;
+  // classes the one-block-per-thread kernel can take when no levels are
+  // asked: its own table (tile0 in warp tiles of 32 blocks) and schedule
+  bool bt;  // the mapping a run without levels uses: one block per thread (else the pair kernel)
   int bt_ntiles, bt_ctas_per_sm, bt_chunk;
   int bt_variant;  // compiled configuration of that kernel (0: the default)
+  bool bt_ok;      // the one-block-per-thread kernel takes this class
 };
 
 }  // namespace
@@ -131,7 +132,8 @@ tx16_status tx16_plan_create(const tx16_image* in, const tx16_image* out, int32_
   p->n = n;
   p->has_dst = out != nullptr;
   for (int c = -1; c <= 5; ++c) {
-    ClassRun r{c, int(p->table.size()), 0, 0, 0, 1, c >= 0 && fused_bt_supports(c, false), 0, 0, 1, 0};
+    const bool bt_ok = c >= 0 && fused_bt_supports(c, false);
+    ClassRun r{c, int(p->table.size()), 0, 0, 0, 1, bt_ok, 0, 0, 1, 0, bt_ok};
     for (int i = 0; i < n; ++i) {
       if (cls[i] != c) continue;
       ImgParam q = params[i];
@@ -226,7 +228,8 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, plan->device) != cudaSuccess) return TX16_ECUDA;
-  // cache: one line per class key "device|zone|dst|tiles_bucket ctas chunk"
+  // cache: one line per class, "device|zone|dst|tiles_bucket[|bt] ctas chunk variant" (variant -1:
+  // the pair kernel)
   std::vector<std::string> cache;
   if (cache_path != nullptr) {
     if (FILE* f = std::fopen(cache_path, "r")) {
@@ -247,50 +250,62 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
     char key[320];
     // the schedule tuned is that of the kernel a run without levels uses
     std::snprintf(key, sizeof key, "%s|%d|%d|%d%s", dev.c_str(), r.zone, int(plan->has_dst), bucket,
-                  r.bt ? "|bt" : "");
-    int& run_ctas = r.bt ? r.bt_ctas_per_sm : r.ctas_per_sm;
-    int& run_chunk = r.bt ? r.bt_chunk : r.chunk;
-    const int run_tiles = r.bt ? r.bt_ntiles : r.ntiles;
+                  r.bt_ok ? "|bt" : "");
+    const int nvar = r.bt_ok ? fused_bt_variants(r.zone) : 0;
+    // apply a schedule: var >= 0 a configuration of the one-block-per-thread
+    // kernel, -1 the pair kernel (two blocks per float2 pair, 16 threads per
+    // pair of blocks: the other mapping of rows and columns to lanes)
+    auto apply = [&](int var, int ctas, int chunk) {
+      r.bt = var >= 0;
+      if (r.bt) {
+        r.bt_variant = var;
+        r.bt_ctas_per_sm = ctas;
+        r.bt_chunk = chunk;
+      } else {
+        r.ctas_per_sm = ctas;
+        r.chunk = chunk;
+      }
+    };
     bool hit = false;
     for (const std::string& c : cache) {
-      int ctas = 0, chunk = 0, var = 0;
+      int ctas = 0, chunk = 0, var = -1;
       char k2[320];
       const int got = std::sscanf(c.c_str(), "%319s %d %d %d", k2, &ctas, &chunk, &var);
-      if (got >= 3 && std::string(k2) == key && (!r.bt || (var >= 0 && var < fused_bt_variants(r.zone)))) {
-        run_ctas = ctas;
-        run_chunk = chunk;
-        if (r.bt) r.bt_variant = got == 4 ? var : 0;
-        hit = true;
-      }
+      if (got < 3 || std::string(k2) != key) continue;
+      if (!r.bt_ok) var = -1;
+      if (var >= nvar) continue;
+      apply(var, ctas, chunk);
+      hit = true;
     }
     if (hit) continue;
-    // candidates: each compiled configuration of the kernel (one block per
-    // thread: warps per CTA, parked column pairs, input stages), and for
-    // each its resident CTAs per SM (the most that fit and up to 4 fewer)
-    // and tiles per claim
+    // candidates: the pair kernel and each compiled configuration of the
+    // one-block-per-thread kernel (warps per CTA, parked column pairs, input
+    // stages), and for each its resident CTAs per SM (the most that fit and
+    // up to 4 fewer) and tiles per claim
     float best = 1e30f;
-    int best_ctas = run_ctas, best_chunk = run_chunk, best_var = r.bt ? r.bt_variant : 0;
-    const int nvar = r.bt ? fused_bt_variants(r.zone) : 1;
+    int best_ctas = 0, best_chunk = 1, best_var = -1;
     const int chunks[] = {1, 2, 4, 8, 16};
-    for (int var = 0; var < nvar; ++var) {
-      const int maxc = r.bt ? fused_bt_list_max_ctas(r.zone, var, plan->has_dst)
-                            : fused_list_max_ctas(r.zone, false, plan->has_dst);
+    for (int var = -1; var < nvar; ++var) {
+      const bool use_bt = var >= 0;
+      const int maxc = use_bt ? fused_bt_list_max_ctas(r.zone, var, plan->has_dst)
+                              : fused_list_max_ctas(r.zone, false, plan->has_dst);
       if (maxc <= 0) continue;
       int warps = 1, park = 0, stages = 1;
-      if (r.bt) fused_bt_variant_info(r.zone, var, &warps, &park, &stages);
-      const int claimers_per_cta = r.bt ? warps : 1;  // warps of a one-block-per-thread CTA claim separately
+      if (use_bt) fused_bt_variant_info(r.zone, var, &warps, &park, &stages);
+      const int claimers_per_cta = use_bt ? warps : 1;  // warps of a one-block-per-thread CTA claim separately
+      const int tiles = use_bt ? r.bt_ntiles : r.ntiles;
       for (int ctas = maxc; ctas >= 1 && ctas >= maxc - 4; --ctas) {
         for (int chunk : chunks) {
-          if (chunk > std::max(1, run_tiles / (ctas * claimers_per_cta * device_sm_count()))) continue;
+          if (chunk > std::max(1, tiles / (ctas * claimers_per_cta * device_sm_count()))) continue;
           float ms = 0.f;
           for (int rep = 0; rep < 3; ++rep) {
             if (cudaMemsetAsync(plan->d_counters + i, 0, sizeof(unsigned), st) != cudaSuccess) return TX16_ECUDA;
             cudaEventRecord(e0, st);
             const tx16_status ls =
-                r.bt ? launch_fused_bt_list(r.zone, var, plan->has_dst, plan->d_bt_table + r.first, r.count,
-                                            r.bt_ntiles, plan->d_counters + i, chunk, ctas, nullptr, st)
-                     : launch_fused_list(r.zone, false, plan->has_dst, plan->d_table + r.first, r.count, r.ntiles,
-                                         plan->d_counters + i, chunk, ctas, nullptr, nullptr, st);
+                use_bt ? launch_fused_bt_list(r.zone, var, plan->has_dst, plan->d_bt_table + r.first, r.count,
+                                              r.bt_ntiles, plan->d_counters + i, chunk, ctas, nullptr, st)
+                       : launch_fused_list(r.zone, false, plan->has_dst, plan->d_table + r.first, r.count, r.ntiles,
+                                           plan->d_counters + i, chunk, ctas, nullptr, nullptr, st);
             if (ls != TX16_OK) return TX16_ECUDA;
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) return TX16_ECUDA;
@@ -307,9 +322,8 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
         }
       }
     }
-    run_ctas = best_ctas;
-    run_chunk = best_chunk;
-    if (r.bt) r.bt_variant = best_var;
+    if (best == 1e30f) continue;  // nothing could run: keep the defaults
+    apply(best_var, best_ctas, best_chunk);
     char line[400];
     std::snprintf(line, sizeof line, "%s %d %d %d\n", key, best_ctas, best_chunk, best_var);
     cache.emplace_back(line);
@@ -364,13 +378,15 @@ tx16_status tx16_plan_set_schedule(tx16_plan* plan, int32_t run, int32_t variant
     return TX16_EINVAL;
   ClassRun& r = plan->runs[run];
   if (r.zone < 0) return TX16_EINVAL;  // the general kernel has no schedule
-  if (r.bt) {
-    if (variant < 0 || variant >= fused_bt_variants(r.zone)) return TX16_EINVAL;
+  if (r.bt_ok && variant >= 0) {
+    if (variant >= fused_bt_variants(r.zone)) return TX16_EINVAL;
+    r.bt = true;
     r.bt_variant = variant;
     r.bt_ctas_per_sm = ctas_per_sm;
     r.bt_chunk = chunk;
   } else {
-    if (variant != 0) return TX16_EINVAL;
+    if (variant != -1 && !(variant == 0 && !r.bt_ok)) return TX16_EINVAL;  // the pair kernel
+    r.bt = false;
     r.ctas_per_sm = ctas_per_sm;
     r.chunk = chunk;
   }

@@ -116,11 +116,12 @@ def test_plan_mixed_depths_and_tiny_steps(tx):
 
 
 def test_every_compiled_configuration_gives_identical_results(tx):
-    """Each group of r <= 64 has several compiled configurations of the
-    one-block-per-thread kernel (warps per CTA, parked column pairs, input
-    stages).  Pinned one by one, with different CTAs per SM and tiles per
-    claim, every configuration writes the same samples and squared errors
-    (and the first run matches the oracle)."""
+    """Each fused group has two mappings of blocks to lanes: the pair kernel
+    (variant -1) and the one-block-per-thread kernel in several compiled
+    configurations (warps per CTA, parked column pairs, input stages).
+    Pinned one by one, with different CTAs per SM and tiles per claim, every
+    mapping and configuration writes the same samples and squared errors (and
+    the first run matches the oracle)."""
     import torch
 
     Hs, Ws = synth.uneven_sizes(31, 36, 16, 720)
@@ -137,7 +138,7 @@ def test_every_compiled_configuration_gives_identical_results(tx):
     sse = torch.zeros(len(imgs), dtype=torch.int64, device="cuda")
     ref_out, ref_sse = None, None
     seen = set()
-    for var in range(3):
+    for var in range(-1, 3):
         for ctas, chunk in ((0, 1), (1, 3)):
             for i in tuned:
                 plan.set_schedule(i, var, ctas, chunk)
@@ -159,11 +160,13 @@ def test_every_compiled_configuration_gives_identical_results(tx):
                 for a, b in zip(ref_out, got):
                     assert torch.equal(a, b)
                 assert torch.equal(ref_sse, sse)
-    # three distinct configurations per group, at least one with two stages
-    assert len(seen) == 12 and any(s[4] == 2 for s in seen)
+    # the pair kernel and three distinct configurations per group, at least
+    # one with two stages
+    assert len(seen) == 16 and any(s[4] == 2 for s in seen)
+    assert all(s[2:] == (0, 0, 0) for s in seen if s[1] == -1)
     with pytest.raises(tx.Tx16Error):
         plan.set_schedule(tuned[0], 3, 0, 1)
     plan.autotune(None)
     for i in tuned:
-        assert 0 <= plan.info()[i]["variant"] < 3
+        assert -1 <= plan.info()[i]["variant"] < 3
     plan.close()
