@@ -510,6 +510,15 @@ def emit_t8(w, T, rnd):
         w("  }")
         w("};")
         w("")
+    for u in range(8):  # row u of T8 is symmetric for even u, antisymmetric for odd u
+        assert all(T8[u][7 - j] == (-1) ** u * T8[u][j] for j in range(8)), "T8 row parity"
+    w("// T8 itself (rows: frequencies u; columns: samples j), for column passes that")
+    w("// accumulate T8 x term by term; row u is symmetric for even u, antisymmetric")
+    w("// for odd u")
+    w("constexpr int kT8[8][8] = {")
+    for u in range(8):
+        w("    {" + ", ".join(str(x) for x in T8[u]) + "},")
+    w("};")
     w("// the T8 networks of the mixed tiling codec: a column keeping rows u < H,")
     w("// a half row keeping columns v < V")
     w("template <int H>")

@@ -72,6 +72,9 @@ struct Mix8Class<1> {
 #ifndef TX16_MIX_STAGES
 #define TX16_MIX_STAGES 1
 #endif
+#ifndef TX16_MIX_MERGED
+#define TX16_MIX_MERGED 1
+#endif
 template <int C16>
 struct MixCfg {
   static constexpr int kWarps = TX16_MIX_WARPS, kMinCtas = TX16_MIX_MINCTAS, kStages = TX16_MIX_STAGES;
@@ -93,13 +96,15 @@ struct Mix8Consts {
 
 __device__ __forceinline__ int scale_class8(int u) { return (u & 1) ? 2 : ((u & 2) ? 1 : 0); }  // 0,2,1,2,0,2,1,2
 
+// col_net: the column pass runs the generated T8 network (its output signs
+// enter the scale); otherwise it accumulates T8 term by term (true signs).
 template <int U8, int V8>
-__device__ __forceinline__ void fill_consts8(const MixedParam& M, Mix8Consts<U8, V8>& Q, int lane) {
+__device__ __forceinline__ void fill_consts8(const MixedParam& M, Mix8Consts<U8, V8>& Q, int lane, bool col_net) {
   for (int idx = lane; idx < U8 * V8; idx += 32) {
     const int u = idx / V8;
     const int v = idx - u * V8;
     const int k = scale_class8(u) + scale_class8(v);
-    const float s = FwdRow8T8::sign(v) * FwdCol8M8::sign(u) < 0 ? -1.f : 1.f;
+    const float s = FwdRow8T8::sign(v) * (col_net ? FwdCol8M8::sign(u) : 1) < 0 ? -1.f : 1.f;
     const float fs = u < int(M.colh8[v]) ? s * (M.f8[k] * (1.f / 256.f)) : 0.f;
     Q.fs[u][v] = f2(fs);
     Q.gg[u][v] = f2(M.g8[k]);
@@ -168,6 +173,10 @@ __device__ __forceinline__ void mixed_tiles(const MixedParam* __restrict__ imgs,
   constexpr int kParkStride = kThreads * 8;
   constexpr int V = K::V, U = K::U, NP = V / 2;
   constexpr int V8 = K8::V, U8 = K8::U;
+  // class 0 (r8 <= 4: four cells per 8x8 block) shares the row loop with the
+  // 16x16 path; class 1 keeps a loop of its own (its 16 accumulators per half
+  // would not fit beside the 16x16 path's registers)
+  constexpr bool kMerged8 = C8 == 0 && TX16_MIX_MERGED;
   static_assert(kPark < NP, "at least one column pair stays in registers");
   extern __shared__ __align__(16) uint8_t mix_smem[];
   __shared__ PairConsts<U, NP> consts16[kWarps];
@@ -224,7 +233,7 @@ __device__ __forceinline__ void mixed_tiles(const MixedParam* __restrict__ imgs,
   prefetch(k, t, 0);
   int stage = 0;
   fill_consts_t<U, NP>(imgs[k].p, Q, lane);
-  fill_consts8<U8, V8>(imgs[k], Q8, lane);
+  fill_consts8<U8, V8>(imgs[k], Q8, lane, !kMerged8);
   unsigned long long acc = 0;
   bool rolling = false;  // the rows arrive pair by pair (one commit group per pair)
 
@@ -249,7 +258,7 @@ __device__ __forceinline__ void mixed_tiles(const MixedParam* __restrict__ imgs,
       end_k = tile_end_of(k);
       __syncwarp();
       fill_consts_t<U, NP>(imgs[k].p, Q, lane);
-      fill_consts8<U8, V8>(imgs[k], Q8, lane);
+      fill_consts8<U8, V8>(imgs[k], Q8, lane, !kMerged8);
     }
     const MixedParam& M = imgs[k];
     const ImgParam& I = M.p;
@@ -258,41 +267,19 @@ __device__ __forceinline__ void mixed_tiles(const MixedParam* __restrict__ imgs,
     const int2 c = valid ? block_coords(I.div_magic, I.nbx, blk) : make_int2(0, 0);
     uint8_t* const dblk = static_cast<uint8_t*>(I.dst) + int64_t(c.x) * 16 * I.dst_pitch + c.y * 16;
 
-    // ================= four 8x8 blocks with T8, one half at a time =================
-    unsigned e8 = 0;
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      float2 R[8][V8];  // R[i][v]: T8 row outputs of rows (i, 15 - i), half hh
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (kStages == 1 && hh == 0 && rolling) cp_async_wait_n(7 - i);  // rows i and 15 - i have arrived
-        const uint2 wa = *reinterpret_cast<const uint2*>(xrows + i * kRowStride + 8 * hh);
-        const uint2 wb = *reinterpret_cast<const uint2*>(xrows + (15 - i) * kRowStride + 8 * hh);
-        float2 X[8];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          X[j] = make_float2(byte256(wa.x, j), byte256(wb.x, j));
-          X[4 + j] = make_float2(byte256(wa.y, j), byte256(wb.y, j));
-        }
-        float2 Rr[V8];
-        N8::FR::run(X, Rr);
-#pragma unroll
-        for (int v = 0; v < V8; ++v) R[i][v] = Rr[v];
-      }
+    // ---- the 8x8 path after its column pass, per half hh: n_of(v, n) gives
+    // n[u] = sign * 256 Y8[u][v] per lane (u < H8[v]; lane y: odd u negated),
+    // the 2^29 of the DC already removed.  Quantiser, inverse column and row
+    // passes, rounding, squared error, the reconstruction into rows8.
+    auto finish8 = [&](int hh, auto&& n_of) -> unsigned {
+      unsigned e = 0;
       float2 Z8[8][V8];  // Z8[m][v] = (row m of the upper block, row 7 - m of the lower) at column v
       static_for<V8>([&](auto vc) {
         constexpr int v = decltype(vc)::value;
         constexpr int H = K8::H[v];
         using CN = Col8Nets<H>;
-        float2 a[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = R[i][v];
         float2 n[H];
-        CN::FC::run(a, n);  // n[u] = sign * 256 Y8[u][v] per lane, plus 2^29 at (0, 0)
-        if (v == 0) {
-          constexpr bool neg = FwdRow8T8::sign(0) * FwdCol8M8::sign(0) < 0;
-          n[0] = __fadd2_rn(n[0], f2(neg ? 536870912.f : -536870912.f));
-        }
+        n_of(vc, n);
         float2 w[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) w[u] = make_float2(0.f, 0.f);
@@ -315,28 +302,21 @@ __device__ __forceinline__ void mixed_tiles(const MixedParam* __restrict__ imgs,
         const uint2 xa = *reinterpret_cast<const uint2*>(xrows + m * kRowStride + 8 * hh);
         const uint2 xb = *reinterpret_cast<const uint2*>(xrows + (15 - m) * kRowStride + 8 * hh);
         unsigned d = __vabsdiffu4(xa.x, pa[0]);
-        e8 = __dp4a(d, d, e8);
+        e = __dp4a(d, d, e);
         d = __vabsdiffu4(xa.y, pa[1]);
-        e8 = __dp4a(d, d, e8);
+        e = __dp4a(d, d, e);
         d = __vabsdiffu4(xb.x, pb[0]);
-        e8 = __dp4a(d, d, e8);
+        e = __dp4a(d, d, e);
         d = __vabsdiffu4(xb.y, pb[1]);
-        e8 = __dp4a(d, d, e8);
+        e = __dp4a(d, d, e);
         *reinterpret_cast<uint2*>(rows8 + m * kRowStride + 8 * hh) = make_uint2(pa[0], pa[1]);
         *reinterpret_cast<uint2*>(rows8 + (15 - m) * kRowStride + 8 * hh) = make_uint2(pb[0], pb[1]);
       }
-    }
-
-    // ================= one 16x16 block with T =================
+      return e;
+    };
+    // ---- the 16x16 row pass of rows (i, 15 - i) from their unpacked samples
     float2 A[16][NP];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      unsigned wa[4], wb[4];
-      load_row_at<1>(xrows + i * kRowStride, kSlot, wa);
-      load_row_at<1>(xrows + (15 - i) * kRowStride, kSlot, wb);
-      float2 X[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) X[j] = make_float2(sample256<1>(wa, j), sample256<1>(wb, j));
+    auto row16 = [&](int i, const float2 (&X)[16]) {
       float2 S[NP], D[NP];
       N::FR::run(X, S, D);
 #pragma unroll
@@ -349,7 +329,99 @@ __device__ __forceinline__ void mixed_tiles(const MixedParam* __restrict__ imgs,
           A[15 - i][cp] = D[cp];
         }
       }
+    };
+    constexpr float kDc8 = FwdRow8T8::sign(0) * (kMerged8 ? 1 : FwdCol8M8::sign(0)) < 0 ? 536870912.f : -536870912.f;
+    unsigned e8 = 0;
+    if constexpr (kMerged8) {
+      // ==== one row loop for both paths: the samples are unpacked once; the
+      // 8x8 column pass accumulates T8 down the row pairs term by term (exact:
+      // every value is an integer multiple of 256 below 2^32)
+      float2 Y8[2][V8][U8];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int v = 0; v < V8; ++v)
+#pragma unroll
+          for (int u = 0; u < U8; ++u) Y8[hh][v][u] = make_float2(0.f, 0.f);
+      static_for<8>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        if (kStages == 1 && rolling) cp_async_wait_n(7 - i);  // rows i and 15 - i have arrived
+        unsigned wa[4], wb[4];
+        load_row_at<1>(xrows + i * kRowStride, kSlot, wa);
+        load_row_at<1>(xrows + (15 - i) * kRowStride, kSlot, wb);
+        float2 X[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) X[j] = make_float2(sample256<1>(wa, j), sample256<1>(wb, j));
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          float2 Rr[V8];
+          N8::FR::run(reinterpret_cast<const float2(&)[8]>(X[8 * hh]), Rr);
+          static_for<V8>([&](auto vc) {
+            constexpr int v = decltype(vc)::value;
+            static_for<U8>([&](auto uc) {
+              constexpr int u = decltype(uc)::value;
+              constexpr int c = u < K8::H[v] ? kT8[u][i] : 0;
+              if constexpr (c > 0) Y8[hh][v][u] = __fadd2_rn(Y8[hh][v][u], Rr[v]);
+              if constexpr (c < 0) Y8[hh][v][u] = sub2(Y8[hh][v][u], Rr[v]);
+            });
+          });
+        }
+        row16(i, X);
+      });
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh)
+        e8 += finish8(hh, [&](auto vc, auto& n) {
+          constexpr int v = decltype(vc)::value;
+          constexpr int Hv = K8::H[v];
+#pragma unroll
+          for (int u = 0; u < Hv; ++u) n[u] = Y8[hh][v][u];
+          if (v == 0) n[0] = __fadd2_rn(n[0], f2(kDc8));
+        });
+    } else {
+      // ==== the 8x8 path on its own, one half at a time: T8 row pass, T8
+      // column networks; then the 16x16 row loop
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float2 R[8][V8];  // R[i][v]: T8 row outputs of rows (i, 15 - i), half hh
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (kStages == 1 && hh == 0 && rolling) cp_async_wait_n(7 - i);  // rows i and 15 - i have arrived
+          const uint2 wa = *reinterpret_cast<const uint2*>(xrows + i * kRowStride + 8 * hh);
+          const uint2 wb = *reinterpret_cast<const uint2*>(xrows + (15 - i) * kRowStride + 8 * hh);
+          float2 X[8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            X[j] = make_float2(byte256(wa.x, j), byte256(wb.x, j));
+            X[4 + j] = make_float2(byte256(wa.y, j), byte256(wb.y, j));
+          }
+          float2 Rr[V8];
+          N8::FR::run(X, Rr);
+#pragma unroll
+          for (int v = 0; v < V8; ++v) R[i][v] = Rr[v];
+        }
+        e8 += finish8(hh, [&](auto vc, auto& n) {
+          constexpr int v = decltype(vc)::value;
+          float2 a[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) a[i] = R[i][v];
+          constexpr int Hv = K8::H[v];
+          Col8Nets<Hv>::FC::run(a, n);  // n[u] = sign * 256 Y8[u][v] per lane, plus 2^29 at (0, 0)
+          if (v == 0) n[0] = __fadd2_rn(n[0], f2(kDc8));
+        });
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        unsigned wa[4], wb[4];
+        load_row_at<1>(xrows + i * kRowStride, kSlot, wa);
+        load_row_at<1>(xrows + (15 - i) * kRowStride, kSlot, wb);
+        float2 X[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) X[j] = make_float2(sample256<1>(wa, j), sample256<1>(wb, j));
+        row16(i, X);
+      }
     }
+
+    // ================= one 16x16 block with T: column pass onwards =================
     float2 Zr[8][V];
     static_for<NP>([&](auto cpc) {
       constexpr int cp = decltype(cpc)::value;

@@ -3775,6 +3775,19 @@ struct InvRow8T8 {
   }
 };
 
+// T8 itself (rows: frequencies u; columns: samples j), for column passes that
+// accumulate T8 x term by term; row u is symmetric for even u, antisymmetric
+// for odd u
+constexpr int kT8[8][8] = {
+    {1, 1, 1, 1, 1, 1, 1, 1},
+    {1, 0, 0, 0, 0, 0, 0, -1},
+    {1, 0, 0, -1, -1, 0, 0, 1},
+    {0, 0, -1, 0, 0, 1, 0, 0},
+    {1, -1, -1, 1, 1, -1, -1, 1},
+    {0, -1, 0, 0, 0, 0, 1, 0},
+    {0, -1, 1, 0, 0, 1, -1, 0},
+    {0, 0, 0, -1, 1, 0, 0, 0},
+};
 // the T8 networks of the mixed tiling codec: a column keeping rows u < H,
 // a half row keeping columns v < V
 template <int H>
