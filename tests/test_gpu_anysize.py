@@ -95,6 +95,9 @@ CASES = [
     ((17, 40), 12, None, 8),      # 16-bit, last block 8 wide: tight pitch
     ((21, 9), 12, 2.0, 256),
     ((48, 64), 8, 16.0, 16),      # whole blocks
+    ((100, 64), 8, 16.0, 128),    # ragged bottom, class E
+    ((40, 48), 8, None, 256),     # ragged bottom, class F, no quantiser
+    ((45, 70), 8, 8.0, 100),      # ragged both ways, class E
 ]
 
 

@@ -267,12 +267,13 @@ def test_wide_and_tall_images(tx):
 # Codec without level output: several images per launch, tiles that straddle
 # images, and batches large enough that every warp codes tiles of several
 # images in turn.  A batch with fewer 32-block warp tiles than the GPU has
-# SMs runs on the two-blocks-per-pair kernel; a larger one, for up to 8 kept
-# columns, on the one-block-per-thread kernel.  `repeat` copies of the set of
-# shapes give both: 1 copy (25 warp tiles) the pair kernel, 20 copies (500
-# warp tiles) the one-block-per-thread kernel.
+# SMs runs on the two-blocks-per-pair kernel; a larger one on the
+# one-block-per-thread kernel (every zonal class).  `repeat` copies of the
+# set of shapes give both: 1 copy (25 warp tiles) the pair kernel, 20 copies
+# (500 warp tiles) the one-block-per-thread kernel.
 # --------------------------------------------------------------------------
-NOLEV_CASES = [(16.0, 8), (None, 8), (16.0, 16), (None, 16), (12.0, 32), (None, 32), (16.0, 64), (8.0, 200)]
+NOLEV_CASES = [(16.0, 8), (None, 8), (16.0, 16), (None, 16), (12.0, 32), (None, 32), (16.0, 64), (None, 64),
+               (16.0, 128), (None, 100), (8.0, 200), (None, 256)]
 
 
 @pytest.mark.parametrize("repeat", [1, 20])
@@ -379,10 +380,10 @@ def test_codec_16bit_2160p_frame(tx):
 # --------------------------------------------------------------------------
 # Clamping at both ends of the sample range: planes of extreme samples whose
 # zonal reconstructions overshoot far below 0 and above the peak (Gibbs-like
-# ringing), through the one-block-per-thread kernels (no levels, r <= 32, a
-# batch of at least one warp tile per SM: `repeat` = 30 copies of the seven
-# planes, 210 warp tiles), the pair kernel (levels requested, r > 32, or the
-# seven planes alone) and the 16-bit path
+# ringing), through the one-block-per-thread kernels (no levels, a batch of
+# at least one warp tile per SM: `repeat` = 30 copies of the seven planes,
+# 210 warp tiles), the pair kernel (levels requested, or the seven planes
+# alone) and the 16-bit path
 # --------------------------------------------------------------------------
 def _extreme_planes(bits):
     peak = (1 << bits) - 1
@@ -399,7 +400,8 @@ def _extreme_planes(bits):
 
 
 @pytest.mark.parametrize("q,r,levels,repeat", [(None, 32, False, 30), (None, 16, False, 30), (64.0, 4, False, 30),
-                                               (64.0, 16, False, 30), (16.0, 32, False, 30), (64.0, 16, False, 1),
+                                               (64.0, 16, False, 30), (16.0, 32, False, 30), (64.0, 64, False, 30),
+                                               (32.0, 128, False, 30), (24.0, 256, False, 30), (64.0, 16, False, 1),
                                                (8.0, 16, True, 1), (64.0, 64, False, 1), (32.0, 256, True, 1),
                                                (None, 150, True, 1)])
 def test_codec_extreme_planes_clamp(tx, q, r, levels, repeat):
