@@ -137,11 +137,12 @@ struct RowNets<16> {
 //      6 x 2: 10249; 1 x 16 with one parked: 10431)
 //   C  4-warp CTAs x 3, one parked: 9729 (none: 9608; two: 9440; 1 x 12 with
 //      one: 9683)
-//   D  1-warp CTAs x 12, one parked: 7522 (two: 7354; 1 x 8 none, 255
-//      registers: 6882)
-//   E  1-warp CTAs x 8 (255 registers), two parked: 5539 (three 5357, one
-//      5524; 2-warp x 4: 5381)
-//   F  1-warp CTAs x 8, one parked: 4359 (two 4229, three 4027)
+//   D  4-warp CTAs x 3, one parked: 7633 (1 x 12 with one: 7514-7522; with
+//      two: 7354; 1 x 8 none, 255 registers: 6882)
+//   E  1-warp CTAs x 8 (255 registers), two parked: 5482-5539 (three 5357,
+//      one 5524; 2-warp x 4: 5381; 4-warp x 2: 5412)
+//   F  1-warp CTAs x 8, one parked: 4334-4359 (two 4229, three 4027; 4-warp
+//      x 2: 4163)
 // Fewer warps with nothing parked beat 16 warps with a pair parked once the
 // warps stopped refilling their tables at every tile.
 #ifndef TX16_BT_WARPS_A
@@ -172,10 +173,10 @@ struct RowNets<16> {
 #define TX16_BT_PARK_C 1
 #endif
 #ifndef TX16_BT_WARPS_D
-#define TX16_BT_WARPS_D 1
+#define TX16_BT_WARPS_D 4
 #endif
 #ifndef TX16_BT_MINCTAS_D
-#define TX16_BT_MINCTAS_D 12
+#define TX16_BT_MINCTAS_D 3
 #endif
 #ifndef TX16_BT_PARK_D
 #define TX16_BT_PARK_D 1
@@ -333,7 +334,7 @@ struct BtAlt<2, 2> {
 };
 template <>
 struct BtAlt<3, 1> {
-  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 2, kStages = 1;
+  static constexpr int kWarps = 1, kMinCtas = 12, kPark = 1, kStages = 1;
 };
 template <>
 struct BtAlt<3, 2> {
