@@ -292,7 +292,8 @@ tx16_status tx16_plan_run_graph(tx16_plan* plan, uint64_t* sse, int32_t* levels,
  * configurations (warps per CTA, column pairs parked in shared memory, input
  * stages: see tx16_plan_variant), and the pair kernel (two blocks per pair of
  * binary32 lanes, CTAs claiming 16-block tiles) -- and, for each, the resident
- * CTAs per SM and the tiles per claim.
+ * CTAs per SM and the tiles per claim (for one block per thread also no
+ * claims: a contiguous run of tiles per CTA).
  * cache_path: a text file of tuned schedules keyed by device, group and size
  * class (read and extended), or NULL.  Synchronous on `stream`; writes the
  * outputs. */
@@ -315,7 +316,9 @@ tx16_status tx16_plan_variant(const tx16_plan* plan, int32_t run, int32_t* varia
 
 /* Pin the schedule of group `run`: configuration index (as tx16_plan_variant
  * reports it: -1 selects the pair kernel), resident CTAs per SM (0 = all that
- * fit) and tiles per claim (>= 1).  Results do not depend on the schedule.
+ * fit) and tiles per claim (>= 1; 0 for the one-block-per-thread kernel: no
+ * claims, each CTA a contiguous run of tiles).  Results do not depend on the
+ * schedule.
  * TX16_EINVAL for a run of the general kernel or out-of-range values. */
 tx16_status tx16_plan_set_schedule(tx16_plan* plan, int32_t run, int32_t variant, int32_t ctas_per_sm,
                                    int32_t chunk);

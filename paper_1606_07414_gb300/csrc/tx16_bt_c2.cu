@@ -6,6 +6,7 @@
 namespace tx16 {
 
 template tx16_status bt_batch<2>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
+template tx16_status bt_batch_keep<2>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
 template tx16_status bt_batch_ragged<2>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 template tx16_status bt_list<2>(int, bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
                                  cudaStream_t);

@@ -6,6 +6,7 @@
 namespace tx16 {
 
 template tx16_status bt_batch<3>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
+template tx16_status bt_batch_keep<3>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
 template tx16_status bt_batch_ragged<3>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 template tx16_status bt_list<3>(int, bool, const ImgParam*, int, int, unsigned*, int, int, unsigned long long*,
                                  cudaStream_t);

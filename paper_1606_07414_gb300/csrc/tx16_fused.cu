@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <vector>
 
 #include "tx16_internal.h"
 #include "tx16_net.cuh"
@@ -523,6 +524,40 @@ int fused_zone_class(const ImgParam* imgs, int n) {
 
 tx16_status launch_fused_u8(const ImgParam* imgs, int n, unsigned long long* sse, int32_t* levels,
                             cudaStream_t stream) {
+  // Without levels, a batch whose images fall in different zonal classes
+  // runs as one launch per class on the one-block-per-thread kernel, each
+  // image adding into its own SSE slot: coded in chunks by position, every
+  // image of a chunk would run at the chunk's largest class.
+  if (levels == nullptr && n > 1) {
+    std::vector<int> cls(n);
+    bool mixed = false;
+    int64_t blocks = 0;
+    for (int i = 0; i < n; ++i) {
+      cls[i] = fused_zone_class(&imgs[i], 1);
+      mixed = mixed || cls[i] != cls[0];
+      blocks += imgs[i].nblk;
+    }
+    const bool dst = imgs[0].dst != nullptr;
+    if (mixed && (blocks + 31) / 32 >= int64_t(device_sm_count())) {
+      std::vector<ImgParam> g;
+      for (int c = 0; c < 6; ++c) {
+        if (!fused_bt_supports(c, false)) continue;
+        g.clear();
+        for (int i = 0; i < n; ++i) {
+          if (cls[i] != c) continue;
+          ImgParam p = imgs[i];
+          p.out_index = i;
+          g.push_back(p);
+        }
+        for (size_t s = 0; s < g.size(); s += kMaxImg) {
+          const int m = int(std::min<size_t>(kMaxImg, g.size() - s));
+          const tx16_status st = launch_fused_bt_grouped(c, dst, g.data() + s, m, sse, stream);
+          if (st != TX16_OK) return st;
+        }
+      }
+      return TX16_OK;
+    }
+  }
   for (int s = 0; s < n; s += kMaxImg) {
     const int m = std::min(kMaxImg, n - s);
     const int zone = fused_zone_class(imgs + s, m);

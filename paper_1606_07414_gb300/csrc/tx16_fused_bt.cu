@@ -11,6 +11,12 @@
 
 namespace tx16 {
 
+extern template tx16_status bt_batch_keep<0>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_keep<1>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_keep<2>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_keep<3>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_keep<4>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
+extern template tx16_status bt_batch_keep<5>(bool, const ImgParam*, int, unsigned long long*, cudaStream_t);
 extern template tx16_status bt_batch<0>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 extern template tx16_status bt_batch<1>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
 extern template tx16_status bt_batch<2>(bool, int, const ImgParam*, int, unsigned long long*, cudaStream_t);
@@ -141,6 +147,19 @@ tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, uns
     case 3: return bt_batch<3>(dst, 1, imgs, n, sse, stream);
     case 4: return bt_batch<4>(dst, 1, imgs, n, sse, stream);
     case 5: return bt_batch<5>(dst, 1, imgs, n, sse, stream);
+    default: return TX16_EINVAL;
+  }
+}
+
+tx16_status launch_fused_bt_grouped(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
+                                    cudaStream_t stream) {
+  switch (zone) {
+    case 0: return bt_batch_keep<0>(dst, imgs, n, sse, stream);
+    case 1: return bt_batch_keep<1>(dst, imgs, n, sse, stream);
+    case 2: return bt_batch_keep<2>(dst, imgs, n, sse, stream);
+    case 3: return bt_batch_keep<3>(dst, imgs, n, sse, stream);
+    case 4: return bt_batch_keep<4>(dst, imgs, n, sse, stream);
+    case 5: return bt_batch_keep<5>(dst, imgs, n, sse, stream);
     default: return TX16_EINVAL;
   }
 }

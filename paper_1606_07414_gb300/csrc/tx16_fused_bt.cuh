@@ -980,6 +980,11 @@ template <int C, int VAR, bool DST>
 __global__ void __launch_bounds__(32 * BtCfg<C, VAR, 1>::kWarps, BtCfg<C, VAR, 1>::kMinCtas)
     fused_bt_list_kernel(const ImgParam* __restrict__ imgs, int nimg, int ntiles, unsigned* counter, int chunk,
                          unsigned long long* sse) {
+  if (chunk == 0) {  // static: a contiguous run of tiles per CTA, no claims
+    CtaChunkWarps sched(int(blockIdx.x), int(gridDim.x), int(threadIdx.x >> 5), BtCfg<C, VAR, 1>::kWarps, ntiles);
+    bt_tiles_t<C, VAR, DST, 1, false>(imgs, nimg, ntiles, sse, sched);
+    return;
+  }
   DynamicWarps sched{counter, ntiles, chunk, 0, 0};
   bt_tiles_t<C, VAR, DST, 1, false>(imgs, nimg, ntiles, sse, sched);
 }
@@ -1079,6 +1084,13 @@ tx16_status bt_batch(bool dst, int sb, const ImgParam* imgs, int n, unsigned lon
     return launch_bt_dst<kMaxImg, C, 2>(dst, imgs, n, sse, stream);
   }
   return TX16_EINVAL;
+}
+// 8-bit images whose out_index are their SSE slots of sse (a subset of a
+// call's images, grouped by zonal class), at most kMaxImg.
+template <int C>
+tx16_status bt_batch_keep(bool dst, const ImgParam* imgs, int n, unsigned long long* sse, cudaStream_t stream) {
+  return dst ? launch_bt<kMaxImg, C, true, 1>(imgs, n, sse, stream, true)
+             : launch_bt<kMaxImg, C, false, 1>(imgs, n, sse, stream, true);
 }
 // Images of ragged height (see kBtMissingShift), out_index = SSE slot of sse,
 // at most kMaxImg.

@@ -86,6 +86,10 @@ int fused_list_max_ctas(int zone, bool lev, bool dst);  // resident CTAs per SM
 bool fused_bt_supports(int zone, bool levels);
 tx16_status launch_fused_bt(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
                             cudaStream_t stream);
+// The same over images whose out_index are their SSE slots of sse (at most
+// kMaxImg): a subset of a call's images, grouped by class.
+tx16_status launch_fused_bt_grouped(int zone, bool dst, const ImgParam* imgs, int n, unsigned long long* sse,
+                                    cudaStream_t stream);
 // Its work-list form: descriptors in device memory with tile0 in warp tiles
 // of 32 blocks (bt_warp_tiles), relative to the list and ascending; warps
 // claim `chunk` tiles at a time from *counter (zeroed before the launch).

@@ -284,7 +284,7 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
     // up to 4 fewer) and tiles per claim
     float best = 1e30f;
     int best_ctas = 0, best_chunk = 1, best_var = -1;
-    const int chunks[] = {1, 2, 4, 8, 16};
+    const int chunks[] = {0, 1, 2, 4, 8, 16};  // 0: a static contiguous run per CTA (one block per thread)
     for (int var = -1; var < nvar; ++var) {
       const bool use_bt = var >= 0;
       const int maxc = use_bt ? fused_bt_list_max_ctas(r.zone, var, plan->has_dst)
@@ -296,6 +296,7 @@ tx16_status tx16_plan_autotune(tx16_plan* plan, const char* cache_path, void* st
       const int tiles = use_bt ? r.bt_ntiles : r.ntiles;
       for (int ctas = maxc; ctas >= 1 && ctas >= maxc - 4; --ctas) {
         for (int chunk : chunks) {
+          if (chunk == 0 && !use_bt) continue;
           if (chunk > std::max(1, tiles / (ctas * claimers_per_cta * device_sm_count()))) continue;
           float ms = 0.f;
           for (int rep = 0; rep < 3; ++rep) {
@@ -374,7 +375,7 @@ tx16_status tx16_plan_variant(const tx16_plan* plan, int32_t run, int32_t* varia
 
 tx16_status tx16_plan_set_schedule(tx16_plan* plan, int32_t run, int32_t variant, int32_t ctas_per_sm,
                                    int32_t chunk) {
-  if (plan == nullptr || run < 0 || run >= int32_t(plan->runs.size()) || ctas_per_sm < 0 || chunk < 1)
+  if (plan == nullptr || run < 0 || run >= int32_t(plan->runs.size()) || ctas_per_sm < 0 || chunk < 0)
     return TX16_EINVAL;
   ClassRun& r = plan->runs[run];
   if (r.zone < 0) return TX16_EINVAL;  // the general kernel has no schedule
@@ -386,6 +387,7 @@ tx16_status tx16_plan_set_schedule(tx16_plan* plan, int32_t run, int32_t variant
     r.bt_chunk = chunk;
   } else {
     if (variant != -1 && !(variant == 0 && !r.bt_ok)) return TX16_EINVAL;  // the pair kernel
+    if (chunk < 1) return TX16_EINVAL;  // claims only
     r.bt = false;
     r.ctas_per_sm = ctas_per_sm;
     r.chunk = chunk;

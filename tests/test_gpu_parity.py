@@ -464,3 +464,26 @@ def test_codec_without_levels_ragged_many_images(tx, q, r):
     assert np.array_equal(got, ref)
     for i in range(n):
         assert int(sse[i].item()) == O.sse(imgs[i], from_dev(outs[i], 8)), i
+
+
+def test_codec_batch_mixed_classes_grouped(tx):
+    """One tx16_codec_batch call (no levels) over images of every zonal class
+    interleaved, large enough for the one-block-per-thread kernel: the library
+    runs one launch per class, each image adding into its own SSE slot."""
+    import torch
+
+    rs = [4, 256, 16, 100, 32, 64, 8, 150, 1]
+    qs = [16.0, None, 8.0, 32.0]
+    shapes = [(80, 272), (48, 528), (160, 640), (32, 48), (64, 16)] * 12  # 223 warp tiles
+    imgs = [synth.ar1_image(4100 + i, h, w, 0.9 + 0.01 * (i % 8), 8) for i, (h, w) in enumerate(shapes)]
+    qp = [(qs[i % 4], rs[i % 9]) for i in range(len(imgs))]
+    keep = [to_dev(im) for im in imgs]
+    outs = [empty_like_img(h, w, 8, pad=16) for h, w in shapes]
+    sse = torch.full((len(imgs),), -1, dtype=torch.int64, device="cuda")
+    tx.tx16_codec_batch([tx.image(d) for d in keep], [tx.image(o) for o in outs], qp, sse=sse)
+    torch.cuda.synchronize()
+    for i, (im, (q, r)) in enumerate(zip(imgs, qp)):
+        ref = oracle_blocks(O.image_to_blocks(im.astype(np.int64)), q, r, 8)
+        rec = from_dev(outs[i], 8)
+        assert np.array_equal(O.image_to_blocks(rec.astype(np.int64)), ref["recon"]), i
+        assert int(sse[i].item()) == O.sse(im, rec), i

@@ -139,7 +139,8 @@ def test_every_compiled_configuration_gives_identical_results(tx):
     ref_out, ref_sse = None, None
     seen = set()
     for var in range(-1, 3):
-        for ctas, chunk in ((0, 1), (1, 3)):
+        # chunk 0: no claims, a contiguous run of tiles per CTA (one block per thread)
+        for ctas, chunk in ((0, 1), (1, 3)) + (((0, 0),) if var >= 0 else ()):
             for i in tuned:
                 plan.set_schedule(i, var, ctas, chunk)
             for o in outs:
