@@ -532,16 +532,17 @@ tx16_status launch_fused_u8(const ImgParam* imgs, int n, unsigned long long* sse
     std::vector<int> cls(n);
     bool mixed = false;
     int64_t blocks = 0;
+    bool all_bt = true;  // every class present runs on the one-block-per-thread kernel
     for (int i = 0; i < n; ++i) {
       cls[i] = fused_zone_class(&imgs[i], 1);
       mixed = mixed || cls[i] != cls[0];
+      all_bt = all_bt && fused_bt_supports(cls[i], false);
       blocks += imgs[i].nblk;
     }
     const bool dst = imgs[0].dst != nullptr;
-    if (mixed && (blocks + 31) / 32 >= int64_t(device_sm_count())) {
+    if (mixed && all_bt && (blocks + 31) / 32 >= int64_t(device_sm_count())) {
       std::vector<ImgParam> g;
       for (int c = 0; c < 6; ++c) {
-        if (!fused_bt_supports(c, false)) continue;
         g.clear();
         for (int i = 0; i < n; ++i) {
           if (cls[i] != c) continue;
