@@ -550,7 +550,9 @@ def sign_fn(signs):
             f"0x{zero:04x}u, i); }}")
 
 
-def main():
+def main(path=None):
+    """Write the header (to `path`, default tx16_pairnet.cuh beside this file),
+    checking every emitted network against the matrix it realises."""
     T = matrix_from_network(False)
     Tt = matrix_from_network(True)
     assert all(Tt[i][j] == T[j][i] for i in range(16) for j in range(16)), "inverse is not T^t"
@@ -678,7 +680,8 @@ def main():
     w(f"constexpr unsigned kFwdNegMask = 0x{sum(1 << i for i, x in enumerate(fwd_sign) if x < 0):04x}u;")
     w("}  // namespace pairnet")
     w("}  // namespace tx16")
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tx16_pairnet.cuh")
+    if path is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tx16_pairnet.cuh")
     with open(path, "w") as f:
         f.write("\n".join(out) + "\n")
     print("wrote", path)

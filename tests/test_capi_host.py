@@ -237,3 +237,19 @@ def test_mixed_8x8_class_heights_are_the_zigzag_column_heights():
         assert U == max(colh), c
         assert H == colh[:V], c
         assert rows[int(c)] == colh, c
+
+
+def test_generated_networks_are_current(tmp_path):
+    """tx16_pairnet.cuh is what gen_networks.py writes today: regenerating it
+    (which re-checks every emitted network against T, T^t, T8 and T8^t on
+    random and unit vectors, and T8's parity and orthogonality) gives the
+    committed header byte for byte."""
+    import importlib.util
+
+    csrc = os.path.join(ROOT, "paper_1606_07414_gb300", "csrc")
+    spec = importlib.util.spec_from_file_location("gen_networks", os.path.join(csrc, "gen_networks.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    out = tmp_path / "pairnet.cuh"
+    gen.main(str(out))
+    assert out.read_bytes() == open(os.path.join(csrc, "tx16_pairnet.cuh"), "rb").read()
