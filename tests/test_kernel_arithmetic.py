@@ -63,3 +63,32 @@ def test_level_magnitude_by_the_2_23_shift():
     m = rd32(rd32(a.astype(np.float64) + 0.5).astype(np.float64) + 2.0 ** 23)
     got = m.astype(np.float64) - 2.0 ** 23
     assert np.array_equal(got, np.floor(a.astype(np.float64) + 0.5))
+
+
+def test_t8_lower_blocks_run_bottom_up():
+    """The mixed-tiling kernel runs the lower 8x8 blocks bottom-up in the
+    second lane (row 7 - i beside row i of the upper block), so both lanes use
+    the same T8 networks.  That rests on two identities, checked here on the
+    oracle's own T8 and its binary32 transposed network:
+      * forward: T8 applied to a reversed column gives (-1)^u times T8 of the
+        column (row u of T8 is symmetric for even u, antisymmetric for odd u);
+      * inverse: the binary32 transposed network applied to (-1)^u w gives the
+        reversed result of applying it to w, bit for bit (each stage output is
+        one rounded operation, and rounding to nearest is odd-symmetric)."""
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle import tx16_oracle as O
+
+    T8 = O.t8_matrix()
+    sign = np.array([(-1) ** u for u in range(8)], dtype=np.int64)
+    rng = np.random.default_rng(8)
+    cols = rng.integers(-40000, 40000, size=(2000, 8))
+    assert np.array_equal(cols[:, ::-1] @ T8.T, (cols @ T8.T) * sign)
+    # binary32 inverse on random coefficients, with exact zeros and ties of magnitude
+    w = (rng.standard_normal((4000, 8)) * rng.choice([1.0, 100.0, 1e4], size=(4000, 1))).astype(F32)
+    w[::7, 3:] = 0.0
+    z = O.t8_transpose_factored_fp32(w)
+    zs = O.t8_transpose_factored_fp32((w * sign.astype(F32)).astype(F32))
+    assert np.array_equal(zs.view(np.int32), z[:, ::-1].view(np.int32))
